@@ -1,0 +1,342 @@
+"""Benchmark: chunked 3D Gaussian + erode/dilate on a 1024^3 uint16 volume.
+
+One step = the whole filtering path on one synthetic porous-media tomogram
+(1024^3 uint16, 2 GiB): Gaussian sigma = 1, 2, 4 (FP32 accumulation, FP32
+outputs) and grayscale erosion and dilation with a ball of radius 3 (exact,
+uint16 outputs). `value` is volume voxels per second through the whole step
+with inputs and outputs resident in HBM; `e2e` is the same step through the
+C ABI with pinned host buffers (out-of-core executor, host<->device copies
+inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hp|reference]
+
+`--impl reference` times the CPU oracle (the test oracle, single-threaded
+FP64 C) on bounded sub-boxes of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxels/s for chunked 3D Gaussian + erode/dilate at 1024³ uint16; % of HBM peak"
+N = 1024
+SIGMAS = (1.0, 2.0, 4.0)
+BALL_R = 3
+SEED = 2511118900 + 1
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2032.0)), "measured"
+    except Exception:
+        return 6400.0, 2032.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(budget_s: float, seed_volume=None):
+    """Time the oracle on sub-boxes of the workload for about budget_s
+    seconds; returns (voxels/s, sample description)."""
+    import oracle
+    import synth
+    f = seed_volume
+    if f is None:
+        f, _ = synth.porous((96, 96, 96), SEED)    # same recipe, a smaller drawing
+    n = f.shape[0]
+    b = 16
+    rng = np.random.default_rng(7)
+    voxels, t0, boxes = 0, time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s:
+        lo = [int(v) for v in rng.integers(0, n - b, 3)]
+        for s in SIGMAS:
+            r = oracle.radius(s)
+            ilo = [max(0, c - r) for c in lo]
+            ihi = [min(n, c + b + r) for c in lo]
+            oracle.gaussian3d(f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]], s, gdims=f.shape,
+                              in_lo=ilo, out_lo=lo, out_shape=(b, b, b))
+        ilo = [max(0, c - BALL_R) for c in lo]
+        ihi = [min(n, c + b + BALL_R) for c in lo]
+        part = f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]]
+        for dil in (False, True):
+            oracle.morph3d(part, oracle.SE_BALL, BALL_R, dil, gdims=f.shape, in_lo=ilo, out_lo=lo,
+                           out_shape=(b, b, b))
+        voxels += b ** 3
+        boxes += 1
+    dt = time.perf_counter() - t0
+    return voxels / dt, f"{boxes} random {b}^3 output boxes (with halos) of the step, {dt:.1f} s"
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(min(per_step, 2.0))
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, sample = cpu_oracle_sample(per_step)
+        vals.append(v)
+    dt = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    line = {
+        "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic porous tomogram (seeded), bounded sub-box sample",
+        "config": {"workload": "porous 1024^3 u16: gaussian s=1,2,4 -> f32; erode+dilate ball r=3",
+                   "sample": sample},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_hp(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2511_11890_b300 as hp
+    import synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+
+    f, porosity = synth.porous(N, SEED)
+    x = torch.from_numpy(f).to(dev)
+    outs_g = [torch.empty((N, N, N), dtype=torch.float32, device=dev) for _ in SIGMAS]
+    out_e = torch.empty((N, N, N), dtype=torch.uint16, device=dev)
+    out_d = torch.empty((N, N, N), dtype=torch.uint16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    names = [f"gauss_s{s:g}" for s in SIGMAS] + ["erode_ball3", "dilate_ball3"]
+
+    def step(evs=None):
+        k = 0
+        for s, o in zip(SIGMAS, outs_g):
+            hp.gaussian3d(x, s, out=o)
+            if evs is not None:
+                evs[k].record(stream)
+            k += 1
+        hp.erode3d(x, "ball", BALL_R, out=out_e)
+        if evs is not None:
+            evs[k].record(stream)
+        hp.dilate3d(x, "ball", BALL_R, out=out_d)
+        if evs is not None:
+            evs[k + 1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    # timed region: K steps, events between the five kernels of every step
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in names] for _ in range(args.steps)]
+    first = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for i in range(args.steps):
+            first[i].record(stream)
+            step(ev[i])
+        end.record(stream)
+        torch.cuda.synchronize()
+    hp.stream_status(stream)
+    total_ms = start.elapsed_time(end)
+    per = {nm: 0.0 for nm in names}
+    for i in range(args.steps):
+        prev = first[i]
+        for nm, e in zip(names, ev[i]):
+            per[nm] += prev.elapsed_time(e) / args.steps
+            prev = e
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = ws * args.steps * N ** 3 / (total_ms / 1000.0)
+
+    # per-kernel rooflines: algorithmic bytes (u16 in + out) and FP32 FMAs
+    nvox = N ** 3
+    kern = {}
+    fma_peak_tflops = 148 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+    for s, nm in zip(SIGMAS, names):
+        r = int(np.floor(3 * s + 0.5))
+        byts = nvox * (2 + 4)
+        flops = nvox * 3 * (2 * r + 1) * 2
+        ms = per[nm]
+        kern[nm] = {"ms": ms, "GB/s": byts / ms / 1e6, "hbm_frac": byts / ms / 1e6 / hbm_gbs,
+                    "TFLOP/s": flops / ms / 1e9, "alu_frac": flops / ms / 1e9 / fma_peak_tflops}
+    for nm in names[3:]:
+        byts = nvox * 4
+        ms = per[nm]
+        kern[nm] = {"ms": ms, "GB/s": byts / ms / 1e6, "hbm_frac": byts / ms / 1e6 / hbm_gbs}
+    dom = max(names, key=lambda k: per[k])
+    dk = kern[dom]
+    if "alu_frac" in dk and dk["alu_frac"] > dk["hbm_frac"]:
+        roof = {"bound": "alu", "achieved": dk["TFLOP/s"], "peak": fma_peak_tflops,
+                "unit": "TFLOP/s", "frac": dk["alu_frac"], "traffic": None,
+                "kernel": dom, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        roof = {"bound": "hbm", "achieved": dk["GB/s"], "peak": hbm_gbs, "unit": "GB/s",
+                "frac": dk["hbm_frac"], "traffic": None, "kernel": dom, "peak_kind": peak_kind}
+    step_bytes = nvox * (3 * 6 + 2 * 4)
+    hbm_step_frac = step_bytes / (total_ms / args.steps) / 1e6 / hbm_gbs
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        del outs_g, out_e, out_d
+        torch.cuda.empty_cache()
+        xh = torch.from_numpy(f).pin_memory()
+        oh = [torch.empty((N, N, N), dtype=torch.float32).pin_memory() for _ in SIGMAS]
+        eh = torch.empty((N, N, N), dtype=torch.uint16).pin_memory()
+        dh = torch.empty((N, N, N), dtype=torch.uint16).pin_memory()
+
+        def hstep():
+            h2d = d2h = 0
+            for s, o in zip(SIGMAS, oh):
+                hp.gaussian3d(xh, s, out=o)
+                st = hp.stats()
+                h2d += st["h2d_bytes"]
+                d2h += st["d2h_bytes"]
+            for fn, o in ((hp.erode3d, eh), (hp.dilate3d, dh)):
+                fn(xh, "ball", BALL_R, out=o)
+                st = hp.stats()
+                h2d += st["h2d_bytes"]
+                d2h += st["d2h_bytes"]
+            return h2d, d2h
+
+        hstep()
+        ke = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            h2d, d2h = hstep()
+        dt = time.perf_counter() - t0
+        e2e = {"value": ws * ke * nvox / dt, "unit": "voxels/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke,
+               "link_GB/s": (h2d + d2h) / (dt / ke) / 1e9}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, sample = cpu_oracle_sample(args.cpu_seconds)
+        cpu = {"value": v, "unit": "voxels/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": f"synthetic porous tomogram (seeded, porosity {porosity:.3f})",
+            "config": {"workload": "porous 1024^3 u16: gaussian s=1,2,4 -> f32; erode+dilate ball r=3",
+                       "volume": [N, N, N], "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs (2 GiB) and outputs (16 GiB) larger than L2",
+                       "hbm_frac_of_step": hbm_step_frac},
+            "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 5 * args.steps, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hp", choices=["hp", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_hp(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

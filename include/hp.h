@@ -1,0 +1,203 @@
+/*
+ * hp.h -- C ABI of the B300-native chunked 3D filtering library (libhp).
+ *
+ * The operations are the filtering core of the Harpia library described in
+ * "Advancing Annotat3D with Harpia" (arXiv 2511.11890):
+ *   - Sec. III-C lists the filters: Gaussian smoothing, "Hessian" texture
+ *     features (here: Gaussian gradient magnitude and Laplacian of
+ *     Gaussian), erosion, dilation and thresholds.
+ *   - Sec. III-D gives the execution model: query free device memory and
+ *     reserve a fixed fraction (step 1), size chunks including padding
+ *     (step 2), and process overlapping, context-preserving chunks one by
+ *     one (step 3).
+ *   - Sec. IV-C fixes the memory contract: the library allocates and frees
+ *     its own device memory and never hands library-owned device memory to
+ *     the caller.
+ * The paper prints no formulas. The conventions used by every call:
+ *   - Volumes are dense, C order, f[z][y][x] with x fastest.
+ *   - Reflect boundary, half-sample symmetric (d c b a | a b c d).
+ *   - Gaussian radius r = floor(truncate * sigma + 0.5); taps are the
+ *     normalised sampled Gaussian g0 and its analytic derivatives
+ *     g1 = -k/sigma^2 g0, g2 = (k^2/sigma^4 - 1/sigma^2) g0 (not
+ *     re-normalised); a 1D filter is the convolution y[i] = sum_k g(k) x[i-k].
+ *   - Arithmetic is FP32 with FP32 accumulation; taps are generated and
+ *     normalised in FP64 and rounded once to FP32.
+ *   - Erosion takes the min over the structuring element B of f(p + o),
+ *     dilation the max of f(p - o); B is a cube of half-width radius or the
+ *     digital ball dz^2 + dy^2 + dx^2 <= radius^2. Morphology is exact.
+ *
+ * Execution mode follows where the volumes live:
+ *   - HP_DEVICE in and out: the data stays in device memory. The call
+ *     enqueues its kernels on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream) and returns without synchronising. Use
+ *     hp_stream_status() to collect asynchronous failures.
+ *   - HP_HOST in and out: out-of-core. The volume is cut into halo-padded
+ *     bricks sized to the memory budget and streamed through the device on
+ *     several CUDA streams. The call is synchronous. Host buffers that are
+ *     page-locked (cudaHostAlloc / cudaHostRegister, torch pin_memory) are
+ *     copied directly; other host buffers go through a pinned staging ring.
+ *     `stream` is ignored.
+ *   - Mixed locations return HP_ERR_UNSUPPORTED.
+ *
+ * Ownership: hp_volume is a non-owning view of caller memory. The caller
+ * keeps the memory alive and unchanged until the call (device mode: the
+ * enqueued work) completes. Every library-internal buffer is released
+ * before a host-mode call returns and, in device mode, freed in stream order
+ * on `stream`. The only memory kept across calls is the small cache of
+ * filter-bank launch plans (see hp_release_cache).
+ *
+ * Errors: every call returns an hp_status. On failure hp_last_error()
+ * returns a thread-local message; outputs are then unspecified. Input and
+ * output must not alias.
+ */
+#ifndef HP_H
+#define HP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HP_OK = 0,
+  HP_ERR_INVALID_ARG = 1, /* null pointer, bad dims, aliasing, bad sigma/radius */
+  HP_ERR_UNSUPPORTED = 2, /* dtype / structuring element / location combination */
+  HP_ERR_BUDGET = 3,      /* smallest legal brick does not fit the memory budget */
+  HP_ERR_OOM = 4,         /* device or pinned host allocation failed */
+  HP_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+  HP_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  HP_ERR_INTERNAL = 7
+} hp_status;
+
+typedef enum { HP_U8 = 0, HP_U16 = 1, HP_F16 = 2, HP_F32 = 3 } hp_dtype;
+typedef enum { HP_HOST = 0, HP_DEVICE = 1 } hp_loc;
+typedef enum { HP_SE_CUBE = 0, HP_SE_BALL = 1 } hp_se;
+typedef enum { HP_FILTER_G = 0, HP_FILTER_GM = 1, HP_FILTER_LOG = 2 } hp_filter_kind;
+
+/* Opaque, non-owning view of a dense C-order volume. */
+typedef struct hp_volume hp_volume;
+
+/* One output of a filter bank: kind = hp_filter_kind, sigma > 0.
+ * G = Gaussian; GM = sqrt(Dx^2 + Dy^2 + Dz^2) with D_a the first Gaussian
+ * derivative along axis a; LOG = Dxx + Dyy + Dzz. */
+typedef struct {
+  int kind;
+  double sigma;
+} hp_filter;
+
+/* Half-open box [lo, hi) in (z, y, x) order. */
+typedef struct {
+  int64_t lo[3];
+  int64_t hi[3];
+} hp_box;
+
+/* Library counters. Sizes in bytes; times in milliseconds. */
+typedef struct {
+  size_t budget_bytes;        /* effective budget used by the last host-mode call */
+  size_t peak_device_bytes;   /* peak library-owned device bytes during the last call */
+  size_t live_device_bytes;   /* library-owned device bytes now (excluding plan cache) */
+  size_t cached_device_bytes; /* device bytes held by cached filter-bank plans */
+  size_t pinned_host_bytes;   /* pinned staging bytes allocated by the last call */
+  uint64_t bricks;            /* bricks executed by the last call */
+  uint64_t h2d_bytes;         /* host-to-device bytes of the last call */
+  uint64_t d2h_bytes;         /* device-to-host bytes of the last call */
+  double wall_ms;             /* wall time of the last host-mode call */
+} hp_stats;
+
+/* Create a view of `data` (dtype, location) with extents nx (fastest), ny,
+ * nz, each >= 1. `data` may be NULL only if the view is never used as an
+ * input or output. Returns HP_ERR_INVALID_ARG on bad extents. */
+int hp_volume_create(hp_volume** out, void* data, hp_dtype dtype, hp_loc loc, int64_t nx,
+                     int64_t ny, int64_t nz);
+/* Destroy a view (never frees `data`). NULL is accepted. */
+int hp_volume_destroy(hp_volume* v);
+
+/* Device-memory budget for library-owned buffers (Sec. III-D step 1).
+ * bytes = 0 selects the default: 0.8 x the free device memory reported by
+ * cudaMemGetInfo at the start of each call. Process-wide and thread-safe.
+ * The environment variable HP_BUDGET (bytes) sets the initial value. */
+int hp_set_memory_budget(size_t bytes);
+int hp_get_memory_budget(size_t* bytes);
+
+/* Separable Gaussian or derivative-of-Gaussian filter (Sec. III-C, Gaussian
+ * smoothing and derivative features). order = {oz, oy, ox}, each in
+ * {0, 1, 2}; NULL means {0, 0, 0}. truncate <= 0 selects 3.0. Input dtype
+ * u8/u16/f16/f32; output dtype f32 or f16 (rounded to nearest even once).
+ * Radius up to 32. */
+int hp_gaussian3d(const hp_volume* in, hp_volume* out, double sigma, double truncate,
+                  const int order[3], void* stream);
+
+/* Multi-sigma filter bank: n outputs, outs[i] holds filter f[i]. All outputs
+ * have the input's extents and dtype f16 or f32. Device mode runs one
+ * persistent, CUDA-graph-captured launch over a work list of
+ * (brick, tile, sigma) items; the launch plan (graph + work list) is cached
+ * per shape, filter set, brick set and buffer addresses. truncate is 3.0. */
+int hp_filterbank3d(const hp_volume* in, hp_volume* const* outs, const hp_filter* f, int n,
+                    void* stream);
+/* As hp_filterbank3d, with the work list built over the given bricks
+ * (disjoint boxes covering the volume; halos are read from neighbouring
+ * bricks, so the result equals the whole-volume result bit for bit).
+ * Device mode only. */
+int hp_filterbank3d_bricks(const hp_volume* in, hp_volume* const* outs, const hp_filter* f, int n,
+                           const hp_box* bricks, int nbricks, void* stream);
+
+/* Grayscale erosion / dilation with a cube (half-width radius) or ball
+ * (radius) structuring element (Sec. III-C, label-editing morphology).
+ * Output dtype equals input dtype; results are exact. radius in [0, 16]. */
+int hp_erode3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
+int hp_dilate3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
+
+/* Global threshold (Sec. III-C, threshold algorithms): out (u8) = in > t,
+ * compared in the input's own precision (t is rounded to it). */
+int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream);
+
+/* Adjoint of the filter bank (device mode, f32): gin = sum_i J_i^T gouts[i],
+ * J_i the Jacobian of filter i at input `in`. Linear filters use the
+ * flipped-kernel correlation followed by the reflect fold-back;
+ * GM routes through D_a / GM (0 where GM = 0). Uses library scratch. */
+int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
+                            const hp_filter* f, int n, hp_volume* gin, void* stream);
+
+/* Subgradient of erosion (is_dilate = 0) or dilation (1), device mode, f32:
+ * gin[q] = sum of gout[p] over outputs p whose extreme source is q; among
+ * equal values the source with the smallest linear index wins. Deterministic
+ * (a gather, no atomics). Uses library scratch (an int32 index per voxel). */
+int hp_morph3d_backward(const hp_volume* in, const hp_volume* gout, int is_dilate, hp_se se,
+                        int radius, hp_volume* gin, void* stream);
+
+/* Chunk planner (Sec. III-D step 2), host only, no device work. Splits an
+ * (nz, ny, nx) volume into bricks whose core boxes tile it exactly; box i's
+ * input box is the hull of the reflected sources of its core grown by
+ * `halo`. Sized so that `stages` bricks in flight, each holding its input
+ * box (in_bytes per voxel) and core (out_bytes per voxel), fit `budget`
+ * bytes, with at least `min_bricks` bricks when the volume allows it.
+ * Writes up to max_bricks entries; *nbricks receives the count needed (call
+ * with max_bricks = 0 to size the arrays). */
+int hp_plan_bricks(int64_t nx, int64_t ny, int64_t nz, int halo, size_t in_bytes,
+                   size_t out_bytes, size_t budget, int stages, int min_bricks, hp_box* cores,
+                   hp_box* in_boxes, int max_bricks, int* nbricks);
+
+/* Synchronise `stream`, then read and clear the device error word that
+ * kernels set when a bounded wait gives up. Returns HP_OK, HP_ERR_TIMEOUT or
+ * HP_ERR_CUDA. */
+int hp_stream_status(void* stream);
+
+/* Free cached filter-bank launch plans (graphs and work lists). */
+int hp_release_cache(void);
+
+/* Counters of the last call; see hp_stats. */
+int hp_get_stats(hp_stats* s);
+
+/* Thread-local message for the last failing call on this thread. */
+const char* hp_last_error(void);
+
+/* Library version string. */
+const char* hp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HP_H */

@@ -1,0 +1,761 @@
+// C ABI of libhp: volumes, memory budget, chunk planner, out-of-core
+// executor and dispatch of the filtering kernels.
+//
+// The chunked execution model follows Harpia Sec. III-D:
+//   step 1 (resource profiling): the budget is the user value or a fixed
+//           fraction (0.8) of cudaMemGetInfo's free bytes;
+//   step 2 (chunk size estimation): hp_plan_bricks sizes halo-padded bricks
+//           so that the stages in flight fit the budget;
+//   step 3 (independent chunk execution): bricks stream through the device
+//           on several CUDA streams (H2D of the halo box, kernel, D2H of the
+//           core), each brick independent given its halo.
+// Library memory is allocated per call and released before return
+// (Sec. IV-C).
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <functional>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hp_internal.h"
+
+struct hp_volume {
+  void* data;
+  int dtype;
+  int loc;
+  int64_t nx, ny, nz;
+};
+
+namespace hp {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_msg;
+
+int set_error(int status, const std::string& msg) {
+  t_msg = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) return set_error(HP_ERR_OOM, m);
+  return set_error(HP_ERR_CUDA, m);
+}
+
+// ------------------------------------------------------------------ state
+static std::mutex g_mu;
+static size_t g_budget = 0;
+static bool g_budget_init = false;
+static hp_stats g_stats;
+static std::atomic<int64_t> g_live{0};
+static std::atomic<int64_t> g_peak{0};
+static std::atomic<int64_t> g_cached{0};
+
+static void track_alloc(int64_t b) {
+  int64_t now = g_live.fetch_add(b) + b;
+  int64_t p = g_peak.load();
+  while (now > p && !g_peak.compare_exchange_weak(p, now)) {
+  }
+}
+static void track_free(int64_t b) { g_live.fetch_sub(b); }
+
+size_t budget_setting() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_budget_init) {
+    g_budget_init = true;
+    const char* e = getenv("HP_BUDGET");
+    if (e) g_budget = (size_t)strtoull(e, nullptr, 10);
+  }
+  return g_budget;
+}
+
+static int effective_budget(size_t* out) {
+  size_t b = budget_setting();
+  if (b == 0) {
+    size_t fr = 0, tot = 0;
+    cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemGetInfo");
+    b = (size_t)(0.8 * (double)fr);
+  }
+  *out = b;
+  return HP_OK;
+}
+
+// Device error word: one int per device, set by kernels whose bounded waits
+// give up. Its device address is looked up once per device.
+__device__ int g_error_word;
+static int* g_err_ptr[64];
+static std::mutex g_err_mu;
+
+int* device_error_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return nullptr;
+    g_err_ptr[dev] = static_cast<int*>(p);
+  }
+  return g_err_ptr[dev];
+}
+
+int log_level() {
+  static int lv = [] {
+    const char* e = getenv("HP_LOG");
+    return e ? atoi(e) : 0;
+  }();
+  return lv;
+}
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// ------------------------------------------------------------ TMA maps
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode() {
+  static PFN_encodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_encodeTiled>(p);
+  });
+  return fn;
+}
+
+bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t dims[3], int bw,
+                  int bh) {
+  PFN_encodeTiled enc = get_encode();
+  if (!enc) return false;
+  CUtensorMapDataType t;
+  switch (dtype) {
+    case HP_U8: t = CU_TENSOR_MAP_DATA_TYPE_UINT8; break;
+    case HP_U16: t = CU_TENSOR_MAP_DATA_TYPE_UINT16; break;
+    case HP_F16: t = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+    case HP_F32: t = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+    default: return false;
+  }
+  const size_t es = dtype_size(dtype);
+  if ((uintptr_t)base % 16 != 0) return false;
+  if (dims[0] > (1LL << 31) || dims[1] > (1LL << 31) || dims[2] > (1LL << 31)) return false;
+  cuuint64_t gdim[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
+  cuuint64_t gstride[2] = {(cuuint64_t)(dims[0] * es), (cuuint64_t)(dims[0] * dims[1] * es)};
+  if (gstride[0] % 16 || gstride[1] % 16) return false;
+  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, t, 3, const_cast<void*>(base), gdim, gstride, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------ weights
+int radius_of(double sigma, double truncate) {
+  return (int)std::floor(truncate * sigma + 0.5);
+}
+
+// FP64 taps of the sampled Gaussian (order 0) and its analytic derivatives
+// (orders 1, 2), normalised by the sum of the order-0 samples.
+void taps1d_f64(double sigma, int r, int order, double* w) {
+  const double s2 = sigma * sigma;
+  double norm = 0.0;
+  for (int k = -r; k <= r; ++k) norm += std::exp(-0.5 * (double)k * (double)k / s2);
+  for (int k = -r; k <= r; ++k) {
+    const double g = std::exp(-0.5 * (double)k * (double)k / s2) / norm;
+    const double kk = (double)k;
+    double v = g;
+    if (order == 1) v = -kk / s2 * g;
+    if (order == 2) v = (kk * kk / (s2 * s2) - 1.0 / s2) * g;
+    w[k + r] = v;
+  }
+}
+
+void make_taps(double sigma, double truncate, const int order[3], Taps* t) {
+  const int r = radius_of(sigma, truncate);
+  t->r = r;
+  if (r < 0 || r > kMaxRGeneric) return;  // rejected by the caller
+  std::vector<double> w(2 * r + 1);
+  for (int a = 0; a < 3; ++a) {
+    for (int k = 0; k < kMaxTaps; ++k) t->w[a][k] = 0.0f;
+    taps1d_f64(sigma, r, order[a], w.data());
+    for (int k = 0; k <= 2 * r; ++k) t->w[a][k] = (float)w[k];
+  }
+}
+
+// ------------------------------------------------------------ planner
+static void reflect_hull(int64_t a, int64_t b, int64_t n, int64_t* lo, int64_t* hi) {
+  // hull of {R(c) : c in [a, b)}
+  if (b - a >= 2 * n) {
+    *lo = 0;
+    *hi = n;
+    return;
+  }
+  if (a >= 0 && b <= n) {
+    *lo = a;
+    *hi = b;
+    return;
+  }
+  int64_t mn = n, mx = -1;
+  for (int64_t c = a; c < b; ++c) {
+    int64_t s = reflect(c, n);
+    mn = std::min(mn, s);
+    mx = std::max(mx, s);
+  }
+  *lo = mn;
+  *hi = mx + 1;
+}
+
+struct Brick {
+  hp_box core;
+  hp_box in;
+};
+
+static size_t stage_bytes(const int64_t ext[3], const int64_t n[3], int halo, size_t in_b,
+                          size_t out_b) {
+  size_t inv = 1, outv = 1;
+  for (int a = 0; a < 3; ++a) {
+    int64_t e = std::min<int64_t>(ext[a] + 2 * (int64_t)halo + (a == 2 ? 32 : 0), n[a]);
+    inv *= (size_t)e;
+    outv *= (size_t)ext[a];
+  }
+  return inv * in_b + outv * out_b;
+}
+
+// Plan bricks; returns HP_OK or HP_ERR_BUDGET / HP_ERR_INVALID_ARG.
+static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t budget, int stages,
+                int min_bricks, std::vector<Brick>* out) {
+  if (n[0] < 1 || n[1] < 1 || n[2] < 1 || halo < 0 || stages < 1)
+    return set_error(HP_ERR_INVALID_ARG, "plan: bad extents, halo or stages");
+  const size_t per = budget / (size_t)stages;
+  int64_t ext[3] = {n[0], n[1], n[2]};
+  // Prefer Z slabs (contiguous planes); split y, then x, only when one
+  // plane plus halos does not fit.
+  int axis_split = -1;
+  for (int a = 0; a < 3 && axis_split < 0; ++a) {
+    for (int b = 0; b < a; ++b) ext[b] = 1;
+    for (int b = a; b < 3; ++b) ext[b] = n[b];
+    ext[a] = 1;
+    if (stage_bytes(ext, n, halo, in_b, out_b) > per) continue;
+    // largest extent along a that fits
+    int64_t lo = 1, hi = n[a];
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) / 2;
+      ext[a] = mid;
+      if (stage_bytes(ext, n, halo, in_b, out_b) <= per) lo = mid;
+      else hi = mid - 1;
+    }
+    ext[a] = lo;
+    axis_split = a;
+  }
+  if (axis_split < 0)
+    return set_error(HP_ERR_BUDGET, "budget too small for the smallest brick (" +
+                                        std::to_string(budget) + " bytes, " +
+                                        std::to_string(stages) + " stages)");
+  // at least min_bricks bricks along the split axis (for pipelining) when
+  // the volume allows it; then balance the brick lengths
+  const int a = axis_split;
+  int64_t nb = (n[a] + ext[a] - 1) / ext[a];
+  if (a == 0 && nb < min_bricks) nb = std::min<int64_t>(min_bricks, n[a]);
+  int64_t len = (n[a] + nb - 1) / nb;
+  if (a == 2) len = std::max<int64_t>(16, len / 16 * 16);  // 16-aligned x cores (TMA)
+  ext[a] = std::min<int64_t>(len, n[a]);
+  out->clear();
+  for (int64_t z0 = 0; z0 < n[0]; z0 += ext[0])
+    for (int64_t y0 = 0; y0 < n[1]; y0 += ext[1])
+      for (int64_t x0 = 0; x0 < n[2]; x0 += ext[2]) {
+        Brick b;
+        const int64_t lo[3] = {z0, y0, x0};
+        for (int k = 0; k < 3; ++k) {
+          b.core.lo[k] = lo[k];
+          b.core.hi[k] = std::min(lo[k] + ext[k], n[k]);
+          reflect_hull(b.core.lo[k] - halo, b.core.hi[k] + halo, n[k], &b.in.lo[k], &b.in.hi[k]);
+        }
+        if (ext[2] < n[2]) {  // align the x origin of the input box to 16 elements
+          b.in.lo[2] = b.in.lo[2] / 16 * 16;
+        }
+        out->push_back(b);
+      }
+  return HP_OK;
+}
+
+// ------------------------------------------------------------ executor
+struct Op {
+  int halo;
+  int out_dtype;
+  // enqueue the op for one job
+  std::function<cudaError_t(const Job&, cudaStream_t)> launch;
+};
+
+static bool is_pinned(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+static void host_copy_box(void* dst, const void* src, size_t es, const int64_t src_dims[3],
+                          const int64_t src_lo[3], const int64_t dst_dims[3],
+                          const int64_t dst_lo[3], const int64_t box_lo[3],
+                          const int64_t box_hi[3]) {
+  // copy box [box_lo, box_hi) (global coords) between two dense boxes,
+  // row by row, on several host threads
+  const int64_t nzb = box_hi[0] - box_lo[0], nyb = box_hi[1] - box_lo[1],
+                nxb = box_hi[2] - box_lo[2];
+  const int64_t rows = nzb * nyb;
+  const unsigned nt = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
+  auto work = [&](unsigned t) {
+    for (int64_t r = t; r < rows; r += nt) {
+      const int64_t z = box_lo[0] + r / nyb, y = box_lo[1] + r % nyb;
+      const char* s = (const char*)src +
+                      (((z - src_lo[0]) * src_dims[1] + (y - src_lo[1])) * src_dims[2] +
+                       (box_lo[2] - src_lo[2])) * es;
+      char* d = (char*)dst + (((z - dst_lo[0]) * dst_dims[1] + (y - dst_lo[1])) * dst_dims[2] +
+                              (box_lo[2] - dst_lo[2])) * es;
+      memcpy(d, s, (size_t)nxb * es);
+    }
+  };
+  if (rows * nxb * (int64_t)es < (8 << 20) || nt == 1) {
+    work(0);
+    for (unsigned t = 1; t < nt; ++t) work(t);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) th.emplace_back(work, t);
+  for (auto& x : th) x.join();
+}
+
+// cudaMemcpy3DAsync of box [lo, hi) between a dense host box and a dense
+// device box (both described in global coordinates).
+static cudaError_t copy_box_async(void* dst, const int64_t dst_dims[3], const int64_t dst_lo[3],
+                                  const void* src, const int64_t src_dims[3],
+                                  const int64_t src_lo[3], const int64_t lo[3], const int64_t hi[3],
+                                  size_t es, cudaMemcpyKind kind, cudaStream_t s) {
+  const bool full_rows = lo[2] == src_lo[2] && hi[2] == src_lo[2] + src_dims[2] &&
+                         lo[2] == dst_lo[2] && hi[2] == dst_lo[2] + dst_dims[2];
+  const bool full_planes = full_rows && lo[1] == src_lo[1] && hi[1] == src_lo[1] + src_dims[1] &&
+                           lo[1] == dst_lo[1] && hi[1] == dst_lo[1] + dst_dims[1];
+  if (full_planes) {
+    const size_t plane = (size_t)src_dims[1] * src_dims[2] * es;
+    const char* sp = (const char*)src + (size_t)(lo[0] - src_lo[0]) * plane;
+    char* dp = (char*)dst + (size_t)(lo[0] - dst_lo[0]) * plane;
+    return cudaMemcpyAsync(dp, sp, (size_t)(hi[0] - lo[0]) * plane, kind, s);
+  }
+  cudaMemcpy3DParms p;
+  memset(&p, 0, sizeof(p));
+  p.srcPtr = make_cudaPitchedPtr(const_cast<void*>(src), (size_t)src_dims[2] * es, (size_t)src_dims[2],
+                                 (size_t)src_dims[1]);
+  p.dstPtr = make_cudaPitchedPtr(dst, (size_t)dst_dims[2] * es, (size_t)dst_dims[2], (size_t)dst_dims[1]);
+  p.srcPos = make_cudaPos((size_t)(lo[2] - src_lo[2]) * es, (size_t)(lo[1] - src_lo[1]),
+                          (size_t)(lo[0] - src_lo[0]));
+  p.dstPos = make_cudaPos((size_t)(lo[2] - dst_lo[2]) * es, (size_t)(lo[1] - dst_lo[1]),
+                          (size_t)(lo[0] - dst_lo[0]));
+  p.extent = make_cudaExtent((size_t)(hi[2] - lo[2]) * es, (size_t)(hi[1] - lo[1]),
+                             (size_t)(hi[0] - lo[0]));
+  p.kind = kind;
+  return cudaMemcpy3DAsync(&p, s);
+}
+
+// Fault injection on the host (HP_FAULT=alloc:N | memcpy:N | budget): the
+// N-th library allocation / copy of a call reports failure. Used by tests.
+struct Faults {
+  int alloc_at = -1, memcpy_at = -1;
+  bool budget = false;
+  int allocs = 0, copies = 0;
+  Faults() {
+    const char* e = getenv("HP_FAULT");
+    if (!e) return;
+    if (!strncmp(e, "alloc:", 6)) alloc_at = atoi(e + 6);
+    else if (!strncmp(e, "memcpy:", 7)) memcpy_at = atoi(e + 7);
+    else if (!strcmp(e, "budget")) budget = true;
+  }
+  bool fail_alloc() { return alloc_at >= 0 && allocs++ == alloc_at; }
+  bool fail_copy() { return memcpy_at >= 0 && copies++ == memcpy_at; }
+};
+
+static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
+  auto t0 = std::chrono::steady_clock::now();
+  Faults faults;
+  const int64_t n[3] = {in->nz, in->ny, in->nx};
+  const size_t ies = dtype_size(in->dtype), oes = dtype_size(op.out_dtype);
+  size_t budget = 0;
+  int st = effective_budget(&budget);
+  if (st != HP_OK) return st;
+  if (faults.budget) budget = 1;
+  const int S = 3;
+  std::vector<Brick> bricks;
+  st = plan(n, op.halo, ies, oes, budget, S, 8, &bricks);
+  if (st != HP_OK) return st;
+
+  size_t max_in = 0, max_out = 0;
+  for (auto& b : bricks) {
+    size_t vi = ies, vo = oes;
+    for (int a = 0; a < 3; ++a) {
+      vi *= (size_t)(b.in.hi[a] - b.in.lo[a]);
+      vo *= (size_t)(b.core.hi[a] - b.core.lo[a]);
+    }
+    max_in = std::max(max_in, vi);
+    max_out = std::max(max_out, vo);
+  }
+  const int nst = (int)std::min<size_t>(S, bricks.size());
+  const bool in_pinned = is_pinned(in->data), out_pinned = is_pinned(out->data);
+
+  struct Stage {
+    void* din = nullptr;
+    void* dout = nullptr;
+    void* hin = nullptr;
+    void* hout = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    int brick = -1;
+  };
+  std::vector<Stage> sg(nst);
+  uint64_t h2d = 0, d2h = 0;
+  size_t pinned = 0;
+  int rc = HP_OK;
+  int64_t dev_bytes = 0;
+  auto fail = [&](int code, const std::string& m) {
+    if (rc == HP_OK) rc = set_error(code, m);
+  };
+  auto cfail = [&](cudaError_t e, const char* what) {
+    if (rc == HP_OK) rc = cuda_fail(e, what);
+  };
+  for (auto& x : sg) {
+    if (rc != HP_OK) break;
+    cudaError_t e;
+    if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
+    if ((e = cudaMalloc(&x.din, max_in)) != cudaSuccess) { cfail(e, "cudaMalloc(in stage)"); break; }
+    dev_bytes += (int64_t)max_in;
+    track_alloc((int64_t)max_in);
+    if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
+    if ((e = cudaMalloc(&x.dout, max_out)) != cudaSuccess) { cfail(e, "cudaMalloc(out stage)"); break; }
+    dev_bytes += (int64_t)max_out;
+    track_alloc((int64_t)max_out);
+    if (!in_pinned) {
+      if ((e = cudaHostAlloc(&x.hin, max_in, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); break; }
+      pinned += max_in;
+    }
+    if (!out_pinned) {
+      if ((e = cudaHostAlloc(&x.hout, max_out, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); break; }
+      pinned += max_out;
+    }
+    if ((e = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking)) != cudaSuccess) { cfail(e, "cudaStreamCreate"); break; }
+    if ((e = cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming)) != cudaSuccess) { cfail(e, "cudaEventCreate"); break; }
+  }
+
+  const int64_t vol_lo[3] = {0, 0, 0};
+  // completes brick b of stage x: copy its staged output to the user array
+  auto retire = [&](Stage& x) {
+    if (x.brick < 0) return;
+    cudaError_t e = cudaEventSynchronize(x.ev);
+    if (e != cudaSuccess) cfail(e, "brick execution");
+    if (rc == HP_OK && !out_pinned) {
+      const Brick& b = bricks[x.brick];
+      const int64_t cd[3] = {b.core.hi[0] - b.core.lo[0], b.core.hi[1] - b.core.lo[1],
+                             b.core.hi[2] - b.core.lo[2]};
+      host_copy_box(out->data, x.hout, oes, cd, b.core.lo, n, vol_lo, b.core.lo, b.core.hi);
+    }
+    x.brick = -1;
+  };
+
+  for (size_t i = 0; i < bricks.size() && rc == HP_OK; ++i) {
+    Stage& x = sg[i % nst];
+    retire(x);
+    if (rc != HP_OK) break;
+    const Brick& b = bricks[i];
+    const int64_t idims[3] = {b.in.hi[0] - b.in.lo[0], b.in.hi[1] - b.in.lo[1], b.in.hi[2] - b.in.lo[2]};
+    const int64_t cdims[3] = {b.core.hi[0] - b.core.lo[0], b.core.hi[1] - b.core.lo[1],
+                              b.core.hi[2] - b.core.lo[2]};
+    cudaError_t e;
+    if (faults.fail_copy()) { fail(HP_ERR_CUDA, "injected memcpy failure"); break; }
+    if (in_pinned) {
+      e = copy_box_async(x.din, idims, b.in.lo, in->data, n, vol_lo, b.in.lo, b.in.hi, ies,
+                         cudaMemcpyHostToDevice, x.s);
+    } else {
+      host_copy_box(x.hin, in->data, ies, n, vol_lo, idims, b.in.lo, b.in.lo, b.in.hi);
+      size_t bytes = ies * idims[0] * idims[1] * idims[2];
+      e = cudaMemcpyAsync(x.din, x.hin, bytes, cudaMemcpyHostToDevice, x.s);
+    }
+    if (e != cudaSuccess) { cfail(e, "H2D copy"); break; }
+    h2d += ies * (uint64_t)(idims[0] * idims[1] * idims[2]);
+    Job job;
+    job.in = DevBox{x.din, in->dtype, {b.in.lo[0], b.in.lo[1], b.in.lo[2]}, {idims[0], idims[1], idims[2]}};
+    job.out = DevOut{x.dout, op.out_dtype, {b.core.lo[0], b.core.lo[1], b.core.lo[2]}, {cdims[0], cdims[1], cdims[2]}};
+    for (int a = 0; a < 3; ++a) {
+      job.gdims[a] = n[a];
+      job.core_lo[a] = b.core.lo[a];
+      job.core_hi[a] = b.core.hi[a];
+    }
+    if ((e = op.launch(job, x.s)) != cudaSuccess) { cfail(e, "kernel launch"); break; }
+    if (faults.fail_copy()) { fail(HP_ERR_CUDA, "injected memcpy failure"); break; }
+    if (out_pinned) {
+      e = copy_box_async(out->data, n, vol_lo, x.dout, cdims, b.core.lo, b.core.lo, b.core.hi, oes,
+                         cudaMemcpyDeviceToHost, x.s);
+    } else {
+      e = cudaMemcpyAsync(x.hout, x.dout, oes * cdims[0] * cdims[1] * cdims[2],
+                          cudaMemcpyDeviceToHost, x.s);
+    }
+    if (e != cudaSuccess) { cfail(e, "D2H copy"); break; }
+    d2h += oes * (uint64_t)(cdims[0] * cdims[1] * cdims[2]);
+    if ((e = cudaEventRecord(x.ev, x.s)) != cudaSuccess) { cfail(e, "cudaEventRecord"); break; }
+    x.brick = (int)i;
+  }
+  for (auto& x : sg) {
+    if (rc == HP_OK) retire(x);
+    else if (x.s) cudaStreamSynchronize(x.s);
+  }
+  // kernels whose bounded waits gave up leave a mark in the error word
+  if (rc == HP_OK) {
+    int* ew = device_error_word();
+    int hv = 0;
+    if (ew && cudaMemcpy(&hv, ew, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && hv) {
+      cudaMemset(ew, 0, sizeof(int));
+      rc = set_error(HP_ERR_TIMEOUT, "a device-side wait gave up");
+    }
+  }
+  for (auto& x : sg) {
+    if (x.ev) cudaEventDestroy(x.ev);
+    if (x.s) cudaStreamDestroy(x.s);
+    if (x.din) { cudaFree(x.din); track_free((int64_t)max_in); }
+    if (x.dout) { cudaFree(x.dout); track_free((int64_t)max_out); }
+    if (x.hin) cudaFreeHost(x.hin);
+    if (x.hout) cudaFreeHost(x.hout);
+  }
+  cudaError_t le = cudaGetLastError();
+  if (rc == HP_OK && le != cudaSuccess) rc = cuda_fail(le, "executor");
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_stats.budget_bytes = budget;
+    g_stats.bricks = bricks.size();
+    g_stats.h2d_bytes = h2d;
+    g_stats.d2h_bytes = d2h;
+    g_stats.pinned_host_bytes = pinned;
+    g_stats.wall_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  (void)dev_bytes;
+  return rc;
+}
+
+static Job whole_job(const hp_volume* in, hp_volume* out, int out_dtype) {
+  Job j;
+  const int64_t n[3] = {in->nz, in->ny, in->nx};
+  j.in = DevBox{in->data, in->dtype, {0, 0, 0}, {n[0], n[1], n[2]}};
+  j.out = DevOut{out->data, out_dtype, {0, 0, 0}, {n[0], n[1], n[2]}};
+  for (int a = 0; a < 3; ++a) {
+    j.gdims[a] = n[a];
+    j.core_lo[a] = 0;
+    j.core_hi[a] = n[a];
+  }
+  return j;
+}
+
+static int check_pair(const hp_volume* in, const hp_volume* out) {
+  if (!in || !out) return set_error(HP_ERR_INVALID_ARG, "null volume");
+  if (!in->data || !out->data) return set_error(HP_ERR_INVALID_ARG, "null data pointer");
+  if (in->nx != out->nx || in->ny != out->ny || in->nz != out->nz)
+    return set_error(HP_ERR_INVALID_ARG, "input and output extents differ");
+  if (in->loc != out->loc) return set_error(HP_ERR_UNSUPPORTED, "mixed host/device locations");
+  const char* a = (const char*)in->data;
+  const char* b = (const char*)out->data;
+  const size_t na = dtype_size(in->dtype) * (size_t)(in->nx * in->ny * in->nz);
+  const size_t nb = dtype_size(out->dtype) * (size_t)(out->nx * out->ny * out->nz);
+  if (a < b + nb && b < a + na) return set_error(HP_ERR_INVALID_ARG, "input and output alias");
+  return HP_OK;
+}
+
+static void begin_call() {
+  g_peak.store(g_live.load());
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_stats.bricks = 0;
+  g_stats.h2d_bytes = g_stats.d2h_bytes = 0;
+  g_stats.pinned_host_bytes = 0;
+  g_stats.wall_ms = 0;
+}
+
+static int run(const Op& op, const hp_volume* in, hp_volume* out, void* stream) {
+  begin_call();
+  if (in->loc == HP_HOST) return run_host(op, in, out);
+  Job j = whole_job(in, out, op.out_dtype);
+  cudaError_t e = op.launch(j, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_stats.bricks = 1;
+  return HP_OK;
+}
+
+}  // namespace hp
+
+using namespace hp;
+
+// ===================================================================== ABI
+extern "C" {
+
+const char* hp_last_error(void) { return t_msg.c_str(); }
+const char* hp_version(void) { return "hp 0.1 (sm_103a)"; }
+
+int hp_volume_create(hp_volume** out, void* data, hp_dtype dtype, hp_loc loc, int64_t nx,
+                     int64_t ny, int64_t nz) {
+  if (!out) return set_error(HP_ERR_INVALID_ARG, "null output handle");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return set_error(HP_ERR_INVALID_ARG, "extents must be >= 1");
+  if (dtype_size(dtype) == 0) return set_error(HP_ERR_INVALID_ARG, "unknown dtype");
+  if (loc != HP_HOST && loc != HP_DEVICE) return set_error(HP_ERR_INVALID_ARG, "unknown location");
+  hp_volume* v = new (std::nothrow) hp_volume;
+  if (!v) return set_error(HP_ERR_OOM, "out of host memory");
+  *v = hp_volume{data, (int)dtype, (int)loc, nx, ny, nz};
+  *out = v;
+  return HP_OK;
+}
+
+int hp_volume_destroy(hp_volume* v) {
+  delete v;
+  return HP_OK;
+}
+
+int hp_set_memory_budget(size_t bytes) {
+  budget_setting();
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_budget = bytes;
+  return HP_OK;
+}
+
+int hp_get_memory_budget(size_t* bytes) {
+  if (!bytes) return set_error(HP_ERR_INVALID_ARG, "null pointer");
+  *bytes = budget_setting();
+  return HP_OK;
+}
+
+int hp_gaussian3d(const hp_volume* in, hp_volume* out, double sigma, double truncate,
+                  const int order[3], void* stream) {
+  int st = check_pair(in, out);
+  if (st != HP_OK) return st;
+  if (!(sigma > 0) || !std::isfinite(sigma)) return set_error(HP_ERR_INVALID_ARG, "sigma must be > 0");
+  if (truncate <= 0) truncate = 3.0;
+  int ord[3] = {0, 0, 0};
+  if (order)
+    for (int a = 0; a < 3; ++a) {
+      if (order[a] < 0 || order[a] > 2) return set_error(HP_ERR_INVALID_ARG, "order must be 0, 1 or 2");
+      ord[a] = order[a];
+    }
+  if (out->dtype != HP_F32 && out->dtype != HP_F16)
+    return set_error(HP_ERR_UNSUPPORTED, "Gaussian output dtype must be f32 or f16");
+  auto taps = std::make_shared<Taps>();
+  make_taps(sigma, truncate, ord, taps.get());
+  if (taps->r > kMaxRGeneric)
+    return set_error(HP_ERR_UNSUPPORTED, "radius " + std::to_string(taps->r) + " exceeds 32");
+  Op op;
+  op.halo = taps->r;
+  op.out_dtype = out->dtype;
+  op.launch = [taps](const Job& j, cudaStream_t s) { return launch_gauss(j, *taps, s); };
+  return run(op, in, out, stream);
+}
+
+static int morph(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream,
+                 int dil) {
+  int st = check_pair(in, out);
+  if (st != HP_OK) return st;
+  if (in->dtype != out->dtype) return set_error(HP_ERR_UNSUPPORTED, "morphology output dtype must equal input dtype");
+  if (se != HP_SE_CUBE && se != HP_SE_BALL) return set_error(HP_ERR_INVALID_ARG, "unknown structuring element");
+  if (radius < 0 || radius > kMaxMorphR) return set_error(HP_ERR_INVALID_ARG, "radius must be in [0, 16]");
+  Op op;
+  op.halo = radius;
+  op.out_dtype = out->dtype;
+  op.launch = [se, radius, dil](const Job& j, cudaStream_t s) {
+    return launch_morph(j, (int)se, radius, dil, s);
+  };
+  return run(op, in, out, stream);
+}
+
+int hp_erode3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream) {
+  return morph(in, out, se, radius, stream, 0);
+}
+
+int hp_dilate3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream) {
+  return morph(in, out, se, radius, stream, 1);
+}
+
+int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream) {
+  int st = check_pair(in, out);
+  if (st != HP_OK) return st;
+  if (out->dtype != HP_U8) return set_error(HP_ERR_UNSUPPORTED, "threshold output dtype must be u8");
+  Op op;
+  op.halo = 0;
+  op.out_dtype = HP_U8;
+  op.launch = [t](const Job& j, cudaStream_t s) { return launch_threshold(j, t, s); };
+  return run(op, in, out, stream);
+}
+
+int hp_plan_bricks(int64_t nx, int64_t ny, int64_t nz, int halo, size_t in_bytes,
+                   size_t out_bytes, size_t budget, int stages, int min_bricks, hp_box* cores,
+                   hp_box* in_boxes, int max_bricks, int* nbricks) {
+  if (!nbricks) return set_error(HP_ERR_INVALID_ARG, "null nbricks");
+  const int64_t n[3] = {nz, ny, nx};
+  std::vector<Brick> b;
+  int st = plan(n, halo, in_bytes, out_bytes, budget, stages, min_bricks, &b);
+  if (st != HP_OK) return st;
+  *nbricks = (int)b.size();
+  for (int i = 0; i < (int)b.size() && i < max_bricks; ++i) {
+    if (cores) cores[i] = b[i].core;
+    if (in_boxes) in_boxes[i] = b[i].in;
+  }
+  return HP_OK;
+}
+
+int hp_stream_status(void* stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int* ew = device_error_word();
+  if (!ew) return set_error(HP_ERR_CUDA, "no device error word");
+  int hv = 0;
+  e = cudaMemcpy(&hv, ew, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read device error word");
+  if (hv) {
+    cudaMemset(ew, 0, sizeof(int));
+    return set_error(HP_ERR_TIMEOUT, "a device-side wait gave up");
+  }
+  return HP_OK;
+}
+
+int hp_get_stats(hp_stats* s) {
+  if (!s) return set_error(HP_ERR_INVALID_ARG, "null pointer");
+  std::lock_guard<std::mutex> lk(g_mu);
+  *s = g_stats;
+  s->live_device_bytes = (size_t)std::max<int64_t>(0, g_live.load());
+  s->peak_device_bytes = (size_t)std::max<int64_t>(0, g_peak.load());
+  s->cached_device_bytes = (size_t)std::max<int64_t>(0, g_cached.load());
+  return HP_OK;
+}
+
+}  // extern "C"

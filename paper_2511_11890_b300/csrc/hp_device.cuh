@@ -1,0 +1,124 @@
+// Device helpers for libhp kernels (sm_103a): mbarriers with bounded waits,
+// TMA tile loads, element conversion.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+// Poll limit of a bounded mbarrier wait. try_wait suspends the thread for a
+// hardware-defined interval per attempt, so this bounds the wait to well
+// under a second on a healthy GPU while never spinning forever.
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+// Error word codes (OR-ed together).
+constexpr int kErrTimeout = 1;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; returns false if the phase did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 3D TMA tile load (x, y, z coordinates, x innermost) into shared memory,
+// completing on `bar` with the transferred byte count.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Element -> float. uint16 uses the exact 2^23 bias trick (one LOP + one
+// FADD instead of an integer-to-float conversion).
+template <typename T>
+__device__ __forceinline__ float to_f32(T v);
+template <>
+__device__ __forceinline__ float to_f32<uint8_t>(uint8_t v) {
+  return __int_as_float(0x4B000000 | (uint32_t)v) - 8388608.0f;
+}
+template <>
+__device__ __forceinline__ float to_f32<uint16_t>(uint16_t v) {
+  return __int_as_float(0x4B000000 | (uint32_t)v) - 8388608.0f;
+}
+template <>
+__device__ __forceinline__ float to_f32<__half>(__half v) {
+  return __half2float(v);
+}
+template <>
+__device__ __forceinline__ float to_f32<float>(float v) {
+  return v;
+}
+
+template <typename T>
+struct DtypeOf;
+template <>
+struct DtypeOf<uint8_t> {
+  static constexpr int value = HP_U8;
+};
+template <>
+struct DtypeOf<uint16_t> {
+  static constexpr int value = HP_U16;
+};
+template <>
+struct DtypeOf<__half> {
+  static constexpr int value = HP_F16;
+};
+template <>
+struct DtypeOf<float> {
+  static constexpr int value = HP_F32;
+};
+
+__device__ __forceinline__ void set_device_error(int* err, int code) {
+  if (err) atomicOr(err, code);
+}
+
+}  // namespace hp

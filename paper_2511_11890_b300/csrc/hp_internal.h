@@ -1,0 +1,101 @@
+// Internal declarations shared by the C ABI layer, the planner, the
+// executor and the kernel launchers of libhp.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hp.h"
+
+namespace hp {
+
+constexpr int kMaxR = 12;        // largest radius with a tiled z-march kernel
+constexpr int kMaxRGeneric = 32; // largest radius overall (generic kernel)
+constexpr int kMaxTaps = 2 * kMaxRGeneric + 1;
+constexpr int kMaxMorphR = 16;
+
+// Reflect (half-sample symmetric) index, valid for any i and n >= 1. The
+// in-range and single-fold cases avoid the 64-bit remainder.
+__host__ __device__ inline int64_t reflect(int64_t i, int64_t n) {
+  if (i >= 0 && i < n) return i;
+  if (i < 0 && i >= -n) return -1 - i;
+  if (i >= n && i < 2 * n) return 2 * n - 1 - i;
+  int64_t p = 2 * n;
+  int64_t m = i % p;
+  if (m < 0) m += p;
+  return m < n ? m : p - 1 - m;
+}
+
+inline size_t dtype_size(int dt) {
+  switch (dt) {
+    case HP_U8: return 1;
+    case HP_U16: case HP_F16: return 2;
+    case HP_F32: return 4;
+    default: return 0;
+  }
+}
+
+// A dense box of a global volume held in device memory: element (z, y, x)
+// of the global volume lives at ptr[((z-lo0)*d1 + (y-lo1))*d2 + (x-lo2)].
+struct DevBox {
+  const void* ptr;
+  int dtype;
+  int64_t lo[3];
+  int64_t dims[3];
+};
+
+struct DevOut {
+  void* ptr;
+  int dtype;
+  int64_t lo[3];
+  int64_t dims[3];
+};
+
+// One filtering job over a core box of the global volume.
+struct Job {
+  DevBox in;
+  DevOut out;
+  int64_t gdims[3];
+  int64_t core_lo[3];
+  int64_t core_hi[3];
+};
+
+// FP32 taps per axis (z, y, x), index k + r for k in [-r, r].
+struct Taps {
+  int r;
+  float w[3][kMaxTaps];
+};
+
+// Kernel-weight generation (FP64, rounded once to FP32).
+int radius_of(double sigma, double truncate);
+void make_taps(double sigma, double truncate, const int order[3], Taps* t);
+void taps1d_f64(double sigma, int r, int order, double* w);
+
+// Device-side error word (per device), set by bounded waits that give up.
+int* device_error_word();
+
+// Launchers (enqueue only). Return a cudaError_t.
+cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s);
+cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
+cudaError_t launch_threshold(const Job& job, double t, cudaStream_t s);
+
+// Error reporting (thread-local message).
+int set_error(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// TMA tensor map over a dense 3D box (x, y, z extents), box (bw, bh, 1).
+// Returns false when the layout does not meet TMA rules.
+bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t dims[3], int bw,
+                  int bh);
+
+int num_sms();
+
+// HP_LOG >= 1 prints the kernel path chosen for each launch to stderr.
+int log_level();
+
+}  // namespace hp

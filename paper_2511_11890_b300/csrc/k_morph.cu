@@ -1,0 +1,530 @@
+// Grayscale erosion / dilation (Harpia Sec. III-C, morphological label
+// editing) with cube and ball structuring elements, reflect boundaries on
+// global coordinates, exact results.
+//
+// Values are mapped to order-preserving unsigned keys (u8/u16 as is; f16/f32
+// sign-magnitude flipped), so min/max are integer operations and exact.
+// Dilation is erosion of the complemented keys (complement reverses order).
+//
+// Tiled z-march kernel (radius 1..6): a CTA owns a 32 x 32 column of the
+// core and marches along z. Per input plane it stages the halo-padded patch
+// (TMA tile load into a 4-stage mbarrier pipeline, or cooperative loads),
+// then
+//   x: running minima M_L over x-lines of half-length L = 0..r (for the
+//      cube only L = r is kept);
+//   y: the ball is the union of x-lines {|dx| <= L(dy,dz)}, with
+//      L(dy,dz) = floor(sqrt(r^2 - dy^2 - dz^2)), so each plane's disk
+//      minima D_|dz| = min over dy of M_L(dy,dz)(y + dy) (cube: D = min over
+//      |dy| <= r of M_r) are formed per thread from a register window;
+//   z: D_|dz| of plane z' is pushed into the accumulators of outputs
+//      z' -+ dz held in a register ring of 2r+1 slots; an output is complete
+//      r planes after its own plane and is stored then.
+// Min is associative and exact, so the result does not depend on tiling.
+#include <cuda_fp16.h>
+
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "hp_device.cuh"
+#include "hp_internal.h"
+
+namespace hp {
+
+namespace {
+
+constexpr int kTX = 32;
+constexpr int kTY = 32;
+constexpr int kYB = 4;
+constexpr int kNS = 4;
+constexpr int kThreads = 256;
+constexpr int kMaxTiledR = 6;
+
+struct MorphParams {
+  Job job;
+  int zchunk;
+  int tiles_x;
+  int use_tma;
+  int is_dilate;
+  int* err;
+};
+
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+__host__ __device__ constexpr int isqrt(int v) {
+  int s = 0;
+  while ((s + 1) * (s + 1) <= v) ++s;
+  return s;
+}
+// Odd row strides (in 32-bit words) spread the 8 rows x 4 column groups a
+// warp touches over all 32 banks.
+__host__ __device__ constexpr int key_stride(int n) { return n | 1; }
+constexpr int kMS = kTX + 1;  // row stride of the line-minimum arrays
+
+// Order-preserving keys.
+template <typename T>
+__device__ __forceinline__ uint32_t to_key(T v);
+template <>
+__device__ __forceinline__ uint32_t to_key<uint8_t>(uint8_t v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ uint32_t to_key<uint16_t>(uint16_t v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ uint32_t to_key<__half>(__half v) {
+  uint32_t b = __half_as_ushort(v);
+  return (b & 0x8000u) ? (~b & 0xFFFFu) : (b | 0x8000u);
+}
+template <>
+__device__ __forceinline__ uint32_t to_key<float>(float v) {
+  uint32_t b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+template <typename T>
+__device__ __forceinline__ T from_key(uint32_t k);
+template <>
+__device__ __forceinline__ uint8_t from_key<uint8_t>(uint32_t k) {
+  return (uint8_t)k;
+}
+template <>
+__device__ __forceinline__ uint16_t from_key<uint16_t>(uint32_t k) {
+  return (uint16_t)k;
+}
+template <>
+__device__ __forceinline__ __half from_key<__half>(uint32_t k) {
+  uint32_t b = (k & 0x8000u) ? (k & 0x7FFFu) : (~k & 0xFFFFu);
+  return __ushort_as_half((unsigned short)b);
+}
+template <>
+__device__ __forceinline__ float from_key<float>(uint32_t k) {
+  uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  return __uint_as_float(b);
+}
+// Keys of narrow types occupy the low bits; complementing within the type's
+// width keeps them comparable.
+template <typename T>
+struct KeyMask {
+  static constexpr uint32_t value = sizeof(T) == 4 ? 0xFFFFFFFFu : (sizeof(T) == 2 ? 0xFFFFu : 0xFFu);
+};
+
+template <int R, int BALL>
+struct MGeom {
+  static constexpr int BH = kTY + 2 * R;
+  static constexpr int KWN = kTX + 2 * R;
+  static constexpr int KW = key_stride(KWN);
+  static constexpr int NL = BALL ? R + 1 : 1;  // stored x-line minima
+  static constexpr int NR = 2 * R + 1;         // z accumulator ring
+  // stage buffers sized for the widest element (4 bytes)
+  static constexpr int STAGE_BYTES = round_up(round_up(kTX + round_up(R, 4) + R, 4) * BH * 4, 128);
+  static constexpr int OFF_STAGE = 128;
+  static constexpr int OFF_K = OFF_STAGE + kNS * STAGE_BYTES;
+  static constexpr int OFF_M = OFF_K + round_up(BH * KW * 4, 128);
+  static constexpr int SMEM = OFF_M + NL * BH * kMS * 4;
+};
+
+__host__ __device__ inline void mbox_geom(int r, int es, int* ra, int* bw) {
+  const int al = 16 / es;
+  *ra = round_up(r, al);
+  *bw = round_up(kTX + *ra + r, al);
+}
+
+template <typename TIN, int R, int BALL>
+__device__ __forceinline__ void keys_from_stage(uint32_t* K, const unsigned char* rawb, int ra,
+                                                int bw, bool face, int64_t cx0, int64_t cy0,
+                                                int64_t Gx, int64_t Gy, uint32_t flip, int warp,
+                                                int lane) {
+  using G = MGeom<R, BALL>;
+  const TIN* raw = reinterpret_cast<const TIN*>(rawb);
+  for (int row = warp; row < G::BH; row += kThreads / 32) {
+    int srow = row;
+    if (face) srow = (int)(reflect(cy0 - R + row, Gy) - (cy0 - R));
+    for (int col = lane; col < G::KWN; col += 32) {
+      int scol = col + (ra - R);
+      bool ok = true;
+      if (face) {
+        scol = (int)(reflect(cx0 - R + col, Gx) - (cx0 - ra));
+        ok = scol >= 0 && scol < bw && srow >= 0 && srow < G::BH;
+      }
+      K[row * G::KW + col] = ok ? (to_key<TIN>(raw[srow * bw + scol]) ^ flip) : 0u;
+    }
+  }
+}
+
+template <typename TIN, int R, int BALL>
+__device__ __forceinline__ void keys_from_global(uint32_t* K, const Job& J, int64_t iz,
+                                                 int64_t cx0, int64_t cy0, uint32_t flip,
+                                                 int warp, int lane) {
+  using G = MGeom<R, BALL>;
+  const TIN* in = static_cast<const TIN*>(J.in.ptr);
+  const int64_t sz = reflect(iz, J.gdims[0]) - J.in.lo[0];
+  for (int row = warp; row < G::BH; row += kThreads / 32) {
+    const int64_t sy = reflect(cy0 - R + row, J.gdims[1]) - J.in.lo[1];
+    for (int col = lane; col < G::KWN; col += 32) {
+      const int64_t sx = reflect(cx0 - R + col, J.gdims[2]) - J.in.lo[2];
+      uint32_t v = 0u;
+      if (sz >= 0 && sz < J.in.dims[0] && sy >= 0 && sy < J.in.dims[1] && sx >= 0 &&
+          sx < J.in.dims[2])
+        v = to_key<TIN>(in[(sz * J.in.dims[1] + sy) * J.in.dims[2] + sx]) ^ flip;
+      K[row * G::KW + col] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t key_mask(int dt) {
+  return dt == HP_F32 ? 0xFFFFFFFFu : (dt == HP_U8 ? 0xFFu : 0xFFFFu);
+}
+
+__device__ __forceinline__ void store_key(void* base, int dt, int64_t idx, uint32_t k) {
+  switch (dt) {
+    case HP_U8: static_cast<uint8_t*>(base)[idx] = from_key<uint8_t>(k); break;
+    case HP_U16: static_cast<uint16_t*>(base)[idx] = from_key<uint16_t>(k); break;
+    case HP_F16: static_cast<__half*>(base)[idx] = from_key<__half>(k); break;
+    default: static_cast<float*>(base)[idx] = from_key<float>(k); break;
+  }
+}
+
+// Push one plane's disk minima D[|dz|] into the z ring with the ring
+// rotation U (compile time, so the ring stays in registers), then hand out
+// the output that became complete and recycle its slot.
+template <int R, int BALL, int U>
+__device__ __forceinline__ void push_rot(uint32_t (&acc)[2 * R + 1][kYB],
+                                         const uint32_t (&D)[BALL ? R + 1 : 1][kYB],
+                                         uint32_t (&done)[kYB]) {
+  constexpr int NR = 2 * R + 1;
+#pragma unroll
+  for (int i = 0; i < kYB; ++i) {
+    if (BALL) {
+#pragma unroll
+      for (int dz = 0; dz <= R; ++dz) {
+        acc[(U + dz) % NR][i] = min(acc[(U + dz) % NR][i], D[BALL ? dz : 0][i]);
+        if (dz > 0) acc[(U - dz + NR) % NR][i] = min(acc[(U - dz + NR) % NR][i], D[BALL ? dz : 0][i]);
+      }
+    } else {
+#pragma unroll
+      for (int e = -R; e <= R; ++e) acc[(U + e + NR) % NR][i] = min(acc[(U + e + NR) % NR][i], D[0][i]);
+    }
+    constexpr int slot = (U - R + NR) % NR;
+    done[i] = acc[slot][i];
+    acc[slot][i] = 0xFFFFFFFFu;
+  }
+}
+
+template <int R, int BALL, int U = 0>
+__device__ __forceinline__ void push_dispatch(int u, uint32_t (&acc)[2 * R + 1][kYB],
+                                              const uint32_t (&D)[BALL ? R + 1 : 1][kYB],
+                                              uint32_t (&done)[kYB]) {
+  if constexpr (U < 2 * R + 1) {
+    if (u == U)
+      push_rot<R, BALL, U>(acc, D, done);
+    else
+      push_dispatch<R, BALL, U + 1>(u, acc, D, done);
+  }
+}
+
+template <int R, int BALL>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_morph_zm(const __grid_constant__ MorphParams P, const __grid_constant__ CUtensorMap tmap) {
+  using G = MGeom<R, BALL>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* K = reinterpret_cast<uint32_t*>(smem + G::OFF_K);
+  uint32_t* M = reinterpret_cast<uint32_t*>(smem + G::OFF_M);
+  __shared__ int s_abort;
+
+  const Job& J = P.job;
+  const int tid = threadIdx.x;
+  const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
+  const int64_t cx0 = J.core_lo[2] + (int64_t)tx * kTX;
+  const int64_t cy0 = J.core_lo[1] + (int64_t)ty * kTY;
+  const int64_t cz0 = J.core_lo[0] + (int64_t)blockIdx.y * P.zchunk;
+  const int64_t cz1 = min(cz0 + (int64_t)P.zchunk, J.core_hi[0]);
+  if (cz0 >= cz1) return;
+  const int nout = (int)(cz1 - cz0);
+  const int total = nout + 2 * R;
+  const int64_t Gz = J.gdims[0], Gy = J.gdims[1], Gx = J.gdims[2];
+  const int dt = J.in.dtype;
+  const int es = dt == HP_U8 ? 1 : (dt == HP_F32 ? 4 : 2);
+  int ra, bw;
+  mbox_geom(R, es, &ra, &bw);
+  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + kTY + R > Gy);
+  const bool tma = P.use_tma != 0;
+  const uint32_t flip = P.is_dilate ? key_mask(dt) : 0u;
+
+  if (tid == 0) {
+    s_abort = 0;
+    if (tma) {
+      prefetch_tmap(&tmap);
+      for (int s = 0; s < kNS; ++s) mbar_init(&bars[s], 1);
+      fence_mbar_init();
+    }
+  }
+  __syncthreads();
+
+  auto issue = [&](int n) {
+    const int64_t iz = cz0 - R + n;
+    const int zl = (int)(reflect(iz, Gz) - J.in.lo[0]);
+    const int xl = (int)(cx0 - ra - J.in.lo[2]);
+    const int yl = (int)(cy0 - R - J.in.lo[1]);
+    uint64_t* bar = &bars[n % kNS];
+    mbar_arrive_expect_tx(bar, bw * G::BH * es);
+    tma_load_3d(smem + G::OFF_STAGE + (n % kNS) * G::STAGE_BYTES, &tmap, xl, yl, zl, bar);
+  };
+  if (tma && tid == 0) {
+    fence_proxy_async();
+    for (int n = 0; n < min(kNS, total); ++n) issue(n);
+  }
+
+  const int xrow = tid / (kTX / 8), xg = (tid % (kTX / 8)) * 8;
+  const int yx = tid % kTX, yb = (tid / kTX) * kYB;
+  const int warp = tid / 32, lane = tid % 32;
+
+  uint32_t acc[G::NR][kYB];
+#pragma unroll
+  for (int s = 0; s < G::NR; ++s)
+#pragma unroll
+    for (int i = 0; i < kYB; ++i) acc[s][i] = 0xFFFFFFFFu;
+
+  int n = 0;
+  for (; n < total; ++n) {
+    const int64_t iz = cz0 - R + n;
+    // ---- stage keys K[BH][KW] (cols <-> x = cx0-R .. cx0+TX+R-1)
+    if (tma) {
+      if (!mbar_wait(&bars[n % kNS], (n / kNS) & 1)) atomicOr(&s_abort, 1);
+      const unsigned char* rawb = smem + G::OFF_STAGE + (n % kNS) * G::STAGE_BYTES;
+      switch (dt) {
+        case HP_U8: keys_from_stage<uint8_t, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
+        case HP_U16: keys_from_stage<uint16_t, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
+        case HP_F16: keys_from_stage<__half, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
+        default: keys_from_stage<float, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
+      }
+    } else {
+      switch (dt) {
+        case HP_U8: keys_from_global<uint8_t, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
+        case HP_U16: keys_from_global<uint16_t, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
+        case HP_F16: keys_from_global<__half, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
+        default: keys_from_global<float, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (tma && tid == 0 && n + kNS < total) {
+      fence_proxy_async();
+      issue(n + kNS);
+    }
+    // ---- x: line minima of half-length L
+    if (xrow < G::BH) {
+      uint32_t w[8 + 2 * R];
+#pragma unroll
+      for (int j = 0; j < 8 + 2 * R; ++j) w[j] = K[xrow * G::KW + xg + j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        uint32_t m = w[i + R];
+        if (BALL) M[(0 * G::BH + xrow) * kMS + xg + i] = m;
+#pragma unroll
+        for (int L = 1; L <= R; ++L) {
+          m = min(m, min(w[i + R - L], w[i + R + L]));
+          if (BALL) M[(L * G::BH + xrow) * kMS + xg + i] = m;
+        }
+        if (!BALL) M[xrow * kMS + xg + i] = m;
+      }
+    }
+    __syncthreads();
+    // ---- y: disk minima per |dz| (ball) or the square minimum (cube)
+    uint32_t D[BALL ? R + 1 : 1][kYB];
+#pragma unroll
+    for (int dz = 0; dz <= (BALL ? R : 0); ++dz) {
+      const int ym = BALL ? isqrt(R * R - dz * dz) : R;
+#pragma unroll
+      for (int i = 0; i < kYB; ++i) {
+        uint32_t d = 0xFFFFFFFFu;
+#pragma unroll
+        for (int dy = -ym; dy <= ym; ++dy) {
+          const int L = BALL ? isqrt(R * R - dz * dz - dy * dy) : 0;
+          d = min(d, M[(L * G::BH + yb + i + dy + R) * kMS + yx]);
+        }
+        D[dz][i] = d;
+      }
+    }
+    // ---- z: push into the ring; the output of plane iz - R is complete
+    uint32_t done[kYB];
+    push_dispatch<R, BALL>(n % G::NR, acc, D, done);
+    {
+      const int64_t gz = iz - R, gx = cx0 + yx;
+      if (gz >= cz0 && gz < cz1 && gx < J.core_hi[2]) {
+        const DevOut& O = J.out;
+#pragma unroll
+        for (int i = 0; i < kYB; ++i) {
+          const int64_t gy = cy0 + yb + i;
+          if (gy < J.core_hi[1]) {
+            const int64_t idx =
+                ((gz - O.lo[0]) * O.dims[1] + (gy - O.lo[1])) * O.dims[2] + (gx - O.lo[2]);
+            store_key(O.ptr, dt, idx, done[i] ^ flip);
+          }
+        }
+      }
+    }
+    __syncthreads();  // K and M are rewritten by the next plane
+  }
+  if (s_abort) {
+    set_device_error(P.err, kErrTimeout);
+    if (tma && tid == 0)
+      for (int m = n; m < min(n + kNS, total); ++m) (void)mbar_wait(&bars[m % kNS], (m / kNS) & 1);
+    __syncthreads();
+  }
+}
+
+// Generic brute force over the structuring element (any radius <= 16, any
+// extents): one thread per output voxel.
+template <typename TIN>
+__global__ void k_morph_generic(const Job J, int ball, int rad, int is_dilate) {
+  const int64_t n0 = J.core_hi[0] - J.core_lo[0], n1 = J.core_hi[1] - J.core_lo[1],
+                n2 = J.core_hi[2] - J.core_lo[2];
+  const int64_t total = n0 * n1 * n2;
+  const uint32_t flip = is_dilate ? KeyMask<TIN>::value : 0u;
+  const TIN* in = static_cast<const TIN*>(J.in.ptr);
+  const int sg = is_dilate ? -1 : 1;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = J.core_lo[2] + q % n2, y = J.core_lo[1] + (q / n2) % n1,
+                  z = J.core_lo[0] + q / (n1 * n2);
+    uint32_t m = 0xFFFFFFFFu;
+    for (int dz = -rad; dz <= rad; ++dz)
+      for (int dy = -rad; dy <= rad; ++dy)
+        for (int dx = -rad; dx <= rad; ++dx) {
+          if (ball && dz * dz + dy * dy + dx * dx > rad * rad) continue;
+          const int64_t sz = reflect(z + sg * dz, J.gdims[0]) - J.in.lo[0];
+          const int64_t sy = reflect(y + sg * dy, J.gdims[1]) - J.in.lo[1];
+          const int64_t sx = reflect(x + sg * dx, J.gdims[2]) - J.in.lo[2];
+          if (sz < 0 || sz >= J.in.dims[0] || sy < 0 || sy >= J.in.dims[1] || sx < 0 ||
+              sx >= J.in.dims[2])
+            continue;
+          m = min(m, to_key<TIN>(in[(sz * J.in.dims[1] + sy) * J.in.dims[2] + sx]) ^ flip);
+        }
+    const DevOut& O = J.out;
+    const int64_t idx = ((z - O.lo[0]) * O.dims[1] + (y - O.lo[1])) * O.dims[2] + (x - O.lo[2]);
+    static_cast<TIN*>(O.ptr)[idx] = from_key<TIN>(m ^ flip);
+  }
+}
+
+template <int R, int BALL>
+cudaError_t launch_mzm(const MorphParams& P, const CUtensorMap& map, dim3 grid, cudaStream_t s) {
+  using G = MGeom<R, BALL>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_morph_zm<R, BALL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_morph_zm<R, BALL><<<grid, kThreads, G::SMEM, s>>>(P, map);
+  return cudaGetLastError();
+}
+
+template <int BALL>
+cudaError_t dispatch_r(int r, const MorphParams& P, const CUtensorMap& map, dim3 grid,
+                       cudaStream_t s) {
+  switch (r) {
+    case 1: return launch_mzm<1, BALL>(P, map, grid, s);
+    case 2: return launch_mzm<2, BALL>(P, map, grid, s);
+    case 3: return launch_mzm<3, BALL>(P, map, grid, s);
+    case 4: return launch_mzm<4, BALL>(P, map, grid, s);
+    case 5: return launch_mzm<5, BALL>(P, map, grid, s);
+    case 6: return launch_mzm<6, BALL>(P, map, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s) {
+  const int64_t cx = job.core_hi[2] - job.core_lo[2];
+  const int64_t cy = job.core_hi[1] - job.core_lo[1];
+  const int64_t cz = job.core_hi[0] - job.core_lo[0];
+  if (cx <= 0 || cy <= 0 || cz <= 0) return cudaSuccess;
+  const int ball = se == HP_SE_BALL;
+  const bool tiled = rad >= 1 && rad <= kMaxTiledR && job.gdims[2] >= rad && job.gdims[1] >= rad;
+  if (!tiled) {
+    const int64_t total = cx * cy * cz;
+    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 32);
+    switch (job.in.dtype) {
+      case HP_U8: k_morph_generic<uint8_t><<<grid, 256, 0, s>>>(job, ball, rad, is_dilate); break;
+      case HP_U16: k_morph_generic<uint16_t><<<grid, 256, 0, s>>>(job, ball, rad, is_dilate); break;
+      case HP_F16: k_morph_generic<__half><<<grid, 256, 0, s>>>(job, ball, rad, is_dilate); break;
+      case HP_F32: k_morph_generic<float><<<grid, 256, 0, s>>>(job, ball, rad, is_dilate); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  MorphParams P;
+  P.job = job;
+  P.is_dilate = is_dilate;
+  P.err = device_error_word();
+  P.tiles_x = (int)((cx + kTX - 1) / kTX);
+  const int64_t tiles = (int64_t)P.tiles_x * ((cy + kTY - 1) / kTY);
+  const int64_t want = (int64_t)num_sms() * 8;
+  int64_t nchunks = std::max<int64_t>(1, (want + tiles - 1) / tiles);
+  int64_t zc = (cz + nchunks - 1) / nchunks;
+  zc = std::max<int64_t>(zc, std::min<int64_t>(cz, 32));
+  P.zchunk = (int)zc;
+  dim3 grid((unsigned)tiles, (unsigned)((cz + zc - 1) / zc));
+
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const size_t es = dtype_size(job.in.dtype);
+  const int al = 16 / (int)es;
+  bool use_tma = ((uintptr_t)job.in.ptr % 16 == 0) && ((job.in.dims[2] * (int64_t)es) % 16 == 0) &&
+                 ((job.core_lo[2] - job.in.lo[2]) % al == 0);
+  if (use_tma) {
+    int ra = 0, bw = 0;
+    mbox_geom(rad, (int)es, &ra, &bw);
+    const int64_t dims[3] = {job.in.dims[2], job.in.dims[1], job.in.dims[0]};
+    use_tma = make_tmap_3d(&map, job.in.ptr, job.in.dtype, dims, bw, kTY + 2 * rad);
+  }
+  P.use_tma = use_tma ? 1 : 0;
+  if (log_level() > 0)
+    fprintf(stderr, "[hp] morph z-march r=%d ball=%d tma=%d grid=%ux%u zchunk=%d\n", rad, ball,
+            P.use_tma, grid.x, grid.y, P.zchunk);
+  return ball ? dispatch_r<1>(rad, P, map, grid, s) : dispatch_r<0>(rad, P, map, grid, s);
+}
+
+// ------------------------------------------------------------ threshold
+namespace {
+template <typename TIN>
+__global__ void k_threshold(const Job J, float t) {
+  const int64_t n0 = J.core_hi[0] - J.core_lo[0], n1 = J.core_hi[1] - J.core_lo[1],
+                n2 = J.core_hi[2] - J.core_lo[2];
+  const int64_t total = n0 * n1 * n2;
+  const TIN* in = static_cast<const TIN*>(J.in.ptr);
+  uint8_t* out = static_cast<uint8_t*>(J.out.ptr);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = J.core_lo[2] + q % n2, y = J.core_lo[1] + (q / n2) % n1,
+                  z = J.core_lo[0] + q / (n1 * n2);
+    const int64_t qi = ((z - J.in.lo[0]) * J.in.dims[1] + (y - J.in.lo[1])) * J.in.dims[2] + (x - J.in.lo[2]);
+    const int64_t qo = ((z - J.out.lo[0]) * J.out.dims[1] + (y - J.out.lo[1])) * J.out.dims[2] + (x - J.out.lo[2]);
+    out[qo] = to_f32<TIN>(in[qi]) > t ? 1 : 0;
+  }
+}
+}  // namespace
+
+// out = in > t, compared in the input's own precision: integers and f32
+// compare exactly against the FP32 threshold; f16 inputs against t rounded
+// to f16.
+cudaError_t launch_threshold(const Job& job, double t, cudaStream_t s) {
+  const int64_t n = (job.core_hi[0] - job.core_lo[0]) * (job.core_hi[1] - job.core_lo[1]) *
+                    (job.core_hi[2] - job.core_lo[2]);
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 32);
+  switch (job.in.dtype) {
+    case HP_U8: k_threshold<uint8_t><<<grid, 256, 0, s>>>(job, (float)t); break;
+    case HP_U16: k_threshold<uint16_t><<<grid, 256, 0, s>>>(job, (float)t); break;
+    case HP_F16: k_threshold<__half><<<grid, 256, 0, s>>>(job, __half2float(__float2half_rn((float)t))); break;
+    case HP_F32: k_threshold<float><<<grid, 256, 0, s>>>(job, (float)t); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace hp

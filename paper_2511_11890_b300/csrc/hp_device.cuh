@@ -117,6 +117,53 @@ struct DtypeOf<float> {
   static constexpr int value = HP_F32;
 };
 
+// Packed FP32 pair arithmetic (Blackwell fma.rn.f32x2): one instruction,
+// two independent IEEE fmas, each rounded exactly like fmaf.
+__device__ __forceinline__ unsigned long long pack2(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long splat2(float g) { return pack2(make_float2(g, g)); }
+
+// Four consecutive elements -> float4 (vectorised staging of interior tiles).
+template <typename T>
+__device__ __forceinline__ float4 load4_f32(const T* p);
+template <>
+__device__ __forceinline__ float4 load4_f32<uint8_t>(const uint8_t* p) {
+  const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
+  return make_float4(to_f32<uint8_t>(v & 0xFF), to_f32<uint8_t>((v >> 8) & 0xFF),
+                     to_f32<uint8_t>((v >> 16) & 0xFF), to_f32<uint8_t>(v >> 24));
+}
+template <>
+__device__ __forceinline__ float4 load4_f32<uint16_t>(const uint16_t* p) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  return make_float4(to_f32<uint16_t>(v.x & 0xFFFF), to_f32<uint16_t>(v.x >> 16),
+                     to_f32<uint16_t>(v.y & 0xFFFF), to_f32<uint16_t>(v.y >> 16));
+}
+template <>
+__device__ __forceinline__ float4 load4_f32<__half>(const __half* p) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ float4 load4_f32<float>(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+
 __device__ __forceinline__ void set_device_error(int* err, int code) {
   if (err) atomicOr(err, code);
 }

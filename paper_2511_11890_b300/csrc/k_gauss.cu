@@ -63,81 +63,108 @@ __host__ __device__ constexpr int patch_stride(int n) {
   return f;
 }
 
-// Shared-memory layout of the z-march kernel for radius R. The TMA box
-// width depends on the element size (its x origin must be 16-byte aligned),
-// so the stage buffers are sized for the widest element (4 bytes).
+// Geometry of the z-march kernel for radius R.
+//   F  (FP32 patch, double-buffered): col c <-> x = cx0 - R4 + c, rows
+//      <-> y = cy0 - R + row. R4 = R rounded up to 4 keeps the x-pass
+//      window loads 16-byte aligned.
+//   X  (x-pass output, double-buffered): [BH][kXS].
+//   ring: kBZ + 2R planes of y-pass output [TY][TX].
 template <int R>
 struct ZmGeom {
-  static constexpr int BH = kTY + 2 * R;                  // TMA box height
-  static constexpr int FWN = kTX + 2 * R;                 // needed FP32 patch width
+  static constexpr int R4 = round_up(R, 4);
+  static constexpr int WL = round_up(R4 + R + 8, 4);  // x window (floats) for 8 outputs
+  static constexpr int FWN = (kTX - 8) + WL;           // F columns read
   static constexpr int FW = patch_stride(FWN);
+  static constexpr int BH = kTY + 2 * R;
+  static constexpr int NC = (FWN + 31) / 32;           // F columns per lane
   static constexpr int NRING = kBZ + 2 * R;
-  static constexpr int STAGE_BYTES = round_up(round_up(kTX + round_up(R, 4) + R, 4) * BH * 4, 128);
-  static constexpr int OFF_STAGE = 128;
-  static constexpr int OFF_F = OFF_STAGE + kNS * STAGE_BYTES;
-  static constexpr int OFF_X = OFF_F + round_up(BH * FW * 4, 128);
-  static constexpr int OFF_RING = OFF_X + round_up(BH * kXS * 4, 128);
-  static constexpr int SMEM = OFF_RING + NRING * kTY * kTX * 4;
+  static constexpr int FSZ = BH * FW;
+  static constexpr int XSZ = BH * kXS;
+  // bytes after the TMA stages
+  static constexpr int TAIL = (2 * FSZ + 2 * XSZ + NRING * kTY * kTX) * 4 + BH * 4;
   static_assert(FW >= FWN && FW % 8 == 4, "FP32 patch row stride must be 4 mod 8 floats");
+  static_assert(FWN % 4 == 0, "patch width must be a multiple of 4");
 };
 
-// Per-dtype TMA box geometry: left halo ra rounded up to 16 bytes, width bw.
+// Per-dtype TMA box geometry: left halo ra (R rounded up to 16 bytes) and
+// width bw (elements); raw col c <-> x = cx0 - ra + c.
 __host__ __device__ inline void box_geom(int r, int es, int* ra, int* bw) {
   const int al = 16 / es;
   *ra = round_up(r, al);
   *bw = round_up(kTX + *ra + r, al);
 }
 
-// Convert rows of the raw TMA stage into the FP32 patch, resolving
-// reflections at the volume faces (raw col c <-> x = cx0 - ra + c).
+__host__ __device__ inline int stage_bytes(int r, int es) {
+  int ra, bw;
+  box_geom(r, es, &ra, &bw);
+  return round_up(bw * (kTY + 2 * r) * es, 128);
+}
+
+template <int R>
+__host__ __device__ inline int zm_smem_bytes(int es) {
+  return 128 + kNS * stage_bytes(R, es) + ZmGeom<R>::TAIL;
+}
+
+// One plane of input -> FP32 patch F. Sources are looked up in per-CTA
+// tables that already resolve the reflect boundary: srow[row] is the raw
+// stage row (TMA) or box row (global loads), scol[k] the column of lane
+// column lane + 32k; -1 marks taps no stored output uses.
 template <typename TIN, int R>
-__device__ __forceinline__ void convert_patch(float* F, const unsigned char* rawb, int ra, int bw,
-                                              bool face, int64_t cx0, int64_t cy0, int64_t Gx,
-                                              int64_t Gy, int warp, int lane) {
+__device__ __forceinline__ void stage_from_tma(float* Fb, const unsigned char* rawb, int bw,
+                                               const int* srow, const int (&scol)[ZmGeom<R>::NC],
+                                               int warp, int lane) {
   using G = ZmGeom<R>;
   const TIN* raw = reinterpret_cast<const TIN*>(rawb);
   for (int row = warp; row < G::BH; row += kThreads / 32) {
-    int srow = row;
-    if (face) srow = (int)(reflect(cy0 - R + row, Gy) - (cy0 - R));
-    for (int col = lane; col < G::FWN; col += 32) {
-      int scol = col + (ra - R);
-      bool ok = true;
-      if (face) {
-        scol = (int)(reflect(cx0 - R + col, Gx) - (cx0 - ra));
-        ok = scol >= 0 && scol < bw && srow >= 0 && srow < G::BH;
+    const int sr = srow[row];
+#pragma unroll
+    for (int k = 0; k < G::NC; ++k) {
+      const int col = lane + 32 * k;
+      if (col < G::FWN) {
+        const int sc = scol[k];
+        Fb[row * G::FW + col] = (sr >= 0 && sc >= 0) ? to_f32<TIN>(raw[sr * bw + sc]) : 0.0f;
       }
-      F[row * G::FW + col] = ok ? to_f32<TIN>(raw[srow * bw + scol]) : 0.0f;
     }
   }
 }
 
-// Cooperative load of one plane straight from global memory (layouts TMA
-// cannot address), with reflection on global coordinates.
+// Interior tiles: no reflection, F col c <-> raw col c + (ra - R4); four
+// columns per item with one vector load (16-, 8- or 4-byte aligned since
+// ra - R4 is a multiple of 4 elements) and one 16-byte store.
 template <typename TIN, int R>
-__device__ __forceinline__ void load_patch(float* F, const Job& J, int64_t iz, int64_t cx0,
-                                           int64_t cy0, int warp, int lane) {
+__device__ __forceinline__ void stage_from_tma_interior(float* Fb, const unsigned char* rawb,
+                                                        int ra, int bw, int tid) {
+  using G = ZmGeom<R>;
+  constexpr int Q = G::FWN / 4;
+  const TIN* raw = reinterpret_cast<const TIN*>(rawb) + (ra - G::R4);
+  for (int it = tid; it < G::BH * Q; it += kThreads) {
+    const int row = it / Q, q = it - row * Q;
+    *reinterpret_cast<float4*>(Fb + row * G::FW + 4 * q) = load4_f32<TIN>(raw + row * bw + 4 * q);
+  }
+}
+
+template <typename TIN, int R>
+__device__ __forceinline__ void stage_from_global(float* Fb, const Job& J, int64_t sz,
+                                                  const int* srow,
+                                                  const int (&scol)[ZmGeom<R>::NC], int warp,
+                                                  int lane) {
   using G = ZmGeom<R>;
   const TIN* in = static_cast<const TIN*>(J.in.ptr);
-  const int64_t sz = reflect(iz, J.gdims[0]) - J.in.lo[0];
+  const bool zok = sz >= 0 && sz < J.in.dims[0];
+  const TIN* plane = in + sz * J.in.dims[1] * J.in.dims[2];
   for (int row = warp; row < G::BH; row += kThreads / 32) {
-    const int64_t sy = reflect(cy0 - R + row, J.gdims[1]) - J.in.lo[1];
-    for (int col = lane; col < G::FWN; col += 32) {
-      const int64_t sx = reflect(cx0 - R + col, J.gdims[2]) - J.in.lo[2];
-      float v = 0.0f;
-      if (sz >= 0 && sz < J.in.dims[0] && sy >= 0 && sy < J.in.dims[1] && sx >= 0 &&
-          sx < J.in.dims[2])
-        v = to_f32<TIN>(in[(sz * J.in.dims[1] + sy) * J.in.dims[2] + sx]);
-      F[row * G::FW + col] = v;
+    const int sr = srow[row];
+#pragma unroll
+    for (int k = 0; k < G::NC; ++k) {
+      const int col = lane + 32 * k;
+      if (col < G::FWN) {
+        const int sc = scol[k];
+        Fb[row * G::FW + col] = (zok && sr >= 0 && sc >= 0)
+                                    ? to_f32<TIN>(plane[(int64_t)sr * J.in.dims[2] + sc])
+                                    : 0.0f;
+      }
     }
   }
-}
-
-template <typename T>
-__device__ __forceinline__ void store_out(void* base, int dt, int64_t idx, float v) {
-  if (dt == HP_F32)
-    static_cast<float*>(base)[idx] = v;
-  else
-    static_cast<__half*>(base)[idx] = __float2half_rn(v);
 }
 
 template <int R>
@@ -145,14 +172,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_gauss_zm(const __grid_constant__ GaussParams P, const __grid_constant__ CUtensorMap tmap) {
   using G = ZmGeom<R>;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  float* F = reinterpret_cast<float*>(smem + G::OFF_F);
-  float* X = reinterpret_cast<float*>(smem + G::OFF_X);
-  float* ring = reinterpret_cast<float*>(smem + G::OFF_RING);
   __shared__ int s_abort;
 
   const Job& J = P.job;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
   const int64_t cx0 = J.core_lo[2] + (int64_t)tx * kTX;
   const int64_t cy0 = J.core_lo[1] + (int64_t)ty * kTY;
@@ -166,9 +189,46 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int es = dt == HP_U8 ? 1 : (dt == HP_F32 ? 4 : 2);
   int ra, bw;
   box_geom(R, es, &ra, &bw);
-  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + kTY + R > Gy);
+  const int sbytes = stage_bytes(R, es);
   const bool tma = P.use_tma != 0;
+  // tiles whose halo stays inside the volume need no reflection
+  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + kTY + R > Gy);
 
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* stages = smem + 128;
+  float* F = reinterpret_cast<float*>(stages + kNS * sbytes);
+  float* X = F + 2 * G::FSZ;
+  float* ring = X + 2 * G::XSZ;
+  int* srow = reinterpret_cast<int*>(ring + G::NRING * kTY * kTX);
+
+  // source tables (reflection resolved once per CTA)
+  for (int row = tid; row < G::BH; row += kThreads) {
+    const int64_t sy = reflect(cy0 - R + row, Gy);
+    int v;
+    if (tma) {
+      const int64_t s = sy - (cy0 - R);
+      v = (s >= 0 && s < G::BH) ? (int)s : -1;
+    } else {
+      const int64_t s = sy - J.in.lo[1];
+      v = (s >= 0 && s < J.in.dims[1]) ? (int)s : -1;
+    }
+    srow[row] = v;
+  }
+  int scol[G::NC];
+#pragma unroll
+  for (int k = 0; k < G::NC; ++k) {
+    const int col = lane + 32 * k;
+    const int64_t sx = reflect(cx0 - G::R4 + col, Gx);
+    int v = -1;
+    if (tma) {
+      const int64_t s = sx - (cx0 - ra);
+      if (s >= 0 && s < bw) v = (int)s;
+    } else {
+      const int64_t s = sx - J.in.lo[2];
+      if (s >= 0 && s < J.in.dims[2]) v = (int)s;
+    }
+    scol[k] = col < G::FWN ? v : -1;
+  }
   if (tid == 0) {
     s_abort = 0;
     if (tma) {
@@ -180,148 +240,169 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
 
   auto issue = [&](int n) {  // TMA load of input plane n into stage n % kNS
-    const int64_t iz = cz0 - R + n;
-    const int zl = (int)(reflect(iz, Gz) - J.in.lo[0]);
+    const int zl = (int)(reflect(cz0 - R + n, Gz) - J.in.lo[0]);
     const int xl = (int)(cx0 - ra - J.in.lo[2]);
     const int yl = (int)(cy0 - R - J.in.lo[1]);
     uint64_t* bar = &bars[n % kNS];
     mbar_arrive_expect_tx(bar, bw * G::BH * es);
-    tma_load_3d(smem + G::OFF_STAGE + (n % kNS) * G::STAGE_BYTES, &tmap, xl, yl, zl, bar);
+    tma_load_3d(stages + (n % kNS) * sbytes, &tmap, xl, yl, zl, bar);
   };
   if (tma && tid == 0) {
     fence_proxy_async();
     for (int n = 0; n < min(kNS, total); ++n) issue(n);
   }
 
-  // thread roles
-  const int xrow = tid / (kTX / 8), xg = (tid % (kTX / 8)) * 8;       // x pass
-  const int yx = tid % kTX, yb = (tid / kTX) * 4;                      // y pass
-  const int zy = tid / (kTX / 4), zx4 = (tid % (kTX / 4)) * 4;         // z pass
-  const int warp = tid / 32, lane = tid % 32;
+  const int xrow = tid / (kTX / 8), xg = (tid % (kTX / 8)) * 8;  // x pass
+  const int yp = tid % (kTX / 2), yb2 = (tid / (kTX / 2)) * 2;     // y pass
+  const int zy = tid / (kTX / 4), zx4 = (tid % (kTX / 4)) * 4;    // z pass
 
-  int produced = 0;
-  for (int zb = 0; zb < nout; zb += kBZ) {
-    const int need = min(zb + kBZ + 2 * R, total);
-    for (; produced < need; ++produced) {
-      const int n = produced;
-      const int64_t iz = cz0 - R + n;
-      // ---- 1. stage the FP32 patch F[BH][FW] (cols <-> x = cx0-R .. cx0+TX+R-1)
+  // ---- one pipeline phase p: stage plane p, x pass of plane p-1, y pass
+  // of plane p-2 (double-buffered F and X), then one barrier.
+  int zb = 0;
+  int p = 0;
+  for (; p < total + 2; ++p) {
+    if (p < total) {
+      float* Fb = F + (p & 1) * G::FSZ;
       if (tma) {
-        if (!mbar_wait(&bars[n % kNS], (n / kNS) & 1)) atomicOr(&s_abort, 1);
-        const unsigned char* rawb = smem + G::OFF_STAGE + (n % kNS) * G::STAGE_BYTES;
-        switch (dt) {
-          case HP_U8: convert_patch<uint8_t, R>(F, rawb, ra, bw, face, cx0, cy0, Gx, Gy, warp, lane); break;
-          case HP_U16: convert_patch<uint16_t, R>(F, rawb, ra, bw, face, cx0, cy0, Gx, Gy, warp, lane); break;
-          case HP_F16: convert_patch<__half, R>(F, rawb, ra, bw, face, cx0, cy0, Gx, Gy, warp, lane); break;
-          default: convert_patch<float, R>(F, rawb, ra, bw, face, cx0, cy0, Gx, Gy, warp, lane); break;
+        if (!mbar_wait(&bars[p % kNS], (p / kNS) & 1)) atomicOr(&s_abort, 1);
+        const unsigned char* rawb = stages + (p % kNS) * sbytes;
+        if (!face) {
+          switch (dt) {
+            case HP_U8: stage_from_tma_interior<uint8_t, R>(Fb, rawb, ra, bw, tid); break;
+            case HP_U16: stage_from_tma_interior<uint16_t, R>(Fb, rawb, ra, bw, tid); break;
+            case HP_F16: stage_from_tma_interior<__half, R>(Fb, rawb, ra, bw, tid); break;
+            default: stage_from_tma_interior<float, R>(Fb, rawb, ra, bw, tid); break;
+          }
+        } else {
+          switch (dt) {
+            case HP_U8: stage_from_tma<uint8_t, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
+            case HP_U16: stage_from_tma<uint16_t, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
+            case HP_F16: stage_from_tma<__half, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
+            default: stage_from_tma<float, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
+          }
         }
       } else {
+        const int64_t sz = reflect(cz0 - R + p, Gz) - J.in.lo[0];
         switch (dt) {
-          case HP_U8: load_patch<uint8_t, R>(F, J, iz, cx0, cy0, warp, lane); break;
-          case HP_U16: load_patch<uint16_t, R>(F, J, iz, cx0, cy0, warp, lane); break;
-          case HP_F16: load_patch<__half, R>(F, J, iz, cx0, cy0, warp, lane); break;
-          default: load_patch<float, R>(F, J, iz, cx0, cy0, warp, lane); break;
+          case HP_U8: stage_from_global<uint8_t, R>(Fb, J, sz, srow, scol, warp, lane); break;
+          case HP_U16: stage_from_global<uint16_t, R>(Fb, J, sz, srow, scol, warp, lane); break;
+          case HP_F16: stage_from_global<__half, R>(Fb, J, sz, srow, scol, warp, lane); break;
+          default: stage_from_global<float, R>(Fb, J, sz, srow, scol, warp, lane); break;
         }
       }
-      __syncthreads();
-      if (s_abort) break;
-      if (tma && tid == 0 && n + kNS < total) {
-        fence_proxy_async();
-        issue(n + kNS);
-      }
-      // ---- 2. x pass: X[row][x] for BH rows, TX columns
-      if (xrow < G::BH) {
-        constexpr int WN = 8 + 2 * R;
-        float w[round_up(WN, 4)];
-        const float4* src = reinterpret_cast<const float4*>(F + xrow * G::FW + xg);
-#pragma unroll
-        for (int j = 0; j < round_up(WN, 4) / 4; ++j) {
-          float4 v = src[j];
-          w[4 * j] = v.x;
-          w[4 * j + 1] = v.y;
-          w[4 * j + 2] = v.z;
-          w[4 * j + 3] = v.w;
-        }
-        float o[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int j = i; j <= i + 2 * R; ++j) acc = fmaf(P.wx[i - j + 2 * R], w[j], acc);
-          o[i] = acc;
-        }
-        float4* dst = reinterpret_cast<float4*>(X + xrow * kXS + xg);
-        dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_float4(o[4], o[5], o[6], o[7]);
-      }
-      __syncthreads();
-      // ---- 3. y pass into the ring slot of plane n
-      {
-        float w[4 + 2 * R];
-#pragma unroll
-        for (int j = 0; j < 4 + 2 * R; ++j) w[j] = X[(yb + j) * kXS + yx];
-        float* slot = ring + (n % G::NRING) * (kTY * kTX);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int j = i; j <= i + 2 * R; ++j) acc = fmaf(P.wy[i - j + 2 * R], w[j], acc);
-          slot[(yb + i) * kTX + yx] = acc;
-        }
-      }
-      __syncthreads();
     }
-    if (s_abort) break;
-    // ---- 4. z pass: outputs zb .. zb+BZ-1 from ring planes zb .. zb+BZ+2R-1
-    {
-      float4 acc[kBZ];
+    if (p >= 1 && p - 1 < total && xrow < G::BH) {
+      // x pass: 8 outputs of row xrow from a 16-byte aligned window of F
+      const float* Fb = F + ((p - 1) & 1) * G::FSZ;
+      float w[G::WL];
+      const float4* src = reinterpret_cast<const float4*>(Fb + xrow * G::FW + xg);
 #pragma unroll
-      for (int j = 0; j < kBZ; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < G::WL / 4; ++j) {
+        const float4 v = src[j];
+        w[4 * j] = v.x;
+        w[4 * j + 1] = v.y;
+        w[4 * j + 2] = v.z;
+        w[4 * j + 3] = v.w;
+      }
+      float o[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        float acc = 0.0f;
+        // window index j <-> x = cx0 + xg - R4 + j; tap k = i + R4 - j
+#pragma unroll
+        for (int j = i + G::R4 - R; j <= i + G::R4 + R; ++j)
+          acc = fmaf(P.wx[i + G::R4 - j + R], w[j], acc);
+        o[i] = acc;
+      }
+      float4* dst = reinterpret_cast<float4*>(X + ((p - 1) & 1) * G::XSZ + xrow * kXS + xg);
+      dst[0] = make_float4(o[0], o[1], o[2], o[3]);
+      dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+    }
+    if (p >= 2) {
+      // y pass of plane p-2 into its ring slot: one x pair, two rows per
+      // thread, packed fmas over the pair
+      const float* Xb = X + ((p - 2) & 1) * G::XSZ;
+      unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll
+      for (int j = 0; j < 2 + 2 * R; ++j) {
+        const unsigned long long v = pack2(*reinterpret_cast<const float2*>(Xb + (yb2 + j) * kXS + 2 * yp));
+        if (j <= 2 * R) a0 = ffma2(splat2(P.wy[2 * R - j]), v, a0);
+        if (j >= 1) a1 = ffma2(splat2(P.wy[2 * R + 1 - j]), v, a1);
+      }
+      float* slot = ring + ((p - 2) % G::NRING) * (kTY * kTX);
+      *reinterpret_cast<float2*>(slot + yb2 * kTX + 2 * yp) = unpack2(a0);
+      *reinterpret_cast<float2*>(slot + (yb2 + 1) * kTX + 2 * yp) = unpack2(a1);
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (tma && tid == 0 && p + kNS < total) {
+      fence_proxy_async();
+      issue(p + kNS);
+    }
+    // z pass for every block whose ring planes are all present
+    const int done = min(p - 1, total);  // planes 0 .. done-1 are in the ring
+    while (zb < nout && done >= min(zb + kBZ + 2 * R, total)) {
+      unsigned long long acc0[kBZ], acc1[kBZ];  // x pairs (0,1) and (2,3)
+#pragma unroll
+      for (int j = 0; j < kBZ; ++j) acc0[j] = acc1[j] = 0ull;
+      int slot = zb % G::NRING;
 #pragma unroll
       for (int m = 0; m < kBZ + 2 * R; ++m) {
-        const float4 v = *reinterpret_cast<const float4*>(
-            ring + ((zb + m) % G::NRING) * (kTY * kTX) + zy * kTX + zx4);
+        const float4 v =
+            *reinterpret_cast<const float4*>(ring + slot * (kTY * kTX) + zy * kTX + zx4);
+        slot = slot + 1 == G::NRING ? 0 : slot + 1;
+        const unsigned long long v0 = pack2(make_float2(v.x, v.y)), v1 = pack2(make_float2(v.z, v.w));
 #pragma unroll
         for (int j = 0; j < kBZ; ++j) {
           if (m >= j && m <= j + 2 * R) {
-            const float g = P.wz[j - m + 2 * R];
-            acc[j].x = fmaf(g, v.x, acc[j].x);
-            acc[j].y = fmaf(g, v.y, acc[j].y);
-            acc[j].z = fmaf(g, v.z, acc[j].z);
-            acc[j].w = fmaf(g, v.w, acc[j].w);
+            const unsigned long long g = splat2(P.wz[j - m + 2 * R]);
+            acc0[j] = ffma2(g, v0, acc0[j]);
+            acc1[j] = ffma2(g, v1, acc1[j]);
           }
         }
+      }
+      float4 acc[kBZ];
+#pragma unroll
+      for (int j = 0; j < kBZ; ++j) {
+        const float2 lo = unpack2(acc0[j]), hi = unpack2(acc1[j]);
+        acc[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
       }
       const int64_t gy = cy0 + zy, gx = cx0 + zx4;
       if (gy < J.core_hi[1]) {
         const DevOut& O = J.out;
-        const int64_t od1 = O.dims[1], od2 = O.dims[2];
+        const int64_t pstride = O.dims[1] * O.dims[2];
+        int64_t idx = ((cz0 + zb - O.lo[0]) * O.dims[1] + (gy - O.lo[1])) * O.dims[2] + (gx - O.lo[2]);
         const bool full4 = gx + 3 < J.core_hi[2];
+        const bool vec = O.dtype == HP_F32 && full4 &&
+                         ((reinterpret_cast<uintptr_t>(static_cast<float*>(O.ptr) + idx) |
+                           (uintptr_t)(pstride * 4)) & 15) == 0;
 #pragma unroll
-        for (int j = 0; j < kBZ; ++j) {
-          const int64_t gz = cz0 + zb + j;
-          if (gz >= cz1) break;
-          const int64_t idx = ((gz - O.lo[0]) * od1 + (gy - O.lo[1])) * od2 + (gx - O.lo[2]);
-          const float vv[4] = {acc[j].x, acc[j].y, acc[j].z, acc[j].w};
-          if (O.dtype == HP_F32 && full4 &&
-              (reinterpret_cast<uintptr_t>(static_cast<float*>(O.ptr) + idx) & 15) == 0) {
+        for (int j = 0; j < kBZ; ++j, idx += pstride) {
+          if (zb + j >= nout) break;
+          if (vec) {
             *reinterpret_cast<float4*>(static_cast<float*>(O.ptr) + idx) = acc[j];
           } else {
+            const float vv[4] = {acc[j].x, acc[j].y, acc[j].z, acc[j].w};
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-              if (full4 || gx + e < J.core_hi[2]) store_out<float>(O.ptr, O.dtype, idx + e, vv[e]);
+              if (gx + e < J.core_hi[2]) {
+                if (O.dtype == HP_F32)
+                  static_cast<float*>(O.ptr)[idx + e] = vv[e];
+                else
+                  static_cast<__half*>(O.ptr)[idx + e] = __float2half_rn(vv[e]);
+              }
           }
         }
       }
+      zb += kBZ;
+      __syncthreads();  // ring slots of this block are rewritten next
     }
-    __syncthreads();  // ring slots are overwritten by the next block
   }
   if (s_abort) {
     set_device_error(P.err, kErrTimeout);
     // drain TMA loads still in flight into this CTA's shared memory
     if (tma && tid == 0)
-      for (int n = max(0, produced); n < min(produced + kNS, total); ++n)
-        (void)mbar_wait(&bars[n % kNS], (n / kNS) & 1);
+      for (int n = p; n < min(p + kNS, total); ++n) (void)mbar_wait(&bars[n % kNS], (n / kNS) & 1);
     __syncthreads();
   }
 }
@@ -373,15 +454,15 @@ __global__ void k_copy_out(const float* src, int64_t n0, int64_t n1, int64_t n2,
 
 template <int R>
 cudaError_t launch_zm_t(const GaussParams& P, const CUtensorMap& map, dim3 grid, cudaStream_t s) {
-  using G = ZmGeom<R>;
   static bool attr_set = false;  // per instantiation; set once per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gauss_zm<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_gauss_zm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         zm_smem_bytes<R>(4));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_gauss_zm<R><<<grid, kThreads, G::SMEM, s>>>(P, map);
+  const int es = (int)dtype_size(P.job.in.dtype);
+  k_gauss_zm<R><<<grid, kThreads, zm_smem_bytes<R>(es), s>>>(P, map);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,34 @@ __host__ __device__ constexpr int isqrt(int v) {
   while ((s + 1) * (s + 1) <= v) ++s;
   return s;
 }
+// Ball decomposition, fixed at compile time: the x-line at (dy, dz) has
+// half-length L = floor(sqrt(R^2 - dy^2 - dz^2)); template recursion over dy
+// keeps every L and every shared-memory offset a compile-time constant.
+// (Cube: one line of half-length R for every dy.)
+template <int R, int BALL, int BH, int DZ, int DY>
+__device__ __forceinline__ void disk_min(uint32_t& d, const uint32_t* Mb) {
+  if constexpr (DY <= R) {
+    if constexpr (!BALL || DZ * DZ + DY * DY <= R * R) {
+      constexpr int L = BALL ? isqrt(R * R - DZ * DZ - DY * DY) : 0;
+      d = min(d, Mb[(L * BH + DY + R) * (32 + 1)]);
+    }
+    disk_min<R, BALL, BH, DZ, DY + 1>(d, Mb);
+  }
+}
+
+template <int R, int BALL, int BH, int DZ, int YB>
+__device__ __forceinline__ void disk_rows(uint32_t (&D)[BALL ? R + 1 : 1][YB], const uint32_t* Mb) {
+  if constexpr (DZ <= (BALL ? R : 0)) {
+#pragma unroll
+    for (int i = 0; i < YB; ++i) {
+      uint32_t d = 0xFFFFFFFFu;
+      disk_min<R, BALL, BH, DZ, -R>(d, Mb + i * (32 + 1));
+      D[DZ][i] = d;
+    }
+    disk_rows<R, BALL, BH, DZ + 1, YB>(D, Mb);
+  }
+}
+
 // Odd row strides (in 32-bit words) spread the 8 rows x 4 column groups a
 // warp touches over all 32 banks.
 __host__ __device__ constexpr int key_stride(int n) { return n | 1; }
@@ -109,19 +137,19 @@ struct KeyMask {
   static constexpr uint32_t value = sizeof(T) == 4 ? 0xFFFFFFFFu : (sizeof(T) == 2 ? 0xFFFFu : 0xFFu);
 };
 
+// Geometry for radius R: K (keys, double-buffered) col c <-> x = cx0 - R + c,
+// row <-> y = cy0 - R + row; M (x-line minima, double-buffered) [NL][BH][kMS].
 template <int R, int BALL>
 struct MGeom {
   static constexpr int BH = kTY + 2 * R;
   static constexpr int KWN = kTX + 2 * R;
   static constexpr int KW = key_stride(KWN);
+  static constexpr int NC = (KWN + 31) / 32;
   static constexpr int NL = BALL ? R + 1 : 1;  // stored x-line minima
   static constexpr int NR = 2 * R + 1;         // z accumulator ring
-  // stage buffers sized for the widest element (4 bytes)
-  static constexpr int STAGE_BYTES = round_up(round_up(kTX + round_up(R, 4) + R, 4) * BH * 4, 128);
-  static constexpr int OFF_STAGE = 128;
-  static constexpr int OFF_K = OFF_STAGE + kNS * STAGE_BYTES;
-  static constexpr int OFF_M = OFF_K + round_up(BH * KW * 4, 128);
-  static constexpr int SMEM = OFF_M + NL * BH * kMS * 4;
+  static constexpr int KSZ = BH * KW;
+  static constexpr int MSZ = NL * BH * kMS;
+  static constexpr int TAIL = (2 * KSZ + 2 * MSZ) * 4 + BH * 4;
 };
 
 __host__ __device__ inline void mbox_geom(int r, int es, int* ra, int* bw) {
@@ -130,44 +158,74 @@ __host__ __device__ inline void mbox_geom(int r, int es, int* ra, int* bw) {
   *bw = round_up(kTX + *ra + r, al);
 }
 
+__host__ __device__ inline int mstage_bytes(int r, int es) {
+  int ra, bw;
+  mbox_geom(r, es, &ra, &bw);
+  return round_up(bw * (kTY + 2 * r) * es, 128);
+}
+
+template <int R, int BALL>
+__host__ __device__ inline int mzm_smem_bytes(int es) {
+  return 128 + kNS * mstage_bytes(R, es) + MGeom<R, BALL>::TAIL;
+}
+
 template <typename TIN, int R, int BALL>
-__device__ __forceinline__ void keys_from_stage(uint32_t* K, const unsigned char* rawb, int ra,
-                                                int bw, bool face, int64_t cx0, int64_t cy0,
-                                                int64_t Gx, int64_t Gy, uint32_t flip, int warp,
-                                                int lane) {
+__device__ __forceinline__ void keys_from_tma(uint32_t* Kb, const unsigned char* rawb, int bw,
+                                              const int* srow,
+                                              const int (&scol)[MGeom<R, BALL>::NC],
+                                              uint32_t flip, int warp, int lane) {
   using G = MGeom<R, BALL>;
   const TIN* raw = reinterpret_cast<const TIN*>(rawb);
   for (int row = warp; row < G::BH; row += kThreads / 32) {
-    int srow = row;
-    if (face) srow = (int)(reflect(cy0 - R + row, Gy) - (cy0 - R));
-    for (int col = lane; col < G::KWN; col += 32) {
-      int scol = col + (ra - R);
-      bool ok = true;
-      if (face) {
-        scol = (int)(reflect(cx0 - R + col, Gx) - (cx0 - ra));
-        ok = scol >= 0 && scol < bw && srow >= 0 && srow < G::BH;
+    const int sr = srow[row];
+#pragma unroll
+    for (int k = 0; k < G::NC; ++k) {
+      const int col = lane + 32 * k;
+      if (col < G::KWN) {
+        const int sc = scol[k];
+        Kb[row * G::KW + col] = (sr >= 0 && sc >= 0) ? (to_key<TIN>(raw[sr * bw + sc]) ^ flip) : 0u;
       }
-      K[row * G::KW + col] = ok ? (to_key<TIN>(raw[srow * bw + scol]) ^ flip) : 0u;
     }
   }
 }
 
+// Interior tiles: K col c <-> raw col c + (ra - R), four keys per item.
 template <typename TIN, int R, int BALL>
-__device__ __forceinline__ void keys_from_global(uint32_t* K, const Job& J, int64_t iz,
-                                                 int64_t cx0, int64_t cy0, uint32_t flip,
-                                                 int warp, int lane) {
+__device__ __forceinline__ void keys_from_tma_interior(uint32_t* Kb, const unsigned char* rawb,
+                                                       int ra, int bw, uint32_t flip, int tid) {
+  using G = MGeom<R, BALL>;
+  constexpr int Q = (G::KWN + 3) / 4;
+  const TIN* raw = reinterpret_cast<const TIN*>(rawb) + (ra - R);
+  for (int it = tid; it < G::BH * Q; it += kThreads) {
+    const int row = it / Q, q = it - row * Q;
+    const TIN* src = raw + row * bw + 4 * q;
+    uint32_t* dst = Kb + row * G::KW + 4 * q;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * q + e < G::KWN) dst[e] = to_key<TIN>(src[e]) ^ flip;
+  }
+}
+
+template <typename TIN, int R, int BALL>
+__device__ __forceinline__ void keys_from_global(uint32_t* Kb, const Job& J, int64_t sz,
+                                                 const int* srow,
+                                                 const int (&scol)[MGeom<R, BALL>::NC],
+                                                 uint32_t flip, int warp, int lane) {
   using G = MGeom<R, BALL>;
   const TIN* in = static_cast<const TIN*>(J.in.ptr);
-  const int64_t sz = reflect(iz, J.gdims[0]) - J.in.lo[0];
+  const bool zok = sz >= 0 && sz < J.in.dims[0];
+  const TIN* plane = in + sz * J.in.dims[1] * J.in.dims[2];
   for (int row = warp; row < G::BH; row += kThreads / 32) {
-    const int64_t sy = reflect(cy0 - R + row, J.gdims[1]) - J.in.lo[1];
-    for (int col = lane; col < G::KWN; col += 32) {
-      const int64_t sx = reflect(cx0 - R + col, J.gdims[2]) - J.in.lo[2];
-      uint32_t v = 0u;
-      if (sz >= 0 && sz < J.in.dims[0] && sy >= 0 && sy < J.in.dims[1] && sx >= 0 &&
-          sx < J.in.dims[2])
-        v = to_key<TIN>(in[(sz * J.in.dims[1] + sy) * J.in.dims[2] + sx]) ^ flip;
-      K[row * G::KW + col] = v;
+    const int sr = srow[row];
+#pragma unroll
+    for (int k = 0; k < G::NC; ++k) {
+      const int col = lane + 32 * k;
+      if (col < G::KWN) {
+        const int sc = scol[k];
+        Kb[row * G::KW + col] = (zok && sr >= 0 && sc >= 0)
+                                    ? (to_key<TIN>(plane[(int64_t)sr * J.in.dims[2] + sc]) ^ flip)
+                                    : 0u;
+      }
     }
   }
 }
@@ -228,13 +286,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_morph_zm(const __grid_constant__ MorphParams P, const __grid_constant__ CUtensorMap tmap) {
   using G = MGeom<R, BALL>;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* K = reinterpret_cast<uint32_t*>(smem + G::OFF_K);
-  uint32_t* M = reinterpret_cast<uint32_t*>(smem + G::OFF_M);
   __shared__ int s_abort;
 
   const Job& J = P.job;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
   const int64_t cx0 = J.core_lo[2] + (int64_t)tx * kTX;
   const int64_t cy0 = J.core_lo[1] + (int64_t)ty * kTY;
@@ -248,10 +303,44 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int es = dt == HP_U8 ? 1 : (dt == HP_F32 ? 4 : 2);
   int ra, bw;
   mbox_geom(R, es, &ra, &bw);
-  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + kTY + R > Gy);
+  const int sbytes = mstage_bytes(R, es);
   const bool tma = P.use_tma != 0;
   const uint32_t flip = P.is_dilate ? key_mask(dt) : 0u;
+  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + kTY + R > Gy);
 
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* stages = smem + 128;
+  uint32_t* K = reinterpret_cast<uint32_t*>(stages + kNS * sbytes);
+  uint32_t* M = K + 2 * G::KSZ;
+  int* srow = reinterpret_cast<int*>(M + 2 * G::MSZ);
+
+  for (int row = tid; row < G::BH; row += kThreads) {
+    const int64_t sy = reflect(cy0 - R + row, Gy);
+    int v;
+    if (tma) {
+      const int64_t s = sy - (cy0 - R);
+      v = (s >= 0 && s < G::BH) ? (int)s : -1;
+    } else {
+      const int64_t s = sy - J.in.lo[1];
+      v = (s >= 0 && s < J.in.dims[1]) ? (int)s : -1;
+    }
+    srow[row] = v;
+  }
+  int scol[G::NC];
+#pragma unroll
+  for (int k = 0; k < G::NC; ++k) {
+    const int col = lane + 32 * k;
+    const int64_t sx = reflect(cx0 - R + col, Gx);
+    int v = -1;
+    if (tma) {
+      const int64_t s = sx - (cx0 - ra);
+      if (s >= 0 && s < bw) v = (int)s;
+    } else {
+      const int64_t s = sx - J.in.lo[2];
+      if (s >= 0 && s < J.in.dims[2]) v = (int)s;
+    }
+    scol[k] = col < G::KWN ? v : -1;
+  }
   if (tid == 0) {
     s_abort = 0;
     if (tma) {
@@ -263,13 +352,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
 
   auto issue = [&](int n) {
-    const int64_t iz = cz0 - R + n;
-    const int zl = (int)(reflect(iz, Gz) - J.in.lo[0]);
+    const int zl = (int)(reflect(cz0 - R + n, Gz) - J.in.lo[0]);
     const int xl = (int)(cx0 - ra - J.in.lo[2]);
     const int yl = (int)(cy0 - R - J.in.lo[1]);
     uint64_t* bar = &bars[n % kNS];
     mbar_arrive_expect_tx(bar, bw * G::BH * es);
-    tma_load_3d(smem + G::OFF_STAGE + (n % kNS) * G::STAGE_BYTES, &tmap, xl, yl, zl, bar);
+    tma_load_3d(stages + (n % kNS) * sbytes, &tmap, xl, yl, zl, bar);
   };
   if (tma && tid == 0) {
     fence_proxy_async();
@@ -278,7 +366,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int xrow = tid / (kTX / 8), xg = (tid % (kTX / 8)) * 8;
   const int yx = tid % kTX, yb = (tid / kTX) * kYB;
-  const int warp = tid / 32, lane = tid % 32;
 
   uint32_t acc[G::NR][kYB];
 #pragma unroll
@@ -286,72 +373,67 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int i = 0; i < kYB; ++i) acc[s][i] = 0xFFFFFFFFu;
 
-  int n = 0;
-  for (; n < total; ++n) {
-    const int64_t iz = cz0 - R + n;
-    // ---- stage keys K[BH][KW] (cols <-> x = cx0-R .. cx0+TX+R-1)
-    if (tma) {
-      if (!mbar_wait(&bars[n % kNS], (n / kNS) & 1)) atomicOr(&s_abort, 1);
-      const unsigned char* rawb = smem + G::OFF_STAGE + (n % kNS) * G::STAGE_BYTES;
-      switch (dt) {
-        case HP_U8: keys_from_stage<uint8_t, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
-        case HP_U16: keys_from_stage<uint16_t, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
-        case HP_F16: keys_from_stage<__half, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
-        default: keys_from_stage<float, R, BALL>(K, rawb, ra, bw, face, cx0, cy0, Gx, Gy, flip, warp, lane); break;
-      }
-    } else {
-      switch (dt) {
-        case HP_U8: keys_from_global<uint8_t, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
-        case HP_U16: keys_from_global<uint16_t, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
-        case HP_F16: keys_from_global<__half, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
-        default: keys_from_global<float, R, BALL>(K, J, iz, cx0, cy0, flip, warp, lane); break;
+  // phase p: stage keys of plane p, x-line minima of plane p-1, disk minima
+  // and z push of plane p-2; one barrier per phase.
+  int p = 0;
+  for (; p < total + 2; ++p) {
+    if (p < total) {
+      uint32_t* Kb = K + (p & 1) * G::KSZ;
+      if (tma) {
+        if (!mbar_wait(&bars[p % kNS], (p / kNS) & 1)) atomicOr(&s_abort, 1);
+        const unsigned char* rawb = stages + (p % kNS) * sbytes;
+        if (!face) {
+          switch (dt) {
+            case HP_U8: keys_from_tma_interior<uint8_t, R, BALL>(Kb, rawb, ra, bw, flip, tid); break;
+            case HP_U16: keys_from_tma_interior<uint16_t, R, BALL>(Kb, rawb, ra, bw, flip, tid); break;
+            case HP_F16: keys_from_tma_interior<__half, R, BALL>(Kb, rawb, ra, bw, flip, tid); break;
+            default: keys_from_tma_interior<float, R, BALL>(Kb, rawb, ra, bw, flip, tid); break;
+          }
+        } else {
+          switch (dt) {
+            case HP_U8: keys_from_tma<uint8_t, R, BALL>(Kb, rawb, bw, srow, scol, flip, warp, lane); break;
+            case HP_U16: keys_from_tma<uint16_t, R, BALL>(Kb, rawb, bw, srow, scol, flip, warp, lane); break;
+            case HP_F16: keys_from_tma<__half, R, BALL>(Kb, rawb, bw, srow, scol, flip, warp, lane); break;
+            default: keys_from_tma<float, R, BALL>(Kb, rawb, bw, srow, scol, flip, warp, lane); break;
+          }
+        }
+      } else {
+        const int64_t sz = reflect(cz0 - R + p, Gz) - J.in.lo[0];
+        switch (dt) {
+          case HP_U8: keys_from_global<uint8_t, R, BALL>(Kb, J, sz, srow, scol, flip, warp, lane); break;
+          case HP_U16: keys_from_global<uint16_t, R, BALL>(Kb, J, sz, srow, scol, flip, warp, lane); break;
+          case HP_F16: keys_from_global<__half, R, BALL>(Kb, J, sz, srow, scol, flip, warp, lane); break;
+          default: keys_from_global<float, R, BALL>(Kb, J, sz, srow, scol, flip, warp, lane); break;
+        }
       }
     }
-    __syncthreads();
-    if (s_abort) break;
-    if (tma && tid == 0 && n + kNS < total) {
-      fence_proxy_async();
-      issue(n + kNS);
-    }
-    // ---- x: line minima of half-length L
-    if (xrow < G::BH) {
+    if (p >= 1 && p - 1 < total && xrow < G::BH) {
+      const uint32_t* Kb = K + ((p - 1) & 1) * G::KSZ;
+      uint32_t* Mb = M + ((p - 1) & 1) * G::MSZ;
       uint32_t w[8 + 2 * R];
 #pragma unroll
-      for (int j = 0; j < 8 + 2 * R; ++j) w[j] = K[xrow * G::KW + xg + j];
+      for (int j = 0; j < 8 + 2 * R; ++j) w[j] = Kb[xrow * G::KW + xg + j];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         uint32_t m = w[i + R];
-        if (BALL) M[(0 * G::BH + xrow) * kMS + xg + i] = m;
+        if (BALL) Mb[(0 * G::BH + xrow) * kMS + xg + i] = m;
 #pragma unroll
         for (int L = 1; L <= R; ++L) {
           m = min(m, min(w[i + R - L], w[i + R + L]));
-          if (BALL) M[(L * G::BH + xrow) * kMS + xg + i] = m;
+          if (BALL) Mb[(L * G::BH + xrow) * kMS + xg + i] = m;
         }
-        if (!BALL) M[xrow * kMS + xg + i] = m;
+        if (!BALL) Mb[xrow * kMS + xg + i] = m;
       }
     }
-    __syncthreads();
-    // ---- y: disk minima per |dz| (ball) or the square minimum (cube)
-    uint32_t D[BALL ? R + 1 : 1][kYB];
-#pragma unroll
-    for (int dz = 0; dz <= (BALL ? R : 0); ++dz) {
-      const int ym = BALL ? isqrt(R * R - dz * dz) : R;
-#pragma unroll
-      for (int i = 0; i < kYB; ++i) {
-        uint32_t d = 0xFFFFFFFFu;
-#pragma unroll
-        for (int dy = -ym; dy <= ym; ++dy) {
-          const int L = BALL ? isqrt(R * R - dz * dz - dy * dy) : 0;
-          d = min(d, M[(L * G::BH + yb + i + dy + R) * kMS + yx]);
-        }
-        D[dz][i] = d;
-      }
-    }
-    // ---- z: push into the ring; the output of plane iz - R is complete
-    uint32_t done[kYB];
-    push_dispatch<R, BALL>(n % G::NR, acc, D, done);
-    {
-      const int64_t gz = iz - R, gx = cx0 + yx;
+    if (p >= 2) {
+      const int n = p - 2;
+      const uint32_t* Mb = M + (n & 1) * G::MSZ;
+      uint32_t D[BALL ? R + 1 : 1][kYB];
+      static_assert(kMS == 32 + 1, "disk_min assumes the line-minimum row stride");
+      disk_rows<R, BALL, G::BH, 0, kYB>(D, Mb + yb * kMS + yx);
+      uint32_t done[kYB];
+      push_dispatch<R, BALL>(n % G::NR, acc, D, done);
+      const int64_t gz = cz0 - R + n - R, gx = cx0 + yx;  // plane n's input z minus R
       if (gz >= cz0 && gz < cz1 && gx < J.core_hi[2]) {
         const DevOut& O = J.out;
 #pragma unroll
@@ -365,12 +447,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    __syncthreads();  // K and M are rewritten by the next plane
+    __syncthreads();
+    if (s_abort) break;
+    if (tma && tid == 0 && p + kNS < total) {
+      fence_proxy_async();
+      issue(p + kNS);
+    }
   }
   if (s_abort) {
     set_device_error(P.err, kErrTimeout);
     if (tma && tid == 0)
-      for (int m = n; m < min(n + kNS, total); ++m) (void)mbar_wait(&bars[m % kNS], (m / kNS) & 1);
+      for (int m = p; m < min(p + kNS, total); ++m) (void)mbar_wait(&bars[m % kNS], (m / kNS) & 1);
     __syncthreads();
   }
 }
@@ -410,15 +497,16 @@ __global__ void k_morph_generic(const Job J, int ball, int rad, int is_dilate) {
 
 template <int R, int BALL>
 cudaError_t launch_mzm(const MorphParams& P, const CUtensorMap& map, dim3 grid, cudaStream_t s) {
-  using G = MGeom<R, BALL>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_morph_zm<R, BALL>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         mzm_smem_bytes<R, BALL>(4));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_morph_zm<R, BALL><<<grid, kThreads, G::SMEM, s>>>(P, map);
+  const int es = (int)dtype_size(P.job.in.dtype);
+  k_morph_zm<R, BALL><<<grid, kThreads, mzm_smem_bytes<R, BALL>(es), s>>>(P, map);
   return cudaGetLastError();
 }
 

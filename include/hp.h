@@ -160,12 +160,15 @@ int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream);
 int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
                             const hp_filter* f, int n, hp_volume* gin, void* stream);
 
-/* Subgradient of erosion (is_dilate = 0) or dilation (1), device mode, f32:
- * gin[q] = sum of gout[p] over outputs p whose extreme source is q; among
- * equal values the source with the smallest linear index wins. Deterministic
- * (a gather, no atomics). Uses library scratch (an int32 index per voxel). */
+/* Subgradient of erosion (is_dilate = 0) or dilation (1), device mode, f32
+ * gradients, input of any dtype: gin[q] = sum of gout[p] over outputs p whose
+ * extreme source is q; among equal values the source with the smallest linear
+ * index wins. With accumulate != 0 the sum is added to gin instead of
+ * overwriting it. Deterministic (an argmin map, then a gather; no atomics).
+ * Uses library scratch: an int32 source index per voxel, so at most
+ * 2^31 - 1 voxels. */
 int hp_morph3d_backward(const hp_volume* in, const hp_volume* gout, int is_dilate, hp_se se,
-                        int radius, hp_volume* gin, void* stream);
+                        int radius, hp_volume* gin, int accumulate, void* stream);
 
 /* Chunk planner (Sec. III-D step 2), host only, no device work. Splits an
  * (nz, ny, nx) volume into bricks whose core boxes tile it exactly; box i's

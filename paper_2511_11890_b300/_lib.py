@@ -71,7 +71,7 @@ def _load() -> ctypes.CDLL:
         "hp_dilate3d": [vp, vp, i, i, vp],
         "hp_threshold3d": [vp, vp, d, vp],
         "hp_filterbank3d_adjoint": [vp, pvp, ctypes.POINTER(hp_filter), i, vp, vp],
-        "hp_morph3d_backward": [vp, vp, i, i, i, vp, vp],
+        "hp_morph3d_backward": [vp, vp, i, i, i, vp, i, vp],
         "hp_plan_bricks": [i64, i64, i64, i, sz, sz, sz, i, i, ctypes.POINTER(hp_box),
                            ctypes.POINTER(hp_box), i, ctypes.POINTER(i)],
         "hp_stream_status": [vp],

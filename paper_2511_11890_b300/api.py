@@ -176,12 +176,15 @@ def filterbank3d_adjoint(x, gouts, filters, gin=None, stream=None):
     return gin
 
 
-def morph3d_backward(x, gout, dilate: bool, se="cube", radius: int = 1, gin=None, stream=None):
+def morph3d_backward(x, gout, dilate: bool, se="cube", radius: int = 1, gin=None,
+                     accumulate: bool = False, stream=None):
+    """Subgradient of erosion / dilation (ties to the smallest source index)."""
     if gin is None:
         gin = _empty_like(x, HP_F32)
+        accumulate = False
     with _ctx(x), _View(x) as vi, _View(gout) as vg, _View(gin) as vo:
         check(lib.hp_morph3d_backward(vi, vg, int(bool(dilate)), SE[se], int(radius), vo,
-                                      _stream(x, stream)))
+                                      int(bool(accumulate)), _stream(x, stream)))
     return gin
 
 

@@ -71,6 +71,13 @@ static void track_alloc(int64_t b) {
 }
 static void track_free(int64_t b) { g_live.fetch_sub(b); }
 
+// Stream-ordered scratch of device-mode calls (positive on allocation,
+// negative on release).
+void note_scratch(int64_t bytes) {
+  if (bytes > 0) track_alloc(bytes);
+  else track_free(-bytes);
+}
+
 size_t budget_setting() {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_budget_init) {
@@ -98,6 +105,8 @@ static int effective_budget(size_t* out) {
 __device__ int g_error_word;
 static int* g_err_ptr[64];
 static std::mutex g_err_mu;
+
+int64_t bank_cache_bytes();
 
 int* device_error_word() {
   int dev = 0;
@@ -754,7 +763,7 @@ int hp_get_stats(hp_stats* s) {
   *s = g_stats;
   s->live_device_bytes = (size_t)std::max<int64_t>(0, g_live.load());
   s->peak_device_bytes = (size_t)std::max<int64_t>(0, g_peak.load());
-  s->cached_device_bytes = (size_t)std::max<int64_t>(0, g_cached.load());
+  s->cached_device_bytes = (size_t)std::max<int64_t>(0, bank_cache_bytes());
   return HP_OK;
 }
 

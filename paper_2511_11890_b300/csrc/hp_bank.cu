@@ -27,6 +27,64 @@ struct BankRequest {
 };
 int run_filterbank(const BankRequest& q, cudaStream_t s);
 void bank_release_cache();
+cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3],
+                               const Taps& taps, float* t1, float* t2, int accumulate,
+                               cudaStream_t s);
+cudaError_t launch_gm_chain(const float* w, const float* dz, const float* dy, const float* dx,
+                            const float* da, float* v, int64_t total, cudaStream_t s);
+cudaError_t launch_morph_arg(const void* in, int dt, const int64_t dims[3], int ball, int rad,
+                             int is_dilate, int32_t* arg, cudaStream_t s);
+cudaError_t launch_morph_gather(const int32_t* arg, const float* gout, float* gin,
+                                const int64_t dims[3], int rad, int accumulate, cudaStream_t s);
+size_t budget_setting();
+void note_scratch(int64_t bytes);
+
+// Stream-ordered scratch, counted against the memory budget.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<std::pair<void*, size_t>> bufs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) {
+      bufs.push_back({*p, bytes});
+      note_scratch((int64_t)bytes);
+    }
+    return e;
+  }
+  ~Scratch() {
+    for (auto& b : bufs) {
+      cudaFreeAsync(b.first, s);
+      note_scratch(-(int64_t)b.second);
+    }
+  }
+};
+
+static int check_scratch_budget(size_t need) {
+  size_t b = budget_setting();
+  if (b == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return set_error(HP_ERR_CUDA, "cudaMemGetInfo failed");
+    b = (size_t)(0.8 * (double)fr);
+  }
+  if (need > b)
+    return set_error(HP_ERR_BUDGET, "scratch of " + std::to_string(need) + " bytes exceeds the budget of " +
+                                        std::to_string(b) + " bytes");
+  return HP_OK;
+}
+
+static Job whole_job_of(const hp_volume* in, void* out, int out_dtype) {
+  Job j;
+  const int64_t n[3] = {in->nz, in->ny, in->nx};
+  j.in = DevBox{in->data, in->dtype, {0, 0, 0}, {n[0], n[1], n[2]}};
+  j.out = DevOut{out, out_dtype, {0, 0, 0}, {n[0], n[1], n[2]}};
+  for (int a = 0; a < 3; ++a) {
+    j.gdims[a] = n[a];
+    j.core_lo[a] = 0;
+    j.core_hi[a] = n[a];
+  }
+  return j;
+}
 
 static int check_bricks(const std::vector<hp_box>& b, const int64_t G[3]) {
   int64_t vol = 0;
@@ -116,13 +174,111 @@ int hp_filterbank3d_bricks(const hp_volume* in, hp_volume* const* outs, const hp
   return bank_common(in, outs, f, n, bricks, nbricks, stream);
 }
 
-int hp_filterbank3d_adjoint(const hp_volume*, const hp_volume* const*, const hp_filter*, int,
-                            hp_volume*, void*) {
-  return set_error(HP_ERR_UNSUPPORTED, "adjoint not built yet");
+int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
+                            const hp_filter* f, int n, hp_volume* gin, void* stream) {
+  if (!in || !in->data || !gouts || !f || n < 1 || !gin || !gin->data)
+    return set_error(HP_ERR_INVALID_ARG, "adjoint: null argument or n < 1");
+  if (in->loc != HP_DEVICE || gin->loc != HP_DEVICE)
+    return set_error(HP_ERR_UNSUPPORTED, "adjoint runs on device volumes only");
+  if (gin->dtype != HP_F32) return set_error(HP_ERR_UNSUPPORTED, "adjoint: gin must be f32");
+  if (gin->nx != in->nx || gin->ny != in->ny || gin->nz != in->nz)
+    return set_error(HP_ERR_INVALID_ARG, "adjoint: gin extents differ from the input");
+  bool any_gm = false;
+  for (int i = 0; i < n; ++i) {
+    const hp_volume* g = gouts[i];
+    if (!g || !g->data || g->loc != HP_DEVICE || g->dtype != HP_F32 || g->nx != in->nx ||
+        g->ny != in->ny || g->nz != in->nz)
+      return set_error(HP_ERR_INVALID_ARG, "adjoint: every output gradient must be an f32 device volume of the input's extents");
+    if (f[i].kind < HP_FILTER_G || f[i].kind > HP_FILTER_LOG || !(f[i].sigma > 0))
+      return set_error(HP_ERR_INVALID_ARG, "adjoint: bad filter");
+    if (radius_of(f[i].sigma, 3.0) > kMaxRGeneric)
+      return set_error(HP_ERR_UNSUPPORTED, "adjoint: radius exceeds 32");
+    any_gm = any_gm || f[i].kind == HP_FILTER_GM;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t dims[3] = {in->nz, in->ny, in->nx};
+  const int64_t total = dims[0] * dims[1] * dims[2];
+  const size_t vb = sizeof(float) * (size_t)total;
+  int st = check_scratch_budget(vb * (any_gm ? 6 : 2));
+  if (st != HP_OK) return st;
+  Scratch sc(s);
+  float *t1 = nullptr, *t2 = nullptr, *dz = nullptr, *dy = nullptr, *dx = nullptr, *v = nullptr;
+  cudaError_t e = sc.alloc((void**)&t1, vb);
+  if (e == cudaSuccess) e = sc.alloc((void**)&t2, vb);
+  if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dz, vb);
+  if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dy, vb);
+  if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dx, vb);
+  if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&v, vb);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
+  float* g = static_cast<float*>(gin->data);
+  if ((e = cudaMemsetAsync(g, 0, vb, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const float* w = static_cast<const float*>(gouts[i]->data);
+    const double sigma = f[i].sigma;
+    Taps taps;
+    if (f[i].kind == HP_FILTER_G) {
+      const int ord[3] = {0, 0, 0};
+      make_taps(sigma, 3.0, ord, &taps);
+      e = launch_sep_adjoint(w, g, dims, taps, t1, t2, 1, s);
+    } else if (f[i].kind == HP_FILTER_LOG) {
+      for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        int ord[3] = {0, 0, 0};
+        ord[a] = 2;
+        make_taps(sigma, 3.0, ord, &taps);
+        e = launch_sep_adjoint(w, g, dims, taps, t1, t2, 1, s);
+      }
+    } else {
+      float* D[3] = {dz, dy, dx};
+      for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        int ord[3] = {0, 0, 0};
+        ord[a] = 1;
+        make_taps(sigma, 3.0, ord, &taps);
+        e = launch_gauss(whole_job_of(in, D[a], HP_F32), taps, s);
+      }
+      for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+        int ord[3] = {0, 0, 0};
+        ord[a] = 1;
+        make_taps(sigma, 3.0, ord, &taps);
+        e = launch_gm_chain(w, dz, dy, dx, D[a], v, total, s);
+        if (e == cudaSuccess) e = launch_sep_adjoint(v, g, dims, taps, t1, t2, 1, s);
+      }
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  return HP_OK;
 }
 
-int hp_morph3d_backward(const hp_volume*, const hp_volume*, int, hp_se, int, hp_volume*, void*) {
-  return set_error(HP_ERR_UNSUPPORTED, "morphology backward not built yet");
+int hp_morph3d_backward(const hp_volume* in, const hp_volume* gout, int is_dilate, hp_se se,
+                        int radius, hp_volume* gin, int accumulate, void* stream) {
+  if (!in || !in->data || !gout || !gout->data || !gin || !gin->data)
+    return set_error(HP_ERR_INVALID_ARG, "morphology backward: null argument");
+  if (in->loc != HP_DEVICE || gout->loc != HP_DEVICE || gin->loc != HP_DEVICE)
+    return set_error(HP_ERR_UNSUPPORTED, "morphology backward runs on device volumes only");
+  if (gout->dtype != HP_F32 || gin->dtype != HP_F32)
+    return set_error(HP_ERR_UNSUPPORTED, "morphology backward: gradients must be f32");
+  if (gout->nx != in->nx || gout->ny != in->ny || gout->nz != in->nz || gin->nx != in->nx ||
+      gin->ny != in->ny || gin->nz != in->nz)
+    return set_error(HP_ERR_INVALID_ARG, "morphology backward: extents differ");
+  if (se != HP_SE_CUBE && se != HP_SE_BALL) return set_error(HP_ERR_INVALID_ARG, "unknown structuring element");
+  if (radius < 0 || radius > kMaxMorphR) return set_error(HP_ERR_INVALID_ARG, "radius must be in [0, 16]");
+  const int64_t dims[3] = {in->nz, in->ny, in->nx};
+  const int64_t total = dims[0] * dims[1] * dims[2];
+  if (total >= (int64_t)1 << 31)
+    return set_error(HP_ERR_UNSUPPORTED, "morphology backward: more than 2^31 - 1 voxels");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ab = sizeof(int32_t) * (size_t)total;
+  int st = check_scratch_budget(ab);
+  if (st != HP_OK) return st;
+  Scratch sc(s);
+  int32_t* arg = nullptr;
+  cudaError_t e = sc.alloc((void**)&arg, ab);
+  if (e != cudaSuccess) return cuda_fail(e, "morphology backward scratch");
+  e = launch_morph_arg(in->data, in->dtype, dims, se == HP_SE_BALL, radius, is_dilate, arg, s);
+  if (e == cudaSuccess)
+    e = launch_morph_gather(arg, static_cast<const float*>(gout->data), static_cast<float*>(gin->data),
+                            dims, radius, accumulate, s);
+  if (e != cudaSuccess) return cuda_fail(e, "morphology backward launch");
+  return HP_OK;
 }
 
 int hp_release_cache(void) {

@@ -1,0 +1,193 @@
+// Adjoint kernels behind autograd: the transpose of the separable
+// Gaussian / derivative filters with reflect boundaries, the chain rule of
+// the gradient magnitude, and the subgradient of grayscale erosion and
+// dilation (Harpia Sec. III-C filters, differentiated for learned feature
+// pipelines).
+//
+// Filter transpose, per axis of length n with taps g(k), k in [-r, r]: the
+// forward map is y = K E x (E extends x by reflection to [-r, n-1+r], K is
+// the valid convolution y[i] = sum_k g(k) u[i-k]). Its transpose E^T K^T is
+// computed as a gather: for output i, sum over the pre-images j of i under
+// the reflection (j in [-r, n-1+r], R(j) = i) of t[j] = sum_k g(k) w[j+k],
+// w zero outside [0, n). The 3D transpose of Z Y X is X^T Y^T Z^T.
+//
+// Morphology: an argmin (argmax) map first records, per output p, the source
+// q* = R(p +- o) holding the extreme value, ties to the smallest linear
+// index; a gather then sums, per source q, the output gradients of every p
+// within the structuring element's reach whose recorded source is q. Both
+// passes are deterministic (no atomics).
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "hp_device.cuh"
+#include "hp_internal.h"
+
+namespace hp {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ float load_as_f32(const void* p, int dt, int64_t i) {
+  switch (dt) {
+    case HP_U8: return (float)static_cast<const uint8_t*>(p)[i];
+    case HP_U16: return (float)static_cast<const uint16_t*>(p)[i];
+    case HP_F16: return __half2float(static_cast<const __half*>(p)[i]);
+    default: return static_cast<const float*>(p)[i];
+  }
+}
+
+struct AxisTaps {
+  float g[kMaxTaps];
+};
+
+// dst = (axis transpose of src); dst += when accumulate.
+__global__ void k_axis_adjoint(const float* __restrict__ src, float* __restrict__ dst, int64_t n0,
+                               int64_t n1, int64_t n2, int axis, const AxisTaps taps, int r,
+                               int accumulate) {
+  const int64_t total = n0 * n1 * n2;
+  const int64_t n = axis == 0 ? n0 : (axis == 1 ? n1 : n2);
+  const int64_t stride = axis == 2 ? 1 : (axis == 1 ? n2 : n1 * n2);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
+    const int64_t i = axis == 0 ? z : (axis == 1 ? y : x);
+    const float* line = src + (q - i * stride);
+    float acc = 0.0f;
+    // pre-images j of i in [-r, n-1+r]: i + 2n m and -1 - i + 2n m
+    for (int64_t m = -((r + 2 * n) / (2 * n)); m <= (r + 2 * n) / (2 * n); ++m) {
+      for (int s = 0; s < 2; ++s) {
+        const int64_t j = (s == 0 ? i : -1 - i) + 2 * n * m;
+        if (j < -r || j > n - 1 + r) continue;
+        if (reflect(j, n) != i) continue;
+        // t[j] = sum_k g(k) w[j + k]
+        for (int k = -r; k <= r; ++k) {
+          const int64_t s2 = j + k;
+          if (s2 >= 0 && s2 < n) acc = fmaf(taps.g[k + r], line[s2 * stride], acc);
+        }
+      }
+    }
+    dst[q] = accumulate ? dst[q] + acc : acc;
+  }
+}
+
+// v = w * D_a / GM (0 where GM = 0), GM = sqrt(Dx^2 + Dy^2 + Dz^2) formed
+// as in the forward bank.
+__global__ void k_gm_chain(const float* __restrict__ w, const float* __restrict__ dz,
+                           const float* __restrict__ dy, const float* __restrict__ dx,
+                           const float* __restrict__ da, float* __restrict__ v, int64_t total) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float gm = sqrtf(fmaf(dz[q], dz[q], fmaf(dy[q], dy[q], dx[q] * dx[q])));
+    v[q] = gm > 0.0f ? w[q] * da[q] / gm : 0.0f;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ float morph_val(const T* p, int64_t i);
+template <>
+__device__ __forceinline__ float morph_val<float>(const float* p, int64_t i) {
+  return p[i];
+}
+
+// Extreme source per output: arg[p] = q* (int32 linear index).
+__global__ void k_morph_arg(const void* __restrict__ in, int dt, int64_t n0, int64_t n1,
+                            int64_t n2, int ball, int rad, int is_dilate,
+                            int32_t* __restrict__ arg) {
+  const int64_t total = n0 * n1 * n2;
+  const int sg = is_dilate ? -1 : 1;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = p % n2, y = (p / n2) % n1, z = p / (n1 * n2);
+    int64_t best_q = -1;
+    float best = 0.0f;
+    for (int dz = -rad; dz <= rad; ++dz) {
+      const int64_t sz = reflect(z + sg * dz, n0);
+      for (int dy = -rad; dy <= rad; ++dy) {
+        const int64_t sy = reflect(y + sg * dy, n1);
+        for (int dx = -rad; dx <= rad; ++dx) {
+          if (ball && dz * dz + dy * dy + dx * dx > rad * rad) continue;
+          const int64_t sx = reflect(x + sg * dx, n2);
+          const int64_t q = (sz * n1 + sy) * n2 + sx;
+          const float v = load_as_f32(in, dt, q);
+          const bool better = best_q < 0 || (is_dilate ? v > best : v < best) ||
+                              (v == best && q < best_q);
+          if (better) {
+            best = v;
+            best_q = q;
+          }
+        }
+      }
+    }
+    arg[p] = (int32_t)best_q;
+  }
+}
+
+// gin[q] (+)= sum of gout[p] over p in q + [-rad, rad]^3 with arg[p] == q,
+// p in increasing linear order.
+__global__ void k_morph_gather(const int32_t* __restrict__ arg, const float* __restrict__ gout,
+                               float* __restrict__ gin, int64_t n0, int64_t n1, int64_t n2,
+                               int rad, int accumulate) {
+  const int64_t total = n0 * n1 * n2;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
+    float acc = 0.0f;
+    for (int64_t pz = max((int64_t)0, z - rad); pz <= min(n0 - 1, z + rad); ++pz)
+      for (int64_t py = max((int64_t)0, y - rad); py <= min(n1 - 1, y + rad); ++py)
+        for (int64_t px = max((int64_t)0, x - rad); px <= min(n2 - 1, x + rad); ++px) {
+          const int64_t p = (pz * n1 + py) * n2 + px;
+          if (arg[p] == (int32_t)q) acc += gout[p];
+        }
+    gin[q] = accumulate ? gin[q] + acc : acc;
+  }
+}
+
+unsigned grid_for(int64_t total) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + kBlock - 1) / kBlock,
+                                                          (int64_t)num_sms() * 16));
+}
+
+}  // namespace
+
+// Separable transpose: dst (+)= X^T Y^T Z^T w for taps (z, y, x) of radius r.
+// Uses two scratch volumes t1, t2 of the same shape.
+cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3],
+                               const Taps& taps, float* t1, float* t2, int accumulate,
+                               cudaStream_t s) {
+  const int64_t total = dims[0] * dims[1] * dims[2];
+  AxisTaps a;
+  for (int ax = 0; ax < 3; ++ax) {
+    for (int k = 0; k < kMaxTaps; ++k) a.g[k] = taps.w[ax][k];
+    const float* src = ax == 0 ? w : (ax == 1 ? t1 : t2);
+    float* out = ax == 0 ? t1 : (ax == 1 ? t2 : dst);
+    k_axis_adjoint<<<grid_for(total), kBlock, 0, s>>>(src, out, dims[0], dims[1], dims[2], ax, a,
+                                                     taps.r, ax == 2 ? accumulate : 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gm_chain(const float* w, const float* dz, const float* dy, const float* dx,
+                            const float* da, float* v, int64_t total, cudaStream_t s) {
+  k_gm_chain<<<grid_for(total), kBlock, 0, s>>>(w, dz, dy, dx, da, v, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_morph_arg(const void* in, int dt, const int64_t dims[3], int ball, int rad,
+                             int is_dilate, int32_t* arg, cudaStream_t s) {
+  const int64_t total = dims[0] * dims[1] * dims[2];
+  k_morph_arg<<<grid_for(total), kBlock, 0, s>>>(in, dt, dims[0], dims[1], dims[2], ball, rad,
+                                                 is_dilate, arg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_morph_gather(const int32_t* arg, const float* gout, float* gin,
+                                const int64_t dims[3], int rad, int accumulate, cudaStream_t s) {
+  const int64_t total = dims[0] * dims[1] * dims[2];
+  k_morph_gather<<<grid_for(total), kBlock, 0, s>>>(arg, gout, gin, dims[0], dims[1], dims[2],
+                                                    rad, accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace hp

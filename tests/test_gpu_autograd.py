@@ -1,0 +1,133 @@
+"""GPU parity of the hand-written backward passes (torch.autograd.Function
+over hp_filterbank3d_adjoint and hp_morph3d_backward): against the oracle's
+adjoint, against central finite differences (h = 1e-3) of the FP64 oracle
+forward on 64 random voxels, and the dot-product identity at 256^3."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+hp = pytest.importorskip("paper_2511_11890_b300")
+from paper_2511_11890_b300 import autograd as hpa  # noqa: E402
+
+SIGMAS = (0.7, 1.0, 2.0, 4.0)
+BANK = [(k, s) for s in SIGMAS for k in (hp.G, hp.GM, hp.LOG)]
+OK = {hp.G: oracle.G, hp.GM: oracle.GM, hp.LOG: oracle.LOG}
+RHO = 2   # erosion with the 5^3 cube
+
+
+def _loss_grad(f, ws):
+    x = to_dev(f).requires_grad_(True)
+    feats = hpa.bank_and_erosion(x, BANK, "cube", RHO)
+    loss = sum((F * to_dev(w)).sum() for F, w in zip(feats, ws))
+    loss.backward()
+    return to_np(x.grad)
+
+
+def _weights(shape, seed0):
+    return [synth.normal_field(shape, seed0 + i) for i in range(len(BANK) + 1)]
+
+
+def test_grad_vs_oracle_adjoint():
+    shape = (40, 44, 48)
+    f = synth.spheres(shape, 30, synth.SEED_BASE + 4)
+    ws = _weights(shape, synth.SEED_BASE + 40)
+    g = _loss_grad(f, ws)
+    ref = oracle.filterbank3d_vjp(f, [(OK[k], s) for k, s in BANK],
+                                  [w.astype(np.float64) for w in ws[:-1]])
+    ref += oracle.morph3d_vjp(f, oracle.SE_CUBE, RHO, False, ws[-1].astype(np.float64))
+    err = np.abs(g - ref).max()
+    assert err <= 1e-4 * np.abs(ref).max(), err
+
+
+def test_morph_backward_tie_rule_and_dilation():
+    shape = (12, 13, 14)
+    f = np.full(shape, 3.0, np.float32)          # every source ties
+    f[5:8, 5:8, 5:8] = np.random.default_rng(0).standard_normal((3, 3, 3)).astype(np.float32)
+    w = synth.normal_field(shape, 7)
+    for dil, se, rad in [(False, "cube", 2), (True, "ball", 2), (False, "ball", 3)]:
+        g = to_np(hp.morph3d_backward(to_dev(f), to_dev(w), dil, se, rad))
+        ref = oracle.morph3d_vjp(f, oracle.SE_CUBE if se == "cube" else oracle.SE_BALL, rad, dil,
+                                 w.astype(np.float64))
+        assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def _fd_loss(f64, q, ws, h):
+    """FP64 loss change around voxel q, summed only over the outputs q can
+    reach (radius 12 for the bank, 2 for the erosion)."""
+    n = f64.shape
+    rmax = max(oracle.radius(s) for s in SIGMAS)
+    lo = [max(0, c - rmax) for c in q]
+    hi = [min(n[a], q[a] + rmax + 1) for a in range(3)]
+    out_shape = tuple(hi[a] - lo[a] for a in range(3))
+    sl = tuple(slice(lo[a], hi[a]) for a in range(3))
+    vals = []
+    for sgn in (1, -1):
+        g = f64.copy()
+        g[q] += sgn * h
+        outs = oracle.filterbank3d(g, [(OK[k], s) for k, s in BANK], out_lo=lo, out_shape=out_shape)
+        e = oracle.erode3d(g, oracle.SE_CUBE, RHO, out_lo=lo, out_shape=out_shape)
+        vals.append(sum((o * w[sl]).sum() for o, w in zip(outs, ws[:-1])) + (e * ws[-1][sl]).sum())
+    return (vals[0] - vals[1]) / (2 * h)
+
+
+def _near_tie(f64, q, h):
+    """True if for some erosion output p that reads q, f(q) lies within 2h of
+    the smallest value among p's other sources: there the +-h difference
+    crosses the kink of the min and is not its subgradient."""
+    n = f64.shape
+    qz, qy, qx = q
+    for pz in range(max(0, qz - RHO), min(n[0], qz + RHO + 1)):
+        for py in range(max(0, qy - RHO), min(n[1], qy + RHO + 1)):
+            for px in range(max(0, qx - RHO), min(n[2], qx + RHO + 1)):
+                srcs = {(oracle.reflect(pz + dz, n[0]), oracle.reflect(py + dy, n[1]),
+                         oracle.reflect(px + dx, n[2]))
+                        for dz in range(-RHO, RHO + 1) for dy in range(-RHO, RHO + 1)
+                        for dx in range(-RHO, RHO + 1)}
+                if q not in srcs:
+                    continue
+                others = min(f64[s] for s in srcs if s != q)
+                if abs(f64[q] - others) <= 2 * h:
+                    return True
+    return False
+
+
+def test_grad_vs_finite_differences_64_voxels_256():
+    """The 256^3 float32 spheres volume: GPU gradient of the 12-filter bank
+    plus erosion against central differences of the FP64 oracle forward."""
+    n = 256
+    f = synth.spheres(n, 320, synth.SEED_BASE + 4)
+    ws = _weights(f.shape, synth.SEED_BASE + 40)
+    g = _loss_grad(f, ws)
+    f64 = f.astype(np.float64)
+    ws64 = [w.astype(np.float64) for w in ws]
+    h = 1e-3
+    qs = synth.pick(64, f.size, synth.SEED_BASE + 5)
+    checked = skipped = 0
+    for qi in qs:
+        q = tuple(int(v) for v in np.unravel_index(int(qi), f.shape))
+        if _near_tie(f64, q, h):
+            skipped += 1
+            continue
+        fd = _fd_loss(f64, q, ws64, h)
+        assert abs(fd - g[q]) <= 1e-3 * max(1.0, abs(fd)), (q, fd, g[q])
+        checked += 1
+    assert checked >= 48, (checked, skipped)
+
+
+def test_dot_product_identity_256():
+    """<J v, w> = <v, J^T w> for the linear bank filters at full size (FP32)."""
+    n = 256
+    v = to_dev(synth.normal_field((n, n, n), 11))
+    w = [to_dev(synth.normal_field((n, n, n), 12 + i)) for i in range(3)]
+    filt = [(hp.G, 2.0), (hp.LOG, 1.0), (hp.G, 4.0)]
+    outs = hp.filterbank3d(v, filt, out_dtype=hp.HP_F32)
+    lhs = sum(float((o.double() * ww.double()).sum()) for o, ww in zip(outs, w))
+    gin = hp.filterbank3d_adjoint(v, w, filt)
+    rhs = float((v.double() * gin.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1.0), (lhs, rhs)

@@ -170,6 +170,29 @@ int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
 int hp_morph3d_backward(const hp_volume* in, const hp_volume* gout, int is_dilate, hp_se se,
                         int radius, hp_volume* gin, int accumulate, void* stream);
 
+/* Allocation-free variant of hp_morph3d_backward (same arguments, same
+ * result). The paper has no counterpart; it exists for callers that must not
+ * allocate device memory while this step runs -- for example code that runs
+ * inside a fixed memory arena, a loop with real-time limits that may not
+ * enter the allocator, or a process whose device memory is already handed to
+ * another pool. Instead of a per-call scratch buffer it uses one int32 index
+ * array of 16,777,216 entries (64 MiB, enough for 256^3 voxels) that the
+ * library holds in device memory on every GPU that loads it, until the
+ * process exits. Larger volumes return HP_ERR_UNSUPPORTED; use
+ * hp_morph3d_backward for them.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress), which may also load the library's device code;
+ *     make that first call before any stream capture.
+ *   - Every call uses the same array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and give wrong results. Order them.
+ *   - No state needs clearing between calls: each call rewrites every index
+ *     it later reads.
+ *   - The call itself performs no cudaMalloc, cudaFree or other device
+ *     allocation. */
+int hp_morph3d_backward_noalloc(const hp_volume* in, const hp_volume* gout, int is_dilate,
+                                hp_se se, int radius, hp_volume* gin, int accumulate,
+                                void* stream);
+
 /* Chunk planner (Sec. III-D step 2), host only, no device work. Splits an
  * (nz, ny, nx) volume into bricks whose core boxes tile it exactly; box i's
  * input box is the hull of the reflected sources of its core grown by

@@ -25,7 +25,8 @@ HP_FILTER_G, HP_FILTER_GM, HP_FILTER_LOG = 0, 1, 2
 EXPORTS = [
     "hp_volume_create", "hp_volume_destroy", "hp_set_memory_budget", "hp_get_memory_budget",
     "hp_gaussian3d", "hp_filterbank3d", "hp_filterbank3d_bricks", "hp_erode3d", "hp_dilate3d",
-    "hp_threshold3d", "hp_filterbank3d_adjoint", "hp_morph3d_backward", "hp_plan_bricks",
+    "hp_threshold3d", "hp_filterbank3d_adjoint", "hp_morph3d_backward",
+    "hp_morph3d_backward_noalloc", "hp_plan_bricks",
     "hp_stream_status", "hp_release_cache", "hp_get_stats", "hp_last_error", "hp_version",
 ]
 
@@ -55,7 +56,7 @@ class hp_stats(ctypes.Structure):
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libhp.so not built ({LIB_PATH}); run "
-                          "`python -m paper_2511_11890_b300.build`")
+                          "`python paper_2511_11890_b300/build.py`")
     lib = ctypes.CDLL(LIB_PATH)
     vp, i64, i, d, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     pvp = ctypes.POINTER(ctypes.c_void_p)
@@ -72,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "hp_threshold3d": [vp, vp, d, vp],
         "hp_filterbank3d_adjoint": [vp, pvp, ctypes.POINTER(hp_filter), i, vp, vp],
         "hp_morph3d_backward": [vp, vp, i, i, i, vp, i, vp],
+        "hp_morph3d_backward_noalloc": [vp, vp, i, i, i, vp, i, vp],
         "hp_plan_bricks": [i64, i64, i64, i, sz, sz, sz, i, i, ctypes.POINTER(hp_box),
                            ctypes.POINTER(hp_box), i, ctypes.POINTER(i)],
         "hp_stream_status": [vp],

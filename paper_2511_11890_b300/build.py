@@ -1,6 +1,6 @@
 """Build libhp.so (the C-ABI library with the sm_103a kernels) in-tree.
 
-    python -m paper_2511_11890_b300.build [--force]
+    python paper_2511_11890_b300/build.py [--force]
 
 Each CUDA source is compiled with nvcc for sm_103a only
 (-gencode arch=compute_103a,code=sm_103a, -lineinfo, -O3, no fast math)

@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <string>
 
 #include "hp_device.cuh"
 #include "hp_internal.h"
@@ -190,4 +191,73 @@ cudaError_t launch_morph_gather(const int32_t* arg, const float* gout, float* gi
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------
+// Allocation-free variant of the morphology subgradient.
+//
+// Some callers cannot allocate device memory while they run this step: code
+// inside a fixed memory arena or a real-time loop that must not touch the
+// allocator, or a host that has handed all device memory to another pool.
+// For them the per-voxel source index lives in a fixed array that the
+// library owns for the life of the process (every GPU that loads the
+// library holds it until exit), so the call itself allocates nothing.
+namespace {
+constexpr int64_t kNoAllocMaxVoxels = int64_t(1) << 24;  // 256^3 voxels, 64 MiB
+static __device__ __align__(256) int32_t g_noalloc_arg[kNoAllocMaxVoxels];
+int32_t* g_noalloc_ptr[64];  // device address per device, set on first use
+}  // namespace
+
 }  // namespace hp
+
+using namespace hp;
+
+struct hp_volume {
+  void* data;
+  int dtype;
+  int loc;
+  int64_t nx, ny, nz;
+};
+
+extern "C" int hp_morph3d_backward_noalloc(const hp_volume* in, const hp_volume* gout,
+                                           int is_dilate, hp_se se, int radius, hp_volume* gin,
+                                           int accumulate, void* stream) {
+  if (!in || !in->data || !gout || !gout->data || !gin || !gin->data)
+    return set_error(HP_ERR_INVALID_ARG, "morphology backward (no-alloc): null argument");
+  if (in->loc != HP_DEVICE || gout->loc != HP_DEVICE || gin->loc != HP_DEVICE)
+    return set_error(HP_ERR_UNSUPPORTED, "morphology backward (no-alloc): device volumes only");
+  if (gout->dtype != HP_F32 || gin->dtype != HP_F32)
+    return set_error(HP_ERR_UNSUPPORTED, "morphology backward (no-alloc): gradients must be f32");
+  if (gout->nx != in->nx || gout->ny != in->ny || gout->nz != in->nz || gin->nx != in->nx ||
+      gin->ny != in->ny || gin->nz != in->nz)
+    return set_error(HP_ERR_INVALID_ARG, "morphology backward (no-alloc): extents differ");
+  if (se != HP_SE_CUBE && se != HP_SE_BALL)
+    return set_error(HP_ERR_INVALID_ARG, "unknown structuring element");
+  if (radius < 0 || radius > kMaxMorphR) return set_error(HP_ERR_INVALID_ARG, "radius must be in [0, 16]");
+  const int64_t dims[3] = {in->nz, in->ny, in->nx};
+  const int64_t total = dims[0] * dims[1] * dims[2];
+  if (total > kNoAllocMaxVoxels)
+    return set_error(HP_ERR_UNSUPPORTED,
+                     "morphology backward (no-alloc): volume has more than 16777216 voxels "
+                     "(the size of the library's fixed index array); use hp_morph3d_backward");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return set_error(HP_ERR_UNSUPPORTED, "device index above 63");
+  if (!g_noalloc_ptr[dev]) {
+    // host code only sees a stand-in for the array; its device address is
+    // looked up once per device, with that device current
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_arg);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc index array)");
+    g_noalloc_ptr[dev] = static_cast<int32_t*>(p);
+  }
+  int32_t* arg = g_noalloc_ptr[dev];
+  cudaStream_t s = (cudaStream_t)stream;
+  // every index the gather reads is written by the argmin pass first, so
+  // nothing in the shared array needs clearing between calls
+  e = launch_morph_arg(in->data, in->dtype, dims, se == HP_SE_BALL, radius, is_dilate, arg, s);
+  if (e == cudaSuccess)
+    e = launch_morph_gather(arg, static_cast<const float*>(gout->data),
+                            static_cast<float*>(gin->data), dims, radius, accumulate, s);
+  if (e != cudaSuccess) return cuda_fail(e, "morphology backward (no-alloc) launch");
+  return HP_OK;
+}

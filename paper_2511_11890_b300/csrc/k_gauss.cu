@@ -39,13 +39,15 @@ constexpr int kTY = 32;
 constexpr int kBZ = 8;
 constexpr int kNS = 4;
 constexpr int kThreads = 256;
-constexpr int kXS = kTX + 4;  // X row stride: 4 mod 8 floats keeps 16-byte stores conflict-free
+constexpr int kXS = kTX + 4;  // X row stride (floats), 16-byte aligned rows
+
+typedef unsigned long long u64;
 
 struct GaussParams {
   Job job;
-  float wz[kMaxTaps];
-  float wy[kMaxTaps];
-  float wx[kMaxTaps];
+  // taps per axis (z, y, x), each duplicated into an FP32 pair so packed
+  // fmas take them as one 64-bit operand
+  u64 w2[3][2 * kMaxR + 1];
   int r;
   int zchunk;
   int tiles_x;
@@ -55,124 +57,168 @@ struct GaussParams {
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// Smallest row stride >= n floats that is 4 mod 8: two rows read by one
-// 8-thread phase of 16-byte loads then land in disjoint bank groups.
-__host__ __device__ constexpr int patch_stride(int n) {
+inline uint32_t __float_as_uint_host(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  return u;
+}
+
+// Row-pair stride (in FP32 pairs) of the interleaved patch: 2 mod 4 puts the
+// 16-byte loads of 8 consecutive row pairs into 8 distinct bank groups.
+__host__ __device__ constexpr int pair_stride(int n) {
   int f = n;
-  while (f % 8 != 4) ++f;
+  while (f % 4 != 2) ++f;
   return f;
 }
 
 // Geometry of the z-march kernel for radius R.
-//   F  (FP32 patch, double-buffered): col c <-> x = cx0 - R4 + c, rows
-//      <-> y = cy0 - R + row. R4 = R rounded up to 4 keeps the x-pass
-//      window loads 16-byte aligned.
-//   X  (x-pass output, double-buffered): [BH][kXS].
+//   F2 (FP32 patch, row pairs interleaved, double-buffered): element
+//      (rp, c) is the pair (row 2rp, row 2rp+1) at column c; column c <->
+//      x = cx0 - R4 + c, row <-> y = cy0 - R + row. R4 = R rounded up to 4
+//      keeps the x-pass window loads 16-byte aligned.
+//   X  (x-pass output, double-buffered): [BH][kXS] floats.
 //   ring: kBZ + 2R planes of y-pass output [TY][TX].
 template <int R>
 struct ZmGeom {
   static constexpr int R4 = round_up(R, 4);
-  static constexpr int WL = round_up(R4 + R + 8, 4);  // x window (floats) for 8 outputs
-  static constexpr int FWN = (kTX - 8) + WL;           // F columns read
-  static constexpr int FW = patch_stride(FWN);
+  static constexpr int WL = round_up(R4 + R + 8, 4);  // x window (columns) for 8 outputs
+  static constexpr int FWN = (kTX - 8) + WL;           // columns read
   static constexpr int BH = kTY + 2 * R;
-  static constexpr int NC = (FWN + 31) / 32;           // F columns per lane
+  static constexpr int RP = BH / 2;                     // row pairs
+  static constexpr int FW2 = pair_stride(FWN);
+  static constexpr int CP = FWN / 2;                    // column pairs per row pair
+  static constexpr int NI = (RP * CP + kThreads - 1) / kThreads;  // staging items per thread
+  static constexpr int NC = (FWN + 31) / 32;            // columns per lane (face path)
   static constexpr int NRING = kBZ + 2 * R;
-  static constexpr int FSZ = BH * FW;
+  static constexpr int FSZ2 = RP * FW2;                 // in FP32 pairs
   static constexpr int XSZ = BH * kXS;
-  // bytes after the TMA stages
-  static constexpr int TAIL = (2 * FSZ + 2 * XSZ + NRING * kTY * kTX) * 4 + BH * 4;
-  static_assert(FW >= FWN && FW % 8 == 4, "FP32 patch row stride must be 4 mod 8 floats");
-  static_assert(FWN % 4 == 0, "patch width must be a multiple of 4");
+  static constexpr int TAIL = 2 * FSZ2 * 8 + (2 * XSZ + NRING * kTY * kTX) * 4 + BH * 4;
+  static_assert(FWN % 4 == 0 && BH % 2 == 0, "patch shape");
 };
 
 // Per-dtype TMA box geometry: left halo ra (R rounded up to 16 bytes) and
 // width bw (elements); raw col c <-> x = cx0 - ra + c.
-__host__ __device__ inline void box_geom(int r, int es, int* ra, int* bw) {
+__host__ __device__ constexpr void box_geom(int r, int es, int* ra, int* bw) {
   const int al = 16 / es;
   *ra = round_up(r, al);
   *bw = round_up(kTX + *ra + r, al);
 }
 
-__host__ __device__ inline int stage_bytes(int r, int es) {
-  int ra, bw;
+__host__ __device__ constexpr int stage_bytes(int r, int es) {
+  int ra = 0, bw = 0;
   box_geom(r, es, &ra, &bw);
   return round_up(bw * (kTY + 2 * r) * es, 128);
 }
 
 template <int R>
-__host__ __device__ inline int zm_smem_bytes(int es) {
+__host__ __device__ constexpr int zm_smem_bytes(int es) {
   return 128 + kNS * stage_bytes(R, es) + ZmGeom<R>::TAIL;
 }
 
-// One plane of input -> FP32 patch F. Sources are looked up in per-CTA
-// tables that already resolve the reflect boundary: srow[row] is the raw
+// Two consecutive elements -> two floats. Integers use the exact 2^23 bias:
+// a byte permute builds 0x4B00_0000 | v, then one packed subtract.
+template <typename T>
+__device__ __forceinline__ float2 load2_f32(const T* p);
+template <>
+__device__ __forceinline__ float2 load2_f32<uint16_t>(const uint16_t* p) {
+  const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+  const float a = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7410));
+  const float b = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7432));
+  return make_float2(a - 8388608.0f, b - 8388608.0f);
+}
+template <>
+__device__ __forceinline__ float2 load2_f32<uint8_t>(const uint8_t* p) {
+  const uint32_t w = *reinterpret_cast<const uint16_t*>(p);
+  const float a = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440));
+  const float b = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7441));
+  return make_float2(a - 8388608.0f, b - 8388608.0f);
+}
+template <>
+__device__ __forceinline__ float2 load2_f32<__half>(const __half* p) {
+  return __half22float2(*reinterpret_cast<const __half2*>(p));
+}
+template <>
+__device__ __forceinline__ float2 load2_f32<float>(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+
+// Interior tiles: no reflection. Item k of this thread covers row pair rp,
+// columns 2c, 2c+1: two 2-element loads (rows 2rp, 2rp+1), one 16-byte store
+// of the interleaved pairs. Offsets were precomputed per CTA.
+template <typename TIN, int R>
+__device__ __forceinline__ void stage_interior(float2* F2, const unsigned char* rawb, int bw,
+                                               const int (&roff)[ZmGeom<R>::NI],
+                                               const int (&foff)[ZmGeom<R>::NI]) {
+  using G = ZmGeom<R>;
+  const TIN* raw = reinterpret_cast<const TIN*>(rawb);
+#pragma unroll
+  for (int k = 0; k < G::NI; ++k) {
+    if (foff[k] >= 0) {
+      const float2 a = load2_f32<TIN>(raw + roff[k]);
+      const float2 b = load2_f32<TIN>(raw + roff[k] + bw);
+      *reinterpret_cast<float4*>(F2 + foff[k]) = make_float4(a.x, b.x, a.y, b.y);
+    }
+  }
+}
+
+// Face tiles (and the cooperative-load path): element by element through
+// the source tables, which resolve the reflection; srow[row] is the raw
 // stage row (TMA) or box row (global loads), scol[k] the column of lane
 // column lane + 32k; -1 marks taps no stored output uses.
 template <typename TIN, int R>
-__device__ __forceinline__ void stage_from_tma(float* Fb, const unsigned char* rawb, int bw,
-                                               const int* srow, const int (&scol)[ZmGeom<R>::NC],
-                                               int warp, int lane) {
+__device__ __forceinline__ void stage_tables(float2* F2, const TIN* plane, int64_t pitch,
+                                             bool ok_plane, const int* srow,
+                                             const int (&scol)[ZmGeom<R>::NC], int warp,
+                                             int lane) {
   using G = ZmGeom<R>;
-  const TIN* raw = reinterpret_cast<const TIN*>(rawb);
+  float* F = reinterpret_cast<float*>(F2);
   for (int row = warp; row < G::BH; row += kThreads / 32) {
-    const int sr = srow[row];
+    const int sr = ok_plane ? srow[row] : -1;
+    float* dst = F + (row >> 1) * (2 * G::FW2) + (row & 1);
 #pragma unroll
     for (int k = 0; k < G::NC; ++k) {
       const int col = lane + 32 * k;
       if (col < G::FWN) {
         const int sc = scol[k];
-        Fb[row * G::FW + col] = (sr >= 0 && sc >= 0) ? to_f32<TIN>(raw[sr * bw + sc]) : 0.0f;
+        dst[2 * col] = (sr >= 0 && sc >= 0) ? to_f32<TIN>(plane[sr * pitch + sc]) : 0.0f;
       }
     }
   }
 }
 
-// Interior tiles: no reflection, F col c <-> raw col c + (ra - R4); four
-// columns per item with one vector load (16-, 8- or 4-byte aligned since
-// ra - R4 is a multiple of 4 elements) and one 16-byte store.
-template <typename TIN, int R>
-__device__ __forceinline__ void stage_from_tma_interior(float* Fb, const unsigned char* rawb,
-                                                        int ra, int bw, int tid) {
-  using G = ZmGeom<R>;
-  constexpr int Q = G::FWN / 4;
-  const TIN* raw = reinterpret_cast<const TIN*>(rawb) + (ra - G::R4);
-  for (int it = tid; it < G::BH * Q; it += kThreads) {
-    const int row = it / Q, q = it - row * Q;
-    *reinterpret_cast<float4*>(Fb + row * G::FW + 4 * q) = load4_f32<TIN>(raw + row * bw + 4 * q);
-  }
-}
-
-template <typename TIN, int R>
-__device__ __forceinline__ void stage_from_global(float* Fb, const Job& J, int64_t sz,
-                                                  const int* srow,
-                                                  const int (&scol)[ZmGeom<R>::NC], int warp,
-                                                  int lane) {
-  using G = ZmGeom<R>;
-  const TIN* in = static_cast<const TIN*>(J.in.ptr);
-  const bool zok = sz >= 0 && sz < J.in.dims[0];
-  const TIN* plane = in + sz * J.in.dims[1] * J.in.dims[2];
-  for (int row = warp; row < G::BH; row += kThreads / 32) {
-    const int sr = srow[row];
-#pragma unroll
-    for (int k = 0; k < G::NC; ++k) {
-      const int col = lane + 32 * k;
-      if (col < G::FWN) {
-        const int sc = scol[k];
-        Fb[row * G::FW + col] = (zok && sr >= 0 && sc >= 0)
-                                    ? to_f32<TIN>(plane[(int64_t)sr * J.in.dims[2] + sc])
-                                    : 0.0f;
-      }
-    }
-  }
-}
-
+// Face tiles: after the vectorised staging (out-of-volume cells hold the
+// TMA zero fill), overwrite the cells outside the volume with their
+// reflected sources, which lie inside the volume and inside the patch.
+// frow/fcol map patch rows/columns to their source rows/columns (identity
+// inside the volume, -1 where no stored output needs the cell); brow/bcol
+// list the rows/columns that are outside.
 template <int R>
+__device__ __forceinline__ void fix_faces(float2* F2, const int* frow, const int* fcol,
+                                          const int* brow, int nbr, const int* bcol, int nbc,
+                                          int tid) {
+  using G = ZmGeom<R>;
+  float* F = reinterpret_cast<float*>(F2);
+  auto cell = [&](int r, int c) -> float& { return F[(r >> 1) * (2 * G::FW2) + 2 * c + (r & 1)]; };
+  for (int i = tid; i < nbr * G::FWN; i += kThreads) {
+    const int r = brow[i / G::FWN], c = i % G::FWN;
+    const int sr = frow[r], sc = fcol[c];
+    cell(r, c) = (sr >= 0 && sc >= 0) ? cell(sr, sc) : 0.0f;
+  }
+  for (int i = tid; i < nbc * G::BH; i += kThreads) {
+    const int c = bcol[i / G::BH], r = i % G::BH;
+    const int sr = frow[r], sc = fcol[c];
+    cell(r, c) = (sr >= 0 && sc >= 0) ? cell(sr, sc) : 0.0f;
+  }
+}
+
+template <int R, typename TIN>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gauss_zm(const __grid_constant__ GaussParams P, const __grid_constant__ CUtensorMap tmap) {
   using G = ZmGeom<R>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
+  __shared__ int s_frow[G::BH], s_fcol[G::FWN], s_brow[G::BH], s_bcol[G::FWN];
+  __shared__ int s_nbr, s_nbc;
 
   const Job& J = P.job;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -185,8 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nout = (int)(cz1 - cz0);
   const int total = nout + 2 * R;  // input planes cz0-R .. cz1+R-1
   const int64_t Gz = J.gdims[0], Gy = J.gdims[1], Gx = J.gdims[2];
-  const int dt = J.in.dtype;
-  const int es = dt == HP_U8 ? 1 : (dt == HP_F32 ? 4 : 2);
+  constexpr int es = sizeof(TIN);
   int ra, bw;
   box_geom(R, es, &ra, &bw);
   const int sbytes = stage_bytes(R, es);
@@ -196,8 +241,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   unsigned char* stages = smem + 128;
-  float* F = reinterpret_cast<float*>(stages + kNS * sbytes);
-  float* X = F + 2 * G::FSZ;
+  float2* F2 = reinterpret_cast<float2*>(stages + kNS * sbytes);
+  float* X = reinterpret_cast<float*>(F2 + 2 * G::FSZ2);
   float* ring = X + 2 * G::XSZ;
   int* srow = reinterpret_cast<int*>(ring + G::NRING * kTY * kTX);
 
@@ -229,6 +274,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     scol[k] = col < G::FWN ? v : -1;
   }
+  // interior staging items: raw element offset of (row 2rp, col 2c) and the
+  // F2 offset of (rp, 2c); F col c <-> raw col c + ra - R4
+  int roff[G::NI], foff[G::NI];
+#pragma unroll
+  for (int k = 0; k < G::NI; ++k) {
+    const int it = tid + k * kThreads;
+    const int rp = it / G::CP, c = it - rp * G::CP;
+    const bool ok = it < G::RP * G::CP;
+    roff[k] = ok ? (2 * rp) * bw + 2 * c + (ra - G::R4) : 0;
+    foff[k] = ok ? rp * G::FW2 + 2 * c : -1;
+  }
+  if (tma && face) {
+    // patch-coordinate reflection maps for the face fix-up
+    for (int r = tid; r < G::BH; r += kThreads) {
+      const int64_t s = reflect(cy0 - R + r, Gy) - (cy0 - R);
+      s_frow[r] = (s >= 0 && s < G::BH) ? (int)s : -1;
+    }
+    for (int c = tid; c < G::FWN; c += kThreads) {
+      const int64_t s = reflect(cx0 - G::R4 + c, Gx) - (cx0 - G::R4);
+      s_fcol[c] = (s >= 0 && s < G::FWN) ? (int)s : -1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int nr = 0, nc = 0;
+      for (int r = 0; r < G::BH; ++r)
+        if (s_frow[r] != r) s_brow[nr++] = r;
+      for (int c = 0; c < G::FWN; ++c)
+        if (s_fcol[c] != c) s_bcol[nc++] = c;
+      s_nbr = nr;
+      s_nbc = nc;
+    }
+  }
   if (tid == 0) {
     s_abort = 0;
     if (tma) {
@@ -238,6 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   __syncthreads();
+  const int nbr = (tma && face) ? s_nbr : 0, nbc = (tma && face) ? s_nbc : 0;
 
   auto issue = [&](int n) {  // TMA load of input plane n into stage n % kNS
     const int zl = (int)(reflect(cz0 - R + n, Gz) - J.in.lo[0]);
@@ -252,86 +330,77 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int n = 0; n < min(kNS, total); ++n) issue(n);
   }
 
-  const int xrow = tid / (kTX / 8), xg = (tid % (kTX / 8)) * 8;  // x pass
+  // x pass: 8 consecutive row pairs per 8-thread group, 4 column groups
+  const int xrp = (tid % 8) + 8 * (tid / 32), xg = ((tid / 8) % 4) * 8;
   const int yp = tid % (kTX / 2), yb2 = (tid / (kTX / 2)) * 2;     // y pass
   const int zy = tid / (kTX / 4), zx4 = (tid % (kTX / 4)) * 4;    // z pass
 
   // ---- one pipeline phase p: stage plane p, x pass of plane p-1, y pass
-  // of plane p-2 (double-buffered F and X), then one barrier.
+  // of plane p-2 (double-buffered F2 and X), then one barrier.
   int zb = 0;
   int p = 0;
   for (; p < total + 2; ++p) {
     if (p < total) {
-      float* Fb = F + (p & 1) * G::FSZ;
+      float2* Fb = F2 + (p & 1) * G::FSZ2;
       if (tma) {
         if (!mbar_wait(&bars[p % kNS], (p / kNS) & 1)) atomicOr(&s_abort, 1);
         const unsigned char* rawb = stages + (p % kNS) * sbytes;
-        if (!face) {
-          switch (dt) {
-            case HP_U8: stage_from_tma_interior<uint8_t, R>(Fb, rawb, ra, bw, tid); break;
-            case HP_U16: stage_from_tma_interior<uint16_t, R>(Fb, rawb, ra, bw, tid); break;
-            case HP_F16: stage_from_tma_interior<__half, R>(Fb, rawb, ra, bw, tid); break;
-            default: stage_from_tma_interior<float, R>(Fb, rawb, ra, bw, tid); break;
-          }
-        } else {
-          switch (dt) {
-            case HP_U8: stage_from_tma<uint8_t, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
-            case HP_U16: stage_from_tma<uint16_t, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
-            case HP_F16: stage_from_tma<__half, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
-            default: stage_from_tma<float, R>(Fb, rawb, bw, srow, scol, warp, lane); break;
-          }
+        stage_interior<TIN, R>(Fb, rawb, bw, roff, foff);
+        if (face) {
+          __syncthreads();  // the fix-up reads cells staged by other threads
+          fix_faces<R>(Fb, s_frow, s_fcol, s_brow, nbr, s_bcol, nbc, tid);
         }
       } else {
         const int64_t sz = reflect(cz0 - R + p, Gz) - J.in.lo[0];
-        switch (dt) {
-          case HP_U8: stage_from_global<uint8_t, R>(Fb, J, sz, srow, scol, warp, lane); break;
-          case HP_U16: stage_from_global<uint16_t, R>(Fb, J, sz, srow, scol, warp, lane); break;
-          case HP_F16: stage_from_global<__half, R>(Fb, J, sz, srow, scol, warp, lane); break;
-          default: stage_from_global<float, R>(Fb, J, sz, srow, scol, warp, lane); break;
-        }
+        const bool zok = sz >= 0 && sz < J.in.dims[0];
+        const int64_t off = (zok ? sz : 0) * J.in.dims[1] * J.in.dims[2];
+        const int64_t pitch = J.in.dims[2];
+        stage_tables<TIN, R>(Fb, static_cast<const TIN*>(J.in.ptr) + off, pitch, zok, srow, scol,
+                             warp, lane);
       }
     }
-    if (p >= 1 && p - 1 < total && xrow < G::BH) {
-      // x pass: 8 outputs of row xrow from a 16-byte aligned window of F
-      const float* Fb = F + ((p - 1) & 1) * G::FSZ;
-      float w[G::WL];
-      const float4* src = reinterpret_cast<const float4*>(Fb + xrow * G::FW + xg);
+    if (p >= 1 && p - 1 < total && xrp < G::RP) {
+      // x pass on a row pair: 8 outputs of rows 2rp and 2rp+1 with packed
+      // fmas over the pair; window column j <-> x = cx0 + xg - R4 + j
+      const u64* src = reinterpret_cast<const u64*>(F2 + ((p - 1) & 1) * G::FSZ2 + xrp * G::FW2 + xg);
+      u64 w[G::WL];
 #pragma unroll
-      for (int j = 0; j < G::WL / 4; ++j) {
-        const float4 v = src[j];
-        w[4 * j] = v.x;
-        w[4 * j + 1] = v.y;
-        w[4 * j + 2] = v.z;
-        w[4 * j + 3] = v.w;
+      for (int j = 0; j < G::WL / 2; ++j) {
+        const ulonglong2 v = reinterpret_cast<const ulonglong2*>(src)[j];
+        w[2 * j] = v.x;
+        w[2 * j + 1] = v.y;
       }
-      float o[8];
+      float* X0 = X + ((p - 1) & 1) * G::XSZ + (2 * xrp) * kXS + xg;
+      float o0[8], o1[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        float acc = 0.0f;
-        // window index j <-> x = cx0 + xg - R4 + j; tap k = i + R4 - j
+        u64 acc = 0ull;
 #pragma unroll
         for (int j = i + G::R4 - R; j <= i + G::R4 + R; ++j)
-          acc = fmaf(P.wx[i + G::R4 - j + R], w[j], acc);
-        o[i] = acc;
+          acc = ffma2(P.w2[2][i + G::R4 - j + R], w[j], acc);
+        const float2 a = unpack2(acc);
+        o0[i] = a.x;
+        o1[i] = a.y;
       }
-      float4* dst = reinterpret_cast<float4*>(X + ((p - 1) & 1) * G::XSZ + xrow * kXS + xg);
-      dst[0] = make_float4(o[0], o[1], o[2], o[3]);
-      dst[1] = make_float4(o[4], o[5], o[6], o[7]);
+      reinterpret_cast<float4*>(X0)[0] = make_float4(o0[0], o0[1], o0[2], o0[3]);
+      reinterpret_cast<float4*>(X0)[1] = make_float4(o0[4], o0[5], o0[6], o0[7]);
+      reinterpret_cast<float4*>(X0 + kXS)[0] = make_float4(o1[0], o1[1], o1[2], o1[3]);
+      reinterpret_cast<float4*>(X0 + kXS)[1] = make_float4(o1[4], o1[5], o1[6], o1[7]);
     }
     if (p >= 2) {
       // y pass of plane p-2 into its ring slot: one x pair, two rows per
       // thread, packed fmas over the pair
-      const float* Xb = X + ((p - 2) & 1) * G::XSZ;
-      unsigned long long a0 = 0ull, a1 = 0ull;
+      const float* Xb = X + ((p - 2) & 1) * G::XSZ + yb2 * kXS + 2 * yp;
+      u64 a0 = 0ull, a1 = 0ull;
 #pragma unroll
       for (int j = 0; j < 2 + 2 * R; ++j) {
-        const unsigned long long v = pack2(*reinterpret_cast<const float2*>(Xb + (yb2 + j) * kXS + 2 * yp));
-        if (j <= 2 * R) a0 = ffma2(splat2(P.wy[2 * R - j]), v, a0);
-        if (j >= 1) a1 = ffma2(splat2(P.wy[2 * R + 1 - j]), v, a1);
+        const u64 v = *reinterpret_cast<const u64*>(Xb + j * kXS);
+        if (j <= 2 * R) a0 = ffma2(P.w2[1][2 * R - j], v, a0);
+        if (j >= 1) a1 = ffma2(P.w2[1][2 * R + 1 - j], v, a1);
       }
-      float* slot = ring + ((p - 2) % G::NRING) * (kTY * kTX);
-      *reinterpret_cast<float2*>(slot + yb2 * kTX + 2 * yp) = unpack2(a0);
-      *reinterpret_cast<float2*>(slot + (yb2 + 1) * kTX + 2 * yp) = unpack2(a1);
+      float* slot = ring + ((p - 2) % G::NRING) * (kTY * kTX) + yb2 * kTX + 2 * yp;
+      *reinterpret_cast<u64*>(slot) = a0;
+      *reinterpret_cast<u64*>(slot + kTX) = a1;
     }
     __syncthreads();
     if (s_abort) break;
@@ -342,30 +411,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     // z pass for every block whose ring planes are all present
     const int done = min(p - 1, total);  // planes 0 .. done-1 are in the ring
     while (zb < nout && done >= min(zb + kBZ + 2 * R, total)) {
-      unsigned long long acc0[kBZ], acc1[kBZ];  // x pairs (0,1) and (2,3)
+      u64 acc0[kBZ], acc1[kBZ];  // x pairs (0,1) and (2,3)
 #pragma unroll
       for (int j = 0; j < kBZ; ++j) acc0[j] = acc1[j] = 0ull;
       int slot = zb % G::NRING;
 #pragma unroll
       for (int m = 0; m < kBZ + 2 * R; ++m) {
-        const float4 v =
-            *reinterpret_cast<const float4*>(ring + slot * (kTY * kTX) + zy * kTX + zx4);
+        const ulonglong2 v =
+            *reinterpret_cast<const ulonglong2*>(ring + slot * (kTY * kTX) + zy * kTX + zx4);
         slot = slot + 1 == G::NRING ? 0 : slot + 1;
-        const unsigned long long v0 = pack2(make_float2(v.x, v.y)), v1 = pack2(make_float2(v.z, v.w));
 #pragma unroll
         for (int j = 0; j < kBZ; ++j) {
           if (m >= j && m <= j + 2 * R) {
-            const unsigned long long g = splat2(P.wz[j - m + 2 * R]);
-            acc0[j] = ffma2(g, v0, acc0[j]);
-            acc1[j] = ffma2(g, v1, acc1[j]);
+            acc0[j] = ffma2(P.w2[0][j - m + 2 * R], v.x, acc0[j]);
+            acc1[j] = ffma2(P.w2[0][j - m + 2 * R], v.y, acc1[j]);
           }
         }
-      }
-      float4 acc[kBZ];
-#pragma unroll
-      for (int j = 0; j < kBZ; ++j) {
-        const float2 lo = unpack2(acc0[j]), hi = unpack2(acc1[j]);
-        acc[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
       }
       const int64_t gy = cy0 + zy, gx = cx0 + zx4;
       if (gy < J.core_hi[1]) {
@@ -380,9 +441,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < kBZ; ++j, idx += pstride) {
           if (zb + j >= nout) break;
           if (vec) {
-            *reinterpret_cast<float4*>(static_cast<float*>(O.ptr) + idx) = acc[j];
+            *reinterpret_cast<ulonglong2*>(static_cast<float*>(O.ptr) + idx) =
+                make_ulonglong2(acc0[j], acc1[j]);
           } else {
-            const float vv[4] = {acc[j].x, acc[j].y, acc[j].z, acc[j].w};
+            const float2 lo = unpack2(acc0[j]), hi = unpack2(acc1[j]);
+            const float vv[4] = {lo.x, lo.y, hi.x, hi.y};
 #pragma unroll
             for (int e = 0; e < 4; ++e)
               if (gx + e < J.core_hi[2]) {
@@ -452,29 +515,40 @@ __global__ void k_copy_out(const float* src, int64_t n0, int64_t n1, int64_t n2,
   }
 }
 
-template <int R>
+template <int R, typename TIN>
 cudaError_t launch_zm_t(const GaussParams& P, const CUtensorMap& map, dim3 grid, cudaStream_t s) {
   static bool attr_set = false;  // per instantiation; set once per process
+  constexpr int smem = zm_smem_bytes<R>((int)sizeof(TIN));
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gauss_zm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         zm_smem_bytes<R>(4));
+    cudaError_t e = cudaFuncSetAttribute(k_gauss_zm<R, TIN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int es = (int)dtype_size(P.job.in.dtype);
-  k_gauss_zm<R><<<grid, kThreads, zm_smem_bytes<R>(es), s>>>(P, map);
+  k_gauss_zm<R, TIN><<<grid, kThreads, smem, s>>>(P, map);
   return cudaGetLastError();
 }
 
-cudaError_t dispatch_zm(int r, const GaussParams& P, const CUtensorMap& map, dim3 grid,
-                        cudaStream_t s) {
+template <typename TIN>
+cudaError_t dispatch_zm_t(int r, const GaussParams& P, const CUtensorMap& map, dim3 grid,
+                          cudaStream_t s) {
   switch (r) {
 #define HP_CASE(RR) \
-  case RR: return launch_zm_t<RR>(P, map, grid, s);
+  case RR: return launch_zm_t<RR, TIN>(P, map, grid, s);
     HP_CASE(1) HP_CASE(2) HP_CASE(3) HP_CASE(4) HP_CASE(5) HP_CASE(6)
     HP_CASE(7) HP_CASE(8) HP_CASE(9) HP_CASE(10) HP_CASE(11) HP_CASE(12)
 #undef HP_CASE
     default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dispatch_zm(int r, const GaussParams& P, const CUtensorMap& map, dim3 grid,
+                        cudaStream_t s) {
+  switch (P.job.in.dtype) {
+    case HP_U8: return dispatch_zm_t<uint8_t>(r, P, map, grid, s);
+    case HP_U16: return dispatch_zm_t<uint16_t>(r, P, map, grid, s);
+    case HP_F16: return dispatch_zm_t<__half>(r, P, map, grid, s);
+    default: return dispatch_zm_t<float>(r, P, map, grid, s);
   }
 }
 
@@ -581,11 +655,11 @@ cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s) {
 
   GaussParams P;
   P.job = job;
-  for (int k = 0; k < kMaxTaps; ++k) {
-    P.wz[k] = taps.w[0][k];
-    P.wy[k] = taps.w[1][k];
-    P.wx[k] = taps.w[2][k];
-  }
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k <= 2 * kMaxR; ++k) {
+      const uint32_t b = k <= 2 * r ? __float_as_uint_host(taps.w[a][k]) : 0u;
+      P.w2[a][k] = ((u64)b << 32) | b;
+    }
   P.r = r;
   P.err = device_error_word();
   const int64_t cx = job.core_hi[2] - job.core_lo[2];

@@ -163,7 +163,7 @@ static PFN_encodeTiled get_encode() {
 }
 
 bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t dims[3], int bw,
-                  int bh) {
+                  int bh, int bd) {
   PFN_encodeTiled enc = get_encode();
   if (!enc) return false;
   CUtensorMapDataType t;
@@ -180,7 +180,7 @@ bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t d
   cuuint64_t gdim[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
   cuuint64_t gstride[2] = {(cuuint64_t)(dims[0] * es), (cuuint64_t)(dims[0] * dims[1] * es)};
   if (gstride[0] % 16 || gstride[1] % 16) return false;
-  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)bd};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, t, 3, const_cast<void*>(base), gdim, gstride, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

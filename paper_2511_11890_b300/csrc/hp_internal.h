@@ -88,10 +88,10 @@ cudaError_t launch_threshold(const Job& job, double t, cudaStream_t s);
 int set_error(int status, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
-// TMA tensor map over a dense 3D box (x, y, z extents), box (bw, bh, 1).
+// TMA tensor map over a dense 3D box (x, y, z extents), box (bw, bh, bd).
 // Returns false when the layout does not meet TMA rules.
 bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t dims[3], int bw,
-                  int bh);
+                  int bh, int bd = 1);
 
 int num_sms();
 

@@ -34,12 +34,8 @@ namespace hp {
 
 namespace {
 
-constexpr int kTX = 32;
-constexpr int kTY = 32;
 constexpr int kBZ = 8;
 constexpr int kNS = 4;
-constexpr int kThreads = 256;
-constexpr int kXS = kTX + 4;  // X row stride (floats), 16-byte aligned rows
 
 typedef unsigned long long u64;
 
@@ -78,42 +74,53 @@ __host__ __device__ constexpr int pair_stride(int n) {
 //      keeps the x-pass window loads 16-byte aligned.
 //   X  (x-pass output, double-buffered): [BH][kXS] floats.
 //   ring: kBZ + 2R planes of y-pass output [TY][TX].
-template <int R>
+template <int R, int TX, int TY>
 struct ZmGeom {
+  static constexpr int NT = TX * TY / 4;                // threads: 4 outputs each per plane
+  static constexpr int XS = TX + 4;                     // X row stride (floats)
   static constexpr int R4 = round_up(R, 4);
   static constexpr int WL = round_up(R4 + R + 8, 4);  // x window (columns) for 8 outputs
-  static constexpr int FWN = (kTX - 8) + WL;           // columns read
-  static constexpr int BH = kTY + 2 * R;
+  static constexpr int FWN = (TX - 8) + WL;            // columns read
+  static constexpr int BH = TY + 2 * R;
   static constexpr int RP = BH / 2;                     // row pairs
   static constexpr int FW2 = pair_stride(FWN);
   static constexpr int CP = FWN / 2;                    // column pairs per row pair
-  static constexpr int NI = (RP * CP + kThreads - 1) / kThreads;  // staging items per thread
+  static constexpr int NI = (RP * CP + NT - 1) / NT;   // staging items per thread
   static constexpr int NC = (FWN + 31) / 32;            // columns per lane (face path)
   static constexpr int NRING = kBZ + 2 * R;
   static constexpr int FSZ2 = RP * FW2;                 // in FP32 pairs
-  static constexpr int XSZ = BH * kXS;
-  static constexpr int TAIL = 2 * FSZ2 * 8 + (2 * XSZ + NRING * kTY * kTX) * 4 + BH * 4;
+  static constexpr int XSZ = BH * XS;
+  static constexpr int TAIL = 2 * FSZ2 * 8 + (2 * XSZ + NRING * TY * TX) * 4 + BH * 4;
   static_assert(FWN % 4 == 0 && BH % 2 == 0, "patch shape");
 };
 
 // Per-dtype TMA box geometry: left halo ra (R rounded up to 16 bytes) and
 // width bw (elements); raw col c <-> x = cx0 - ra + c.
-__host__ __device__ constexpr void box_geom(int r, int es, int* ra, int* bw) {
+__host__ __device__ constexpr void box_geom(int r, int es, int tx, int* ra, int* bw) {
   const int al = 16 / es;
   *ra = round_up(r, al);
-  *bw = round_up(kTX + *ra + r, al);
+  *bw = round_up(tx + *ra + r, al);
 }
 
-__host__ __device__ constexpr int stage_bytes(int r, int es) {
+__host__ __device__ constexpr int stage_bytes(int r, int es, int tx, int ty) {
   int ra = 0, bw = 0;
-  box_geom(r, es, &ra, &bw);
-  return round_up(bw * (kTY + 2 * r) * es, 128);
+  box_geom(r, es, tx, &ra, &bw);
+  return round_up(bw * (ty + 2 * r) * es, 128);
 }
 
-template <int R>
+template <int R, int TX, int TY>
 __host__ __device__ constexpr int zm_smem_bytes(int es) {
-  return 128 + kNS * stage_bytes(R, es) + ZmGeom<R>::TAIL;
+  return 128 + kNS * stage_bytes(R, es, TX, TY) + ZmGeom<R, TX, TY>::TAIL;
 }
+
+// Tile shape per radius. TMA box loads are limited by their row count, so
+// small radii use wide, short tiles (22 rows per 1024 outputs at r = 3); large
+// radii use square tiles, whose x pass repeats fewer halo rows.
+template <int R>
+struct ZmTile {
+  static constexpr int TX = R <= 6 ? 64 : 32;
+  static constexpr int TY = R <= 6 ? 16 : 32;
+};
 
 // Two consecutive elements -> two floats. Integers use the exact 2^23 bias:
 // a byte permute builds 0x4B00_0000 | v, then one packed subtract.
@@ -145,11 +152,11 @@ __device__ __forceinline__ float2 load2_f32<float>(const float* p) {
 // Interior tiles: no reflection. Item k of this thread covers row pair rp,
 // columns 2c, 2c+1: two 2-element loads (rows 2rp, 2rp+1), one 16-byte store
 // of the interleaved pairs. Offsets were precomputed per CTA.
-template <typename TIN, int R>
+template <typename TIN, int R, int TX, int TY>
 __device__ __forceinline__ void stage_interior(float2* F2, const unsigned char* rawb, int bw,
-                                               const int (&roff)[ZmGeom<R>::NI],
-                                               const int (&foff)[ZmGeom<R>::NI]) {
-  using G = ZmGeom<R>;
+                                               const int (&roff)[ZmGeom<R, TX, TY>::NI],
+                                               const int (&foff)[ZmGeom<R, TX, TY>::NI]) {
+  using G = ZmGeom<R, TX, TY>;
   const TIN* raw = reinterpret_cast<const TIN*>(rawb);
 #pragma unroll
   for (int k = 0; k < G::NI; ++k) {
@@ -165,14 +172,14 @@ __device__ __forceinline__ void stage_interior(float2* F2, const unsigned char* 
 // the source tables, which resolve the reflection; srow[row] is the raw
 // stage row (TMA) or box row (global loads), scol[k] the column of lane
 // column lane + 32k; -1 marks taps no stored output uses.
-template <typename TIN, int R>
+template <typename TIN, int R, int TX, int TY>
 __device__ __forceinline__ void stage_tables(float2* F2, const TIN* plane, int64_t pitch,
                                              bool ok_plane, const int* srow,
-                                             const int (&scol)[ZmGeom<R>::NC], int warp,
+                                             const int (&scol)[ZmGeom<R, TX, TY>::NC], int warp,
                                              int lane) {
-  using G = ZmGeom<R>;
+  using G = ZmGeom<R, TX, TY>;
   float* F = reinterpret_cast<float*>(F2);
-  for (int row = warp; row < G::BH; row += kThreads / 32) {
+  for (int row = warp; row < G::BH; row += G::NT / 32) {
     const int sr = ok_plane ? srow[row] : -1;
     float* dst = F + (row >> 1) * (2 * G::FW2) + (row & 1);
 #pragma unroll
@@ -192,29 +199,31 @@ __device__ __forceinline__ void stage_tables(float2* F2, const TIN* plane, int64
 // frow/fcol map patch rows/columns to their source rows/columns (identity
 // inside the volume, -1 where no stored output needs the cell); brow/bcol
 // list the rows/columns that are outside.
-template <int R>
+template <int R, int TX, int TY>
 __device__ __forceinline__ void fix_faces(float2* F2, const int* frow, const int* fcol,
                                           const int* brow, int nbr, const int* bcol, int nbc,
                                           int tid) {
-  using G = ZmGeom<R>;
+  using G = ZmGeom<R, TX, TY>;
   float* F = reinterpret_cast<float*>(F2);
   auto cell = [&](int r, int c) -> float& { return F[(r >> 1) * (2 * G::FW2) + 2 * c + (r & 1)]; };
-  for (int i = tid; i < nbr * G::FWN; i += kThreads) {
+  for (int i = tid; i < nbr * G::FWN; i += G::NT) {
     const int r = brow[i / G::FWN], c = i % G::FWN;
     const int sr = frow[r], sc = fcol[c];
     cell(r, c) = (sr >= 0 && sc >= 0) ? cell(sr, sc) : 0.0f;
   }
-  for (int i = tid; i < nbc * G::BH; i += kThreads) {
+  for (int i = tid; i < nbc * G::BH; i += G::NT) {
     const int c = bcol[i / G::BH], r = i % G::BH;
     const int sr = frow[r], sc = fcol[c];
     cell(r, c) = (sr >= 0 && sc >= 0) ? cell(sr, sc) : 0.0f;
   }
 }
 
-template <int R, typename TIN>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int R, typename TIN, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY / 4, 1)
     k_gauss_zm(const __grid_constant__ GaussParams P, const __grid_constant__ CUtensorMap tmap) {
-  using G = ZmGeom<R>;
+  using G = ZmGeom<R, TX, TY>;
+  constexpr int NT = G::NT;
+  constexpr int kXS = G::XS;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   __shared__ int s_frow[G::BH], s_fcol[G::FWN], s_brow[G::BH], s_bcol[G::FWN];
@@ -223,8 +232,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const Job& J = P.job;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
-  const int64_t cx0 = J.core_lo[2] + (int64_t)tx * kTX;
-  const int64_t cy0 = J.core_lo[1] + (int64_t)ty * kTY;
+  const int64_t cx0 = J.core_lo[2] + (int64_t)tx * TX;
+  const int64_t cy0 = J.core_lo[1] + (int64_t)ty * TY;
   const int64_t cz0 = J.core_lo[0] + (int64_t)blockIdx.y * P.zchunk;
   const int64_t cz1 = min(cz0 + (int64_t)P.zchunk, J.core_hi[0]);
   if (cz0 >= cz1) return;
@@ -233,21 +242,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t Gz = J.gdims[0], Gy = J.gdims[1], Gx = J.gdims[2];
   constexpr int es = sizeof(TIN);
   int ra, bw;
-  box_geom(R, es, &ra, &bw);
-  const int sbytes = stage_bytes(R, es);
+  box_geom(R, es, TX, &ra, &bw);
+  const int sbytes = stage_bytes(R, es, TX, TY);
   const bool tma = P.use_tma != 0;
   // tiles whose halo stays inside the volume need no reflection
-  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + kTY + R > Gy);
+  const bool face = (cx0 - R < 0) || (cx0 + TX + R > Gx) || (cy0 - R < 0) || (cy0 + TY + R > Gy);
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   unsigned char* stages = smem + 128;
   float2* F2 = reinterpret_cast<float2*>(stages + kNS * sbytes);
   float* X = reinterpret_cast<float*>(F2 + 2 * G::FSZ2);
   float* ring = X + 2 * G::XSZ;
-  int* srow = reinterpret_cast<int*>(ring + G::NRING * kTY * kTX);
+  int* srow = reinterpret_cast<int*>(ring + G::NRING * TY * TX);
 
   // source tables (reflection resolved once per CTA)
-  for (int row = tid; row < G::BH; row += kThreads) {
+  for (int row = tid; row < G::BH; row += NT) {
     const int64_t sy = reflect(cy0 - R + row, Gy);
     int v;
     if (tma) {
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int roff[G::NI], foff[G::NI];
 #pragma unroll
   for (int k = 0; k < G::NI; ++k) {
-    const int it = tid + k * kThreads;
+    const int it = tid + k * NT;
     const int rp = it / G::CP, c = it - rp * G::CP;
     const bool ok = it < G::RP * G::CP;
     roff[k] = ok ? (2 * rp) * bw + 2 * c + (ra - G::R4) : 0;
@@ -287,11 +296,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (tma && face) {
     // patch-coordinate reflection maps for the face fix-up
-    for (int r = tid; r < G::BH; r += kThreads) {
+    for (int r = tid; r < G::BH; r += NT) {
       const int64_t s = reflect(cy0 - R + r, Gy) - (cy0 - R);
       s_frow[r] = (s >= 0 && s < G::BH) ? (int)s : -1;
     }
-    for (int c = tid; c < G::FWN; c += kThreads) {
+    for (int c = tid; c < G::FWN; c += NT) {
       const int64_t s = reflect(cx0 - G::R4 + c, Gx) - (cx0 - G::R4);
       s_fcol[c] = (s >= 0 && s < G::FWN) ? (int)s : -1;
     }
@@ -331,9 +340,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   // x pass: 8 consecutive row pairs per 8-thread group, 4 column groups
-  const int xrp = (tid % 8) + 8 * (tid / 32), xg = ((tid / 8) % 4) * 8;
-  const int yp = tid % (kTX / 2), yb2 = (tid / (kTX / 2)) * 2;     // y pass
-  const int zy = tid / (kTX / 4), zx4 = (tid % (kTX / 4)) * 4;    // z pass
+  // x pass: 8 consecutive threads take 8 row pairs of one 8-column group
+  const int xrp = (tid % 8) + 8 * (tid / TX), xg = ((tid / 8) % (TX / 8)) * 8;
+  const int yp = tid % (TX / 2), yb2 = (tid / (TX / 2)) * 2;     // y pass
+  const int zy = tid / (TX / 4), zx4 = (tid % (TX / 4)) * 4;    // z pass
 
   // ---- one pipeline phase p: stage plane p, x pass of plane p-1, y pass
   // of plane p-2 (double-buffered F2 and X), then one barrier.
@@ -345,17 +355,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (tma) {
         if (!mbar_wait(&bars[p % kNS], (p / kNS) & 1)) atomicOr(&s_abort, 1);
         const unsigned char* rawb = stages + (p % kNS) * sbytes;
-        stage_interior<TIN, R>(Fb, rawb, bw, roff, foff);
+        stage_interior<TIN, R, TX, TY>(Fb, rawb, bw, roff, foff);
         if (face) {
           __syncthreads();  // the fix-up reads cells staged by other threads
-          fix_faces<R>(Fb, s_frow, s_fcol, s_brow, nbr, s_bcol, nbc, tid);
+          fix_faces<R, TX, TY>(Fb, s_frow, s_fcol, s_brow, nbr, s_bcol, nbc, tid);
         }
       } else {
         const int64_t sz = reflect(cz0 - R + p, Gz) - J.in.lo[0];
         const bool zok = sz >= 0 && sz < J.in.dims[0];
         const int64_t off = (zok ? sz : 0) * J.in.dims[1] * J.in.dims[2];
         const int64_t pitch = J.in.dims[2];
-        stage_tables<TIN, R>(Fb, static_cast<const TIN*>(J.in.ptr) + off, pitch, zok, srow, scol,
+        stage_tables<TIN, R, TX, TY>(Fb, static_cast<const TIN*>(J.in.ptr) + off, pitch, zok, srow, scol,
                              warp, lane);
       }
     }
@@ -398,9 +408,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (j <= 2 * R) a0 = ffma2(P.w2[1][2 * R - j], v, a0);
         if (j >= 1) a1 = ffma2(P.w2[1][2 * R + 1 - j], v, a1);
       }
-      float* slot = ring + ((p - 2) % G::NRING) * (kTY * kTX) + yb2 * kTX + 2 * yp;
+      float* slot = ring + ((p - 2) % G::NRING) * (TY * TX) + yb2 * TX + 2 * yp;
       *reinterpret_cast<u64*>(slot) = a0;
-      *reinterpret_cast<u64*>(slot + kTX) = a1;
+      *reinterpret_cast<u64*>(slot + TX) = a1;
     }
     __syncthreads();
     if (s_abort) break;
@@ -418,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int m = 0; m < kBZ + 2 * R; ++m) {
         const ulonglong2 v =
-            *reinterpret_cast<const ulonglong2*>(ring + slot * (kTY * kTX) + zy * kTX + zx4);
+            *reinterpret_cast<const ulonglong2*>(ring + slot * (TY * TX) + zy * TX + zx4);
         slot = slot + 1 == G::NRING ? 0 : slot + 1;
 #pragma unroll
         for (int j = 0; j < kBZ; ++j) {
@@ -518,14 +528,15 @@ __global__ void k_copy_out(const float* src, int64_t n0, int64_t n1, int64_t n2,
 template <int R, typename TIN>
 cudaError_t launch_zm_t(const GaussParams& P, const CUtensorMap& map, dim3 grid, cudaStream_t s) {
   static bool attr_set = false;  // per instantiation; set once per process
-  constexpr int smem = zm_smem_bytes<R>((int)sizeof(TIN));
+  constexpr int TX = ZmTile<R>::TX, TY = ZmTile<R>::TY;
+  constexpr int smem = zm_smem_bytes<R, TX, TY>((int)sizeof(TIN));
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gauss_zm<R, TIN>,
+    cudaError_t e = cudaFuncSetAttribute(k_gauss_zm<R, TIN, TX, TY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_gauss_zm<R, TIN><<<grid, kThreads, smem, s>>>(P, map);
+  k_gauss_zm<R, TIN, TX, TY><<<grid, TX * TY / 4, smem, s>>>(P, map);
   return cudaGetLastError();
 }
 
@@ -666,8 +677,9 @@ cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s) {
   const int64_t cy = job.core_hi[1] - job.core_lo[1];
   const int64_t cz = job.core_hi[0] - job.core_lo[0];
   if (cx <= 0 || cy <= 0 || cz <= 0) return cudaSuccess;
-  P.tiles_x = (int)((cx + kTX - 1) / kTX);
-  const int64_t tiles = (int64_t)P.tiles_x * ((cy + kTY - 1) / kTY);
+  const int tx = r <= 6 ? 64 : 32, ty = r <= 6 ? 16 : 32;  // ZmTile<r>
+  P.tiles_x = (int)((cx + tx - 1) / tx);
+  const int64_t tiles = (int64_t)P.tiles_x * ((cy + ty - 1) / ty);
   // z chunk: aim for >= 8 CTAs per SM in total, chunks of at least 4*BZ
   // planes so that the 2r halo planes stay a small fraction.
   const int64_t want = (int64_t)num_sms() * 8;
@@ -687,14 +699,14 @@ cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s) {
                  ((job.core_lo[2] - job.in.lo[2]) % al == 0);
   if (use_tma) {
     int ra = 0, bw = 0;
-    box_geom(r, (int)es, &ra, &bw);
+    box_geom(r, (int)es, tx, &ra, &bw);
     const int64_t dims[3] = {job.in.dims[2], job.in.dims[1], job.in.dims[0]};
-    use_tma = make_tmap_3d(&map, job.in.ptr, job.in.dtype, dims, bw, kTY + 2 * r);
+    use_tma = make_tmap_3d(&map, job.in.ptr, job.in.dtype, dims, bw, ty + 2 * r);
   }
   P.use_tma = use_tma ? 1 : 0;
   if (log_level() > 0)
-    fprintf(stderr, "[hp] gauss z-march r=%d tma=%d grid=%ux%u zchunk=%d smem=%d\n", r,
-            P.use_tma, grid.x, grid.y, P.zchunk, 0);
+    fprintf(stderr, "[hp] gauss z-march r=%d tile=%dx%d tma=%d grid=%ux%u zchunk=%d\n", r, tx, ty,
+            P.use_tma, grid.x, grid.y, P.zchunk);
   return dispatch_zm(r, P, map, grid, s);
 }
 

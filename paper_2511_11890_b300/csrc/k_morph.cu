@@ -71,6 +71,28 @@ __device__ __forceinline__ void disk_min(uint32_t& d, const uint32_t* Mb) {
   }
 }
 
+// Ball of radius 3: the disks share one 3-row minimum A of M2:
+//   D1 = min(M2[y-2..y+2]) = min(A, M2[y-2], M2[y+2])      (|dz| = 1)
+//   D0 = min(D1, M3[y], M0[y-3], M0[y+3])                  (|dz| = 0; M2[y] >= M3[y])
+//   D2 = min(A, M1[y-2], M1[y+2])                          (|dz| = 2)
+//   D3 = M0[y]                                             (|dz| = 3)
+// (half-lengths floor(sqrt(9 - dy^2 - dz^2)); 9 min operations per row
+// instead of 18).
+template <int BH, int YB>
+__device__ __forceinline__ void disk_rows_ball3(uint32_t (&D)[4][YB], const uint32_t* Mb) {
+  constexpr int S = 32 + 1;
+  auto m = [&](int L, int dy, int i) { return Mb[(L * BH + dy + 3) * S + i * S]; };
+#pragma unroll
+  for (int i = 0; i < YB; ++i) {
+    const uint32_t a = min(min(m(2, -1, i), m(2, 0, i)), m(2, 1, i));
+    const uint32_t d1 = min(a, min(m(2, -2, i), m(2, 2, i)));
+    D[1][i] = d1;
+    D[0][i] = min(min(d1, m(3, 0, i)), min(m(0, -3, i), m(0, 3, i)));
+    D[2][i] = min(a, min(m(1, -2, i), m(1, 2, i)));
+    D[3][i] = m(0, 0, i);
+  }
+}
+
 template <int R, int BALL, int BH, int DZ, int YB>
 __device__ __forceinline__ void disk_rows(uint32_t (&D)[BALL ? R + 1 : 1][YB], const uint32_t* Mb) {
   if constexpr (DZ <= (BALL ? R : 0)) {
@@ -413,16 +435,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t w[8 + 2 * R];
 #pragma unroll
       for (int j = 0; j < 8 + 2 * R; ++j) w[j] = Kb[xrow * G::KW + xg + j];
+      // window index j <-> x = cx0 + xg - R + j. Line minima of growing
+      // half-length: M1 = min of 3, then M_L[j] = min(M_{L-1}[j-1], M_{L-1}[j+1])
+      // (the two windows of half-length L-1 cover the one of half-length L).
+      uint32_t m[8 + 2 * R];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        uint32_t m = w[i + R];
-        if (BALL) Mb[(0 * G::BH + xrow) * kMS + xg + i] = m;
+      for (int j = 0; j < 8 + 2 * R; ++j) m[j] = w[j];
 #pragma unroll
-        for (int L = 1; L <= R; ++L) {
-          m = min(m, min(w[i + R - L], w[i + R + L]));
-          if (BALL) Mb[(L * G::BH + xrow) * kMS + xg + i] = m;
+      for (int i = 0; i < 8; ++i)
+        if (BALL) Mb[(0 * G::BH + xrow) * kMS + xg + i] = w[i + R];
+#pragma unroll
+      for (int L = 1; L <= R; ++L) {
+        uint32_t t[8 + 2 * R];
+#pragma unroll
+        for (int j = L; j < 8 + 2 * R - L; ++j)
+          t[j] = L == 1 ? min(min(m[j - 1], m[j]), m[j + 1]) : min(m[j - 1], m[j + 1]);
+#pragma unroll
+        for (int j = L; j < 8 + 2 * R - L; ++j) m[j] = t[j];
+        if (BALL || L == R) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            Mb[((BALL ? L : 0) * G::BH + xrow) * kMS + xg + i] = m[i + R];
         }
-        if (!BALL) Mb[xrow * kMS + xg + i] = m;
       }
     }
     if (p >= 2) {
@@ -430,7 +464,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t* Mb = M + (n & 1) * G::MSZ;
       uint32_t D[BALL ? R + 1 : 1][kYB];
       static_assert(kMS == 32 + 1, "disk_min assumes the line-minimum row stride");
-      disk_rows<R, BALL, G::BH, 0, kYB>(D, Mb + yb * kMS + yx);
+      if constexpr (BALL && R == 3)
+        disk_rows_ball3<G::BH, kYB>(D, Mb + yb * kMS + yx);
+      else
+        disk_rows<R, BALL, G::BH, 0, kYB>(D, Mb + yb * kMS + yx);
       uint32_t done[kYB];
       push_dispatch<R, BALL>(n % G::NR, acc, D, done);
       const int64_t gz = cz0 - R + n - R, gx = cx0 + yx;  // plane n's input z minus R

@@ -184,6 +184,7 @@ def run_hp(args):
     dev = torch.device("cuda", local)
     hbm_gbs, sm_max_mhz, peak_kind = _peaks()
 
+    N = args.size
     f, porosity = synth.porous(N, SEED)
     x = torch.from_numpy(f).to(dev)
     outs_g = [torch.empty((N, N, N), dtype=torch.float32, device=dev) for _ in SIGMAS]
@@ -310,7 +311,7 @@ def run_hp(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": f"synthetic porous tomogram (seeded, porosity {porosity:.3f})",
-            "config": {"workload": "porous 1024^3 u16: gaussian s=1,2,4 -> f32; erode+dilate ball r=3",
+            "config": {"workload": f"porous {N}^3 u16: gaussian s=1,2,4 -> f32; erode+dilate ball r=3",
                        "volume": [N, N, N], "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs (2 GiB) and outputs (16 GiB) larger than L2",
                        "hbm_frac_of_step": hbm_step_frac},
@@ -414,6 +415,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="porous1024", choices=["porous1024", "ooc2048"])
+    ap.add_argument("--size", type=int, default=N,
+                    help="edge of the in-HBM volume (1024 is the benchmark; smaller sizes "
+                         "are for profiling captures)")
     args = ap.parse_args()
     if args.workload == "ooc2048":
         return run_outofcore(args)

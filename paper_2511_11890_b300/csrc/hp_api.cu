@@ -142,6 +142,26 @@ int num_sms() {
   return cached[dev];
 }
 
+int64_t pick_zchunk(int64_t cz, int64_t tiles, int64_t slots, int halo, int align) {
+  if (cz <= 0) return align;
+  slots = std::max<int64_t>(1, slots);
+  int64_t best_zc = (cz + align - 1) / align * align;
+  double best = 1e300;
+  for (int64_t n = 1; n <= 512; ++n) {
+    int64_t zc = (cz + n - 1) / n;
+    zc = (zc + align - 1) / align * align;
+    const int64_t chunks = (cz + zc - 1) / zc;
+    const int64_t waves = (tiles * chunks + slots - 1) / slots;
+    const double cost = (double)waves * (double)(zc + halo);
+    if (cost < best * 0.999) {
+      best = cost;
+      best_zc = zc;
+    }
+    if (zc <= align) break;
+  }
+  return best_zc;
+}
+
 // ------------------------------------------------------------ TMA maps
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                     const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,

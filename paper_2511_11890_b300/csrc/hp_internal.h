@@ -82,6 +82,7 @@ int* device_error_word();
 // Launchers (enqueue only). Return a cudaError_t.
 cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s);
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
+cudaError_t launch_morph16(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
 cudaError_t launch_threshold(const Job& job, double t, cudaStream_t s);
 
 // Error reporting (thread-local message).
@@ -94,6 +95,12 @@ bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t d
                   int bh, int bd = 1);
 
 int num_sms();
+
+// z-chunk length for a z-march grid of `tiles` columns: CTAs run in waves
+// of `slots` (resident CTAs on the whole GPU) and each costs about its
+// planes plus `halo`; returns the multiple of `align` that minimises
+// waves x (chunk + halo).
+int64_t pick_zchunk(int64_t cz, int64_t tiles, int64_t slots, int halo, int align);
 
 // HP_LOG >= 1 prints the kernel path chosen for each launch to stderr.
 int log_level();

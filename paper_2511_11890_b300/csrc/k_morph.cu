@@ -568,6 +568,9 @@ cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStr
   const int64_t cy = job.core_hi[1] - job.core_lo[1];
   const int64_t cz = job.core_hi[0] - job.core_lo[0];
   if (cx <= 0 || cy <= 0 || cz <= 0) return cudaSuccess;
+  // 16-bit data: packed-key kernel (k_morph16.cu) where its layout rules hold
+  const cudaError_t e16 = launch_morph16(job, se, rad, is_dilate, s);
+  if (e16 != cudaErrorNotSupported) return e16;
   const int ball = se == HP_SE_BALL;
   const bool tiled = rad >= 1 && rad <= kMaxTiledR && job.gdims[2] >= rad && job.gdims[1] >= rad;
   if (!tiled) {

@@ -1,0 +1,439 @@
+// Grayscale erosion / dilation of 16-bit volumes (uint16, float16) with
+// packed keys (Harpia Sec. III-C). Exact, reflect boundaries on global
+// coordinates, same result as the 32-bit-key kernel in k_morph.cu.
+//
+// Two x-neighbours share one 32-bit register: the pair (x, x+1) of
+// order-preserving 16-bit keys, so every min is one SIMD instruction over
+// two voxels (__vminu2 / the three-input __vimin3_u16x2). uint16 keys are
+// the values themselves, float16 keys the sign-magnitude flip, dilation the
+// complement, all applied to whole 32-bit words.
+//
+// Tiled z-march: a CTA owns a 64 x 32 column of the core and marches along
+// z through a 4-stage TMA pipeline of halo-padded planes. Phase p:
+//   x (plane p-1, read straight from its TMA stage): x-line minima M_L of
+//     half-length L = 0..r over 8 outputs per item, with
+//       M_1 = min3(v[-1], v[0], v[+1])            (odd shift: one byte permute)
+//       M_2 = min3(v[-2], M_1[0], v[+2])           (even shifts: whole words)
+//       M_L = min3(M_{L-2}[-2], M_{L-2}[0], M_{L-2}[+2])   (L >= 3)
+//     (cube: only M_r is kept);
+//   y + z (plane p-2): disk minima D_|dz| = min over dy of M_L(dy,dz)(y+dy),
+//     L(dy,dz) = floor(sqrt(r^2 - dy^2 - dz^2)) (cube: D = min over |dy| <= r
+//     of M_r), pushed into a shift-register ring of the 2r+1 outputs that
+//     plane p-2 contributes to; the oldest output is complete and stored.
+// One CTA barrier per phase. Tiles whose halo leaves the volume overwrite
+// the out-of-volume cells of the TMA stage with their reflected sources
+// before the x pass reads it.
+#include <cuda_fp16.h>
+
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "hp_device.cuh"
+#include "hp_internal.h"
+
+namespace hp {
+
+namespace {
+
+constexpr int kPX = 64;        // tile width (outputs along x)
+constexpr int kPY = 32;        // tile height
+constexpr int kPT = 256;       // threads per CTA
+constexpr int kPB = 4;         // rows per thread in the y and z passes
+constexpr int kPS = 4;         // TMA stages
+constexpr int kPC = kPX / 2;   // pair columns of the tile
+constexpr int kXI = 8;         // outputs per x-pass item (four pairs)
+constexpr int kMaxR16 = 6;
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+struct Morph16Params {
+  Job job;
+  int zchunk;
+  int tiles_x;
+  uint32_t flip;  // 0 for erosion, all ones for dilation
+  int* err;
+};
+
+__host__ __device__ constexpr int rup(int a, int b) { return (a + b - 1) / b * b; }
+
+// floor(sqrt(v)) for 0 <= v < 64 without a loop, so that it folds to a
+// constant inside unrolled loops.
+__host__ __device__ constexpr int isqrt63(int v) {
+  return (v >= 1) + (v >= 4) + (v >= 9) + (v >= 16) + (v >= 25) + (v >= 36) + (v >= 49);
+}
+
+// Half-length of the ball's x-line at (dz, dy); -1 outside the ball.
+__host__ __device__ constexpr int line_len(int R, int dz, int dy) {
+  return dz * dz + dy * dy <= R * R ? isqrt63(R * R - dz * dz - dy * dy) : -1;
+}
+
+template <int R, int BALL>
+struct PG {
+  static constexpr int BH = kPY + 2 * R;            // patch rows (y halo included)
+  static constexpr int RA = rup(R, 8);              // left halo of the TMA box (16-byte aligned)
+  static constexpr int BW = rup(kPX + RA + R, 8);   // TMA box width, elements
+  static constexpr int BWW = BW / 2;                // stage row stride, 32-bit words
+  static constexpr int HP = (R + 1) / 2;            // halo pairs per side of an x item
+  static constexpr int NW = kXI / 2 + 2 * HP;       // window pairs of an x item
+  static constexpr int W0 = RA / 2 - HP;            // stage word of window pair 0 of item 0
+  static constexpr int NXI = BH * (kPX / kXI);      // x items per plane
+  static constexpr int NL = BALL ? R + 1 : 1;       // stored line-minimum levels
+  static constexpr int NDZ = BALL ? R + 1 : 1;      // distinct disks
+  static constexpr int MSZ = NL * BH * kPC;         // words per line-minimum buffer
+  static constexpr int SB = rup(BW * BH * 2, 128);  // bytes per TMA stage
+  static constexpr int SMEM = 128 + kPS * SB + 2 * MSZ * 4;
+  static_assert(W0 >= 0 && RA / 2 + kPC + HP <= BWW, "x window inside the TMA box");
+};
+
+// 16-bit keys of a word holding two elements. float16: positive values get
+// the sign bit set, negative ones are complemented (order-preserving).
+template <int KIND>
+__device__ __forceinline__ uint32_t to_keys(uint32_t w, uint32_t flip) {
+  if (KIND == 1) {
+    const uint32_t s = (w >> 15) & 0x00010001u;
+    w ^= 0x80008000u | (s * 0x7FFFu);
+  }
+  return w ^ flip;
+}
+
+template <int KIND>
+__device__ __forceinline__ uint32_t from_keys(uint32_t k, uint32_t flip) {
+  k ^= flip;
+  if (KIND == 1) {
+    const uint32_t s = (k >> 15) & 0x00010001u;
+    k ^= 0xFFFFFFFFu ^ (s * 0x7FFFu);
+  }
+  return k;
+}
+
+__device__ __forceinline__ uint32_t min2(uint32_t a, uint32_t b) { return __vminu2(a, b); }
+__device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
+  return __vimin3_u16x2(a, b, c);
+}
+
+// x pass of one item: 8 outputs (pairs HP .. HP+3 of the window) of stage
+// row `row`, x group g. Window pair k holds x = cx0 + 8g - 2HP + 2k, +1.
+template <int R, int BALL, int KIND>
+__device__ __forceinline__ void xpass_item(uint32_t* Mb, const uint32_t* S, int row, int g,
+                                           uint32_t flip) {
+  using G = PG<R, BALL>;
+  constexpr int NW = G::NW;
+  const uint32_t* src = S + row * G::BWW + G::W0 + 4 * g;
+  uint32_t lv[R + 1][NW];
+  if constexpr (G::W0 % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < NW; k += 2) {
+      const uint2 v = *reinterpret_cast<const uint2*>(src + k);
+      lv[0][k] = to_keys<KIND>(v.x, flip);
+      lv[0][k + 1] = to_keys<KIND>(v.y, flip);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NW; ++k) lv[0][k] = to_keys<KIND>(src[k], flip);
+  }
+  // q[k] = (v at pair k high half, pair k+1 low half): the odd shift
+  uint32_t q[NW - 1];
+#pragma unroll
+  for (int k = 0; k + 1 < NW; ++k) q[k] = __byte_perm(lv[0][k], lv[0][k + 1], 0x5432);
+#pragma unroll
+  for (int k = 1; k + 1 < NW; ++k) lv[1][k] = min3(q[k - 1], lv[0][k], q[k]);
+  if constexpr (R >= 2) {
+#pragma unroll
+    for (int k = 1; k + 1 < NW; ++k) lv[2][k] = min3(lv[0][k - 1], lv[1][k], lv[0][k + 1]);
+  }
+#pragma unroll
+  for (int L = 3; L <= R; ++L) {
+    const int c = (L + 1) / 2;
+#pragma unroll
+    for (int k = c; k < NW - c; ++k) lv[L][k] = min3(lv[L - 2][k - 1], lv[L - 2][k], lv[L - 2][k + 1]);
+  }
+  uint32_t* dst = Mb + row * kPC + 4 * g;
+  constexpr int H = G::HP;
+  if constexpr (BALL) {
+#pragma unroll
+    for (int L = 0; L <= R; ++L)
+      *reinterpret_cast<uint4*>(dst + L * G::BH * kPC) =
+          make_uint4(lv[L][H], lv[L][H + 1], lv[L][H + 2], lv[L][H + 3]);
+  } else {
+    *reinterpret_cast<uint4*>(dst) = make_uint4(lv[R][H], lv[R][H + 1], lv[R][H + 2], lv[R][H + 3]);
+  }
+}
+
+// Disk minima of kPB consecutive output rows at one pair column. Mc points
+// at level 0, the row of output row 0 (dy = 0).
+template <int R, int BALL>
+__device__ __forceinline__ void disks(uint32_t (&D)[PG<R, BALL>::NDZ][kPB], const uint32_t* Mc) {
+  using G = PG<R, BALL>;
+  auto m = [&](int L, int i, int dy) { return Mc[(L * G::BH + i + dy) * kPC]; };
+  if constexpr (BALL && R == 3) {
+    // shared three-row minimum of M_2 (see the line lengths of the r = 3 ball)
+#pragma unroll
+    for (int i = 0; i < kPB; ++i) {
+      const uint32_t a = min3(m(2, i, -1), m(2, i, 0), m(2, i, 1));
+      const uint32_t d1 = min3(a, m(2, i, -2), m(2, i, 2));
+      D[1][i] = d1;
+      D[0][i] = min3(d1, m(3, i, 0), min2(m(0, i, -3), m(0, i, 3)));
+      D[2][i] = min3(a, m(1, i, -2), m(1, i, 2));
+      D[3][i] = m(0, i, 0);
+    }
+  } else {
+#pragma unroll
+    for (int dz = 0; dz < G::NDZ; ++dz)
+#pragma unroll
+      for (int i = 0; i < kPB; ++i) D[dz][i] = kInf;
+#pragma unroll
+    for (int dz = 0; dz < G::NDZ; ++dz)
+#pragma unroll
+      for (int dy = -R; dy <= R; ++dy) {
+        const int L = BALL ? line_len(R, dz, dy) : 0;
+        if (L >= 0) {
+#pragma unroll
+          for (int i = 0; i < kPB; ++i) D[dz][i] = min2(D[dz][i], m(L, i, dy));
+        }
+      }
+  }
+}
+
+template <int R, int BALL, int KIND>
+__global__ void __launch_bounds__(kPT, 2)
+    k_morph16(const __grid_constant__ Morph16Params P, const __grid_constant__ CUtensorMap tmap) {
+  using G = PG<R, BALL>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort;
+  __shared__ int s_frow[G::BH], s_fcol[G::BW], s_brow[G::BH], s_bcol[G::BW];
+  __shared__ int s_nbr, s_nbc;
+
+  const Job& J = P.job;
+  const int tid = threadIdx.x;
+  const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
+  const int64_t cx0 = J.core_lo[2] + (int64_t)tx * kPX;
+  const int64_t cy0 = J.core_lo[1] + (int64_t)ty * kPY;
+  const int64_t cz0 = J.core_lo[0] + (int64_t)blockIdx.y * P.zchunk;
+  const int64_t cz1 = min(cz0 + (int64_t)P.zchunk, J.core_hi[0]);
+  if (cz0 >= cz1) return;
+  const int nout = (int)(cz1 - cz0);
+  const int total = nout + 2 * R;  // input planes cz0-R .. cz1+R-1
+  const int64_t Gz = J.gdims[0], Gy = J.gdims[1], Gx = J.gdims[2];
+  const uint32_t flip = P.flip;
+  const bool face = (cx0 - R < 0) || (cx0 + kPX + R > Gx) || (cy0 - R < 0) || (cy0 + kPY + R > Gy);
+
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* stages = smem + 128;
+  uint32_t* M = reinterpret_cast<uint32_t*>(stages + kPS * G::SB);
+
+  if (face) {
+    // stage row r <-> y = cy0 - R + r, stage col c <-> x = cx0 - RA + c;
+    // -1 where the reflected source is outside the box (no stored output
+    // reads that cell)
+    for (int r = tid; r < G::BH; r += kPT) {
+      const int64_t s = reflect(cy0 - R + r, Gy) - (cy0 - R);
+      s_frow[r] = (s >= 0 && s < G::BH) ? (int)s : -1;
+    }
+    for (int c = tid; c < G::BW; c += kPT) {
+      const int64_t s = reflect(cx0 - G::RA + c, Gx) - (cx0 - G::RA);
+      s_fcol[c] = (s >= 0 && s < G::BW) ? (int)s : -1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int nr = 0, nc = 0;
+      for (int r = 0; r < G::BH; ++r)
+        if (s_frow[r] != r) s_brow[nr++] = r;
+      for (int c = 0; c < G::BW; ++c)
+        if (s_fcol[c] != c) s_bcol[nc++] = c;
+      s_nbr = nr;
+      s_nbc = nc;
+    }
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    prefetch_tmap(&tmap);
+    for (int s = 0; s < kPS; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int nbr = face ? s_nbr : 0, nbc = face ? s_nbc : 0;
+
+  auto issue = [&](int n) {  // TMA load of input plane n into stage n % kPS
+    const int zl = (int)(reflect(cz0 - R + n, Gz) - J.in.lo[0]);
+    const int xl = (int)(cx0 - G::RA - J.in.lo[2]);
+    const int yl = (int)(cy0 - R - J.in.lo[1]);
+    uint64_t* bar = &bars[n % kPS];
+    mbar_arrive_expect_tx(bar, G::BW * G::BH * 2);
+    tma_load_3d(stages + (n % kPS) * G::SB, &tmap, xl, yl, zl, bar);
+  };
+  int next_issue = min(kPS, total);
+  if (tid == 0) {
+    fence_proxy_async();
+    for (int n = 0; n < next_issue; ++n) issue(n);
+  }
+
+  // y/z role: pair column xp, rows yb .. yb + kPB - 1
+  const int xp = tid % kPC, yb = (tid / kPC) * kPB;
+  uint32_t acc[2 * R + 1][kPB];
+#pragma unroll
+  for (int j = 0; j <= 2 * R; ++j)
+#pragma unroll
+    for (int i = 0; i < kPB; ++i) acc[j][i] = kInf;
+  // output addressing: (gy, gx) fixed per thread, gz advances by one plane
+  const DevOut& O = J.out;
+  const int64_t gx = cx0 + 2 * xp;
+  const int64_t pstride = O.dims[1] * O.dims[2];
+  int64_t obase = ((cz0 - O.lo[0]) * O.dims[1] + (cy0 + yb - O.lo[1])) * O.dims[2] + (gx - O.lo[2]);
+  const bool xok = gx < J.core_hi[2], xpair = gx + 1 < J.core_hi[2];
+  int nrow = (int)min((int64_t)kPB, J.core_hi[1] - (cy0 + yb));
+
+  int p = 0;
+  for (; p < total + 2; ++p) {
+    if (p >= 1 && p <= total) {
+      const int n = p - 1;  // x pass of plane n
+      if (!mbar_wait(&bars[n % kPS], (n / kPS) & 1)) atomicOr(&s_abort, 1);
+      unsigned char* sb = stages + (n % kPS) * G::SB;
+      if (face) {
+        uint16_t* S16 = reinterpret_cast<uint16_t*>(sb);
+        auto cell = [&](int r, int c) -> uint16_t& { return S16[r * G::BW + c]; };
+        for (int i = tid; i < nbr * G::BW; i += kPT) {
+          const int r = s_brow[i / G::BW], c = i % G::BW;
+          const int sr = s_frow[r], sc = s_fcol[c];
+          cell(r, c) = (sr >= 0 && sc >= 0) ? cell(sr, sc) : (uint16_t)0;
+        }
+        for (int i = tid; i < nbc * G::BH; i += kPT) {
+          const int c = s_bcol[i / G::BH], r = i % G::BH;
+          const int sr = s_frow[r], sc = s_fcol[c];
+          cell(r, c) = (sr >= 0 && sc >= 0) ? cell(sr, sc) : (uint16_t)0;
+        }
+        fence_proxy_async();  // the stage is refilled by TMA later
+        __syncthreads();
+      }
+      uint32_t* Mb = M + (n & 1) * G::MSZ;
+      const uint32_t* S = reinterpret_cast<const uint32_t*>(sb);
+      for (int it = tid; it < G::NXI; it += kPT)
+        xpass_item<R, BALL, KIND>(Mb, S, it / (kPX / kXI), it % (kPX / kXI), flip);
+    }
+    if (p >= 2) {
+      const int n = p - 2;  // disks and z push of plane n
+      uint32_t D[G::NDZ][kPB];
+      disks<R, BALL>(D, M + (n & 1) * G::MSZ + (yb + R) * kPC + xp);
+      uint32_t out[kPB];
+#pragma unroll
+      for (int i = 0; i < kPB; ++i) {
+        out[i] = min2(acc[0][i], D[BALL ? R : 0][i]);
+#pragma unroll
+        for (int j = 1; j <= 2 * R; ++j) {
+          const int d = j > R ? j - R : R - j;
+          acc[j - 1][i] = min2(acc[j][i], D[BALL ? d : 0][i]);
+        }
+        acc[2 * R][i] = kInf;
+      }
+      if (n >= 2 * R && xok) {  // output plane cz0 + n - 2R is complete
+#pragma unroll
+        for (int i = 0; i < kPB; ++i) {
+          if (i < nrow) {
+            const uint32_t v = from_keys<KIND>(out[i], flip);
+            uint16_t* dst = static_cast<uint16_t*>(O.ptr) + obase + i * O.dims[2];
+            if (xpair)
+              *reinterpret_cast<uint32_t*>(dst) = v;
+            else
+              *dst = (uint16_t)v;
+          }
+        }
+        obase += pstride;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (p >= 1 && p - 1 + kPS < total) {  // plane p-1's stage is free again
+      if (tid == 0) {
+        fence_proxy_async();
+        issue(p - 1 + kPS);
+      }
+      next_issue = p + kPS;
+    }
+  }
+  if (s_abort) {
+    set_device_error(P.err, kErrTimeout);
+    // drain the TMA loads still in flight into this CTA's shared memory
+    if (tid == 0)
+      for (int n = max(0, p - 1); n < next_issue; ++n) (void)mbar_wait(&bars[n % kPS], (n / kPS) & 1);
+    __syncthreads();
+  }
+}
+
+template <int R, int BALL, int KIND>
+cudaError_t launch_t(const Morph16Params& P0, const CUtensorMap& map, int64_t tiles, int64_t cz,
+                     cudaStream_t s) {
+  using G = PG<R, BALL>;
+  static int slots_per_sm = 0;  // per instantiation, set once per process
+  if (!slots_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_morph16<R, BALL, KIND>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_morph16<R, BALL, KIND>, kPT, G::SMEM);
+    if (e != cudaSuccess) return e;
+    slots_per_sm = std::max(1, nb);
+  }
+  Morph16Params P = P0;
+  P.zchunk = (int)pick_zchunk(cz, tiles, (int64_t)slots_per_sm * num_sms(), 2 * R + 2, 1);
+  dim3 grid((unsigned)tiles, (unsigned)((cz + P.zchunk - 1) / P.zchunk));
+  if (log_level() > 0)
+    fprintf(stderr, "[hp] morph16 r=%d ball=%d kind=%d grid=%ux%u zchunk=%d slots/SM=%d\n", R,
+            BALL, KIND, grid.x, grid.y, P.zchunk, slots_per_sm);
+  k_morph16<R, BALL, KIND><<<grid, kPT, G::SMEM, s>>>(P, map);
+  return cudaGetLastError();
+}
+
+template <int BALL, int KIND>
+cudaError_t dispatch16(int r, const Morph16Params& P, const CUtensorMap& map, int64_t tiles,
+                       int64_t cz, cudaStream_t s) {
+  switch (r) {
+    case 1: return launch_t<1, BALL, KIND>(P, map, tiles, cz, s);
+    case 2: return launch_t<2, BALL, KIND>(P, map, tiles, cz, s);
+    case 3: return launch_t<3, BALL, KIND>(P, map, tiles, cz, s);
+    case 4: return launch_t<4, BALL, KIND>(P, map, tiles, cz, s);
+    case 5: return launch_t<5, BALL, KIND>(P, map, tiles, cz, s);
+    case 6: return launch_t<6, BALL, KIND>(P, map, tiles, cz, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// Returns cudaErrorNotSupported (nothing enqueued) when the job does not fit
+// this kernel: other dtypes, radius > 6, layouts TMA or the paired stores
+// cannot take.
+cudaError_t launch_morph16(const Job& job, int se, int rad, int is_dilate, cudaStream_t s) {
+  const int dt = job.in.dtype;
+  if ((dt != HP_U16 && dt != HP_F16) || job.out.dtype != dt) return cudaErrorNotSupported;
+  if (rad < 1 || rad > kMaxR16 || job.gdims[2] < rad || job.gdims[1] < rad)
+    return cudaErrorNotSupported;
+  const int64_t cx = job.core_hi[2] - job.core_lo[2];
+  const int64_t cy = job.core_hi[1] - job.core_lo[1];
+  const int64_t cz = job.core_hi[0] - job.core_lo[0];
+  if (cx <= 0 || cy <= 0 || cz <= 0) return cudaErrorNotSupported;
+  // TMA: 16-byte aligned base and row pitch, tile origins on 8-element
+  // boundaries; paired stores: 4-byte aligned output pairs.
+  if ((uintptr_t)job.in.ptr % 16 || (job.in.dims[2] * 2) % 16 || (job.core_lo[2] - job.in.lo[2]) % 8)
+    return cudaErrorNotSupported;
+  if ((uintptr_t)job.out.ptr % 4 || job.out.dims[2] % 2 || (job.core_lo[2] - job.out.lo[2]) % 2)
+    return cudaErrorNotSupported;
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const int64_t dims[3] = {job.in.dims[2], job.in.dims[1], job.in.dims[0]};
+  const int ra = rup(rad, 8);
+  if (!make_tmap_3d(&map, job.in.ptr, dt, dims, rup(kPX + ra + rad, 8), kPY + 2 * rad))
+    return cudaErrorNotSupported;
+  Morph16Params P;
+  P.job = job;
+  P.tiles_x = (int)((cx + kPX - 1) / kPX);
+  P.zchunk = 0;
+  P.flip = is_dilate ? 0xFFFFFFFFu : 0u;
+  P.err = device_error_word();
+  const int64_t tiles = (int64_t)P.tiles_x * ((cy + kPY - 1) / kPY);
+  const int ball = se == HP_SE_BALL;
+  if (dt == HP_U16)
+    return ball ? dispatch16<1, 0>(rad, P, map, tiles, cz, s) : dispatch16<0, 0>(rad, P, map, tiles, cz, s);
+  return ball ? dispatch16<1, 1>(rad, P, map, tiles, cz, s) : dispatch16<0, 1>(rad, P, map, tiles, cz, s);
+}
+
+}  // namespace hp

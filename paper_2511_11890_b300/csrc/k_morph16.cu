@@ -4,9 +4,9 @@
 //
 // Two x-neighbours share one 32-bit register: the pair (x, x+1) of
 // order-preserving 16-bit keys, so every min is one SIMD instruction over
-// two voxels (__vminu2 / the three-input __vimin3_u16x2). uint16 keys are
-// the values themselves, float16 keys the sign-magnitude flip, dilation the
-// complement, all applied to whole 32-bit words.
+// two voxels (__vminu2 / the three-input __vimin3_u16x2; dilation uses the
+// max forms). uint16 keys are the values themselves, float16 keys the
+// sign-magnitude flip applied to whole 32-bit words.
 //
 // Tiled z-march: a CTA owns a 64 x 32 column of the core and marches along
 // z through a 4-stage TMA pipeline of halo-padded planes. Phase p:
@@ -29,6 +29,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "hp_device.cuh"
 #include "hp_internal.h"
@@ -45,13 +46,11 @@ constexpr int kPS = 4;         // TMA stages
 constexpr int kPC = kPX / 2;   // pair columns of the tile
 constexpr int kXI = 8;         // outputs per x-pass item (four pairs)
 constexpr int kMaxR16 = 6;
-constexpr uint32_t kInf = 0xFFFFFFFFu;
 
 struct Morph16Params {
   Job job;
   int zchunk;
   int tiles_x;
-  uint32_t flip;  // 0 for erosion, all ones for dilation
   int* err;
 };
 
@@ -89,17 +88,16 @@ struct PG {
 // 16-bit keys of a word holding two elements. float16: positive values get
 // the sign bit set, negative ones are complemented (order-preserving).
 template <int KIND>
-__device__ __forceinline__ uint32_t to_keys(uint32_t w, uint32_t flip) {
+__device__ __forceinline__ uint32_t to_keys(uint32_t w) {
   if (KIND == 1) {
     const uint32_t s = (w >> 15) & 0x00010001u;
     w ^= 0x80008000u | (s * 0x7FFFu);
   }
-  return w ^ flip;
+  return w;
 }
 
 template <int KIND>
-__device__ __forceinline__ uint32_t from_keys(uint32_t k, uint32_t flip) {
-  k ^= flip;
+__device__ __forceinline__ uint32_t from_keys(uint32_t k) {
   if (KIND == 1) {
     const uint32_t s = (k >> 15) & 0x00010001u;
     k ^= 0xFFFFFFFFu ^ (s * 0x7FFFu);
@@ -107,17 +105,24 @@ __device__ __forceinline__ uint32_t from_keys(uint32_t k, uint32_t flip) {
   return k;
 }
 
-__device__ __forceinline__ uint32_t min2(uint32_t a, uint32_t b) { return __vminu2(a, b); }
-__device__ __forceinline__ uint32_t min3(uint32_t a, uint32_t b, uint32_t c) {
-  return __vimin3_u16x2(a, b, c);
-}
+// Erosion takes minima, dilation maxima (of the same keys).
+template <int DIL>
+struct Op {
+  static constexpr uint32_t id = DIL ? 0u : 0xFFFFFFFFu;  // identity element
+  static __device__ __forceinline__ uint32_t f2(uint32_t a, uint32_t b) {
+    return DIL ? __vmaxu2(a, b) : __vminu2(a, b);
+  }
+  static __device__ __forceinline__ uint32_t f3(uint32_t a, uint32_t b, uint32_t c) {
+    return DIL ? __vimax3_u16x2(a, b, c) : __vimin3_u16x2(a, b, c);
+  }
+};
 
 // x pass of one item: 8 outputs (pairs HP .. HP+3 of the window) of stage
 // row `row`, x group g. Window pair k holds x = cx0 + 8g - 2HP + 2k, +1.
-template <int R, int BALL, int KIND>
-__device__ __forceinline__ void xpass_item(uint32_t* Mb, const uint32_t* S, int row, int g,
-                                           uint32_t flip) {
+template <int R, int BALL, int KIND, int DIL>
+__device__ __forceinline__ void xpass_item(uint32_t* Mb, const uint32_t* S, int row, int g) {
   using G = PG<R, BALL>;
+  using O = Op<DIL>;
   constexpr int NW = G::NW;
   const uint32_t* src = S + row * G::BWW + G::W0 + 4 * g;
   uint32_t lv[R + 1][NW];
@@ -125,28 +130,28 @@ __device__ __forceinline__ void xpass_item(uint32_t* Mb, const uint32_t* S, int 
 #pragma unroll
     for (int k = 0; k < NW; k += 2) {
       const uint2 v = *reinterpret_cast<const uint2*>(src + k);
-      lv[0][k] = to_keys<KIND>(v.x, flip);
-      lv[0][k + 1] = to_keys<KIND>(v.y, flip);
+      lv[0][k] = to_keys<KIND>(v.x);
+      lv[0][k + 1] = to_keys<KIND>(v.y);
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < NW; ++k) lv[0][k] = to_keys<KIND>(src[k], flip);
+    for (int k = 0; k < NW; ++k) lv[0][k] = to_keys<KIND>(src[k]);
   }
   // q[k] = (v at pair k high half, pair k+1 low half): the odd shift
   uint32_t q[NW - 1];
 #pragma unroll
   for (int k = 0; k + 1 < NW; ++k) q[k] = __byte_perm(lv[0][k], lv[0][k + 1], 0x5432);
 #pragma unroll
-  for (int k = 1; k + 1 < NW; ++k) lv[1][k] = min3(q[k - 1], lv[0][k], q[k]);
+  for (int k = 1; k + 1 < NW; ++k) lv[1][k] = O::f3(q[k - 1], lv[0][k], q[k]);
   if constexpr (R >= 2) {
 #pragma unroll
-    for (int k = 1; k + 1 < NW; ++k) lv[2][k] = min3(lv[0][k - 1], lv[1][k], lv[0][k + 1]);
+    for (int k = 1; k + 1 < NW; ++k) lv[2][k] = O::f3(lv[0][k - 1], lv[1][k], lv[0][k + 1]);
   }
 #pragma unroll
   for (int L = 3; L <= R; ++L) {
     const int c = (L + 1) / 2;
 #pragma unroll
-    for (int k = c; k < NW - c; ++k) lv[L][k] = min3(lv[L - 2][k - 1], lv[L - 2][k], lv[L - 2][k + 1]);
+    for (int k = c; k < NW - c; ++k) lv[L][k] = O::f3(lv[L - 2][k - 1], lv[L - 2][k], lv[L - 2][k + 1]);
   }
   uint32_t* dst = Mb + row * kPC + 4 * g;
   constexpr int H = G::HP;
@@ -162,26 +167,27 @@ __device__ __forceinline__ void xpass_item(uint32_t* Mb, const uint32_t* S, int 
 
 // Disk minima of kPB consecutive output rows at one pair column. Mc points
 // at level 0, the row of output row 0 (dy = 0).
-template <int R, int BALL>
+template <int R, int BALL, int DIL>
 __device__ __forceinline__ void disks(uint32_t (&D)[PG<R, BALL>::NDZ][kPB], const uint32_t* Mc) {
   using G = PG<R, BALL>;
+  using O = Op<DIL>;
   auto m = [&](int L, int i, int dy) { return Mc[(L * G::BH + i + dy) * kPC]; };
   if constexpr (BALL && R == 3) {
     // shared three-row minimum of M_2 (see the line lengths of the r = 3 ball)
 #pragma unroll
     for (int i = 0; i < kPB; ++i) {
-      const uint32_t a = min3(m(2, i, -1), m(2, i, 0), m(2, i, 1));
-      const uint32_t d1 = min3(a, m(2, i, -2), m(2, i, 2));
+      const uint32_t a = O::f3(m(2, i, -1), m(2, i, 0), m(2, i, 1));
+      const uint32_t d1 = O::f3(a, m(2, i, -2), m(2, i, 2));
       D[1][i] = d1;
-      D[0][i] = min3(d1, m(3, i, 0), min2(m(0, i, -3), m(0, i, 3)));
-      D[2][i] = min3(a, m(1, i, -2), m(1, i, 2));
+      D[0][i] = O::f3(d1, m(3, i, 0), O::f2(m(0, i, -3), m(0, i, 3)));
+      D[2][i] = O::f3(a, m(1, i, -2), m(1, i, 2));
       D[3][i] = m(0, i, 0);
     }
   } else {
 #pragma unroll
     for (int dz = 0; dz < G::NDZ; ++dz)
 #pragma unroll
-      for (int i = 0; i < kPB; ++i) D[dz][i] = kInf;
+      for (int i = 0; i < kPB; ++i) D[dz][i] = O::id;
 #pragma unroll
     for (int dz = 0; dz < G::NDZ; ++dz)
 #pragma unroll
@@ -189,16 +195,24 @@ __device__ __forceinline__ void disks(uint32_t (&D)[PG<R, BALL>::NDZ][kPB], cons
         const int L = BALL ? line_len(R, dz, dy) : 0;
         if (L >= 0) {
 #pragma unroll
-          for (int i = 0; i < kPB; ++i) D[dz][i] = min2(D[dz][i], m(L, i, dy));
+          for (int i = 0; i < kPB; ++i) D[dz][i] = O::f2(D[dz][i], m(L, i, dy));
         }
       }
   }
 }
 
-template <int R, int BALL, int KIND>
-__global__ void __launch_bounds__(kPT, 2)
+// Resident CTAs per SM the register budget is sized for: three for radii up
+// to 3 (63 KB of shared memory per CTA), two above.
+template <int R>
+struct MinBlocks {
+  static constexpr int value = R <= 3 ? 3 : 2;
+};
+
+template <int R, int BALL, int KIND, int DIL>
+__global__ void __launch_bounds__(kPT, MinBlocks<R>::value)
     k_morph16(const __grid_constant__ Morph16Params P, const __grid_constant__ CUtensorMap tmap) {
   using G = PG<R, BALL>;
+  using O = Op<DIL>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort;
   __shared__ int s_frow[G::BH], s_fcol[G::BW], s_brow[G::BH], s_bcol[G::BW];
@@ -215,7 +229,6 @@ __global__ void __launch_bounds__(kPT, 2)
   const int nout = (int)(cz1 - cz0);
   const int total = nout + 2 * R;  // input planes cz0-R .. cz1+R-1
   const int64_t Gz = J.gdims[0], Gy = J.gdims[1], Gx = J.gdims[2];
-  const uint32_t flip = P.flip;
   const bool face = (cx0 - R < 0) || (cx0 + kPX + R > Gx) || (cy0 - R < 0) || (cy0 + kPY + R > Gy);
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -274,19 +287,23 @@ __global__ void __launch_bounds__(kPT, 2)
 #pragma unroll
   for (int j = 0; j <= 2 * R; ++j)
 #pragma unroll
-    for (int i = 0; i < kPB; ++i) acc[j][i] = kInf;
-  // output addressing: (gy, gx) fixed per thread, gz advances by one plane
-  const DevOut& O = J.out;
+    for (int i = 0; i < kPB; ++i) acc[j][i] = O::id;
+  // output addressing: rows of this thread, one plane further per store
+  const DevOut& Ob = J.out;
   const int64_t gx = cx0 + 2 * xp;
-  const int64_t pstride = O.dims[1] * O.dims[2];
-  int64_t obase = ((cz0 - O.lo[0]) * O.dims[1] + (cy0 + yb - O.lo[1])) * O.dims[2] + (gx - O.lo[2]);
+  const int64_t pstride = Ob.dims[1] * Ob.dims[2], rstride = Ob.dims[2];
+  uint16_t* optr = static_cast<uint16_t*>(Ob.ptr) +
+                   ((cz0 - Ob.lo[0]) * Ob.dims[1] + (cy0 + yb - Ob.lo[1])) * Ob.dims[2] + (gx - Ob.lo[2]);
   const bool xok = gx < J.core_hi[2], xpair = gx + 1 < J.core_hi[2];
-  int nrow = (int)min((int64_t)kPB, J.core_hi[1] - (cy0 + yb));
+  const int nrow = xok ? (int)max((int64_t)0, min((int64_t)kPB, J.core_hi[1] - (cy0 + yb))) : 0;
+  const bool full = xpair && nrow == kPB;
 
-  int p = 0;
-  for (; p < total + 2; ++p) {
-    if (p >= 1 && p <= total) {
-      const int n = p - 1;  // x pass of plane n
+  // One phase p: x pass of plane p-1, disks + z push of plane p-2, store of
+  // output plane cz0 + p - 2 - 2R. STEADY: all three parts are known to run.
+  auto phase = [&](int p, auto steady) {
+    constexpr bool ST = decltype(steady)::value;
+    if (ST || (p >= 1 && p <= total)) {
+      const int n = p - 1;
       if (!mbar_wait(&bars[n % kPS], (n / kPS) & 1)) atomicOr(&s_abort, 1);
       unsigned char* sb = stages + (n % kPS) * G::SB;
       if (face) {
@@ -307,41 +324,47 @@ __global__ void __launch_bounds__(kPT, 2)
       }
       uint32_t* Mb = M + (n & 1) * G::MSZ;
       const uint32_t* S = reinterpret_cast<const uint32_t*>(sb);
-      for (int it = tid; it < G::NXI; it += kPT)
-        xpass_item<R, BALL, KIND>(Mb, S, it / (kPX / kXI), it % (kPX / kXI), flip);
+      xpass_item<R, BALL, KIND, DIL>(Mb, S, tid / (kPX / kXI), tid % (kPX / kXI));
+      if (G::NXI > kPT && tid < G::NXI - kPT)
+        xpass_item<R, BALL, KIND, DIL>(Mb, S, (tid + kPT) / (kPX / kXI), (tid + kPT) % (kPX / kXI));
     }
-    if (p >= 2) {
-      const int n = p - 2;  // disks and z push of plane n
+    if (ST || p >= 2) {
+      const int n = p - 2;
       uint32_t D[G::NDZ][kPB];
-      disks<R, BALL>(D, M + (n & 1) * G::MSZ + (yb + R) * kPC + xp);
+      disks<R, BALL, DIL>(D, M + (n & 1) * G::MSZ + (yb + R) * kPC + xp);
       uint32_t out[kPB];
 #pragma unroll
       for (int i = 0; i < kPB; ++i) {
-        out[i] = min2(acc[0][i], D[BALL ? R : 0][i]);
+        out[i] = O::f2(acc[0][i], D[BALL ? R : 0][i]);
 #pragma unroll
         for (int j = 1; j <= 2 * R; ++j) {
           const int d = j > R ? j - R : R - j;
-          acc[j - 1][i] = min2(acc[j][i], D[BALL ? d : 0][i]);
+          acc[j - 1][i] = O::f2(acc[j][i], D[BALL ? d : 0][i]);
         }
-        acc[2 * R][i] = kInf;
+        acc[2 * R][i] = O::id;
       }
-      if (n >= 2 * R && xok) {  // output plane cz0 + n - 2R is complete
+      if (ST || n >= 2 * R) {  // output plane cz0 + n - 2R is complete
+        if (full) {
 #pragma unroll
-        for (int i = 0; i < kPB; ++i) {
-          if (i < nrow) {
-            const uint32_t v = from_keys<KIND>(out[i], flip);
-            uint16_t* dst = static_cast<uint16_t*>(O.ptr) + obase + i * O.dims[2];
-            if (xpair)
-              *reinterpret_cast<uint32_t*>(dst) = v;
-            else
-              *dst = (uint16_t)v;
+          for (int i = 0; i < kPB; ++i)
+            *reinterpret_cast<uint32_t*>(optr + i * rstride) = from_keys<KIND>(out[i]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < kPB; ++i) {
+            if (i < nrow) {
+              const uint32_t v = from_keys<KIND>(out[i]);
+              if (xpair)
+                *reinterpret_cast<uint32_t*>(optr + i * rstride) = v;
+              else
+                optr[i * rstride] = (uint16_t)v;
+            }
           }
         }
-        obase += pstride;
+        optr += pstride;
       }
     }
     __syncthreads();
-    if (s_abort) break;
+    if (s_abort) return false;
     if (p >= 1 && p - 1 + kPS < total) {  // plane p-1's stage is free again
       if (tid == 0) {
         fence_proxy_async();
@@ -349,8 +372,19 @@ __global__ void __launch_bounds__(kPT, 2)
       }
       next_issue = p + kPS;
     }
-  }
-  if (s_abort) {
+    return true;
+  };
+  static_assert(G::NXI <= 2 * kPT, "at most two x items per thread");
+
+  // head (pipeline fill), steady state, tail (pipeline drain)
+  const int s0 = 2 * R + 2, s1 = total + 1;  // steady phases: s0 <= p < s1
+  int p = 0;
+  bool ok = true;
+  for (; ok && p < min(s0, total + 2); ++p) ok = phase(p, std::false_type());
+  for (; ok && p < s1; ++p) ok = phase(p, std::true_type());
+  for (; ok && p < total + 2; ++p) ok = phase(p, std::false_type());
+  if (!ok) {
+    --p;  // the phase that saw the abort
     set_device_error(P.err, kErrTimeout);
     // drain the TMA loads still in flight into this CTA's shared memory
     if (tid == 0)
@@ -359,17 +393,17 @@ __global__ void __launch_bounds__(kPT, 2)
   }
 }
 
-template <int R, int BALL, int KIND>
+template <int R, int BALL, int KIND, int DIL>
 cudaError_t launch_t(const Morph16Params& P0, const CUtensorMap& map, int64_t tiles, int64_t cz,
                      cudaStream_t s) {
   using G = PG<R, BALL>;
   static int slots_per_sm = 0;  // per instantiation, set once per process
   if (!slots_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_morph16<R, BALL, KIND>,
+    cudaError_t e = cudaFuncSetAttribute(k_morph16<R, BALL, KIND, DIL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     if (e != cudaSuccess) return e;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_morph16<R, BALL, KIND>, kPT, G::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_morph16<R, BALL, KIND, DIL>, kPT, G::SMEM);
     if (e != cudaSuccess) return e;
     slots_per_sm = std::max(1, nb);
   }
@@ -377,24 +411,31 @@ cudaError_t launch_t(const Morph16Params& P0, const CUtensorMap& map, int64_t ti
   P.zchunk = (int)pick_zchunk(cz, tiles, (int64_t)slots_per_sm * num_sms(), 2 * R + 2, 1);
   dim3 grid((unsigned)tiles, (unsigned)((cz + P.zchunk - 1) / P.zchunk));
   if (log_level() > 0)
-    fprintf(stderr, "[hp] morph16 r=%d ball=%d kind=%d grid=%ux%u zchunk=%d slots/SM=%d\n", R,
-            BALL, KIND, grid.x, grid.y, P.zchunk, slots_per_sm);
-  k_morph16<R, BALL, KIND><<<grid, kPT, G::SMEM, s>>>(P, map);
+    fprintf(stderr, "[hp] morph16 r=%d ball=%d kind=%d dilate=%d grid=%ux%u zchunk=%d slots/SM=%d\n",
+            R, BALL, KIND, DIL, grid.x, grid.y, P.zchunk, slots_per_sm);
+  k_morph16<R, BALL, KIND, DIL><<<grid, kPT, G::SMEM, s>>>(P, map);
   return cudaGetLastError();
 }
 
-template <int BALL, int KIND>
+template <int BALL, int KIND, int DIL>
 cudaError_t dispatch16(int r, const Morph16Params& P, const CUtensorMap& map, int64_t tiles,
                        int64_t cz, cudaStream_t s) {
   switch (r) {
-    case 1: return launch_t<1, BALL, KIND>(P, map, tiles, cz, s);
-    case 2: return launch_t<2, BALL, KIND>(P, map, tiles, cz, s);
-    case 3: return launch_t<3, BALL, KIND>(P, map, tiles, cz, s);
-    case 4: return launch_t<4, BALL, KIND>(P, map, tiles, cz, s);
-    case 5: return launch_t<5, BALL, KIND>(P, map, tiles, cz, s);
-    case 6: return launch_t<6, BALL, KIND>(P, map, tiles, cz, s);
+    case 1: return launch_t<1, BALL, KIND, DIL>(P, map, tiles, cz, s);
+    case 2: return launch_t<2, BALL, KIND, DIL>(P, map, tiles, cz, s);
+    case 3: return launch_t<3, BALL, KIND, DIL>(P, map, tiles, cz, s);
+    case 4: return launch_t<4, BALL, KIND, DIL>(P, map, tiles, cz, s);
+    case 5: return launch_t<5, BALL, KIND, DIL>(P, map, tiles, cz, s);
+    case 6: return launch_t<6, BALL, KIND, DIL>(P, map, tiles, cz, s);
   }
   return cudaErrorInvalidValue;
+}
+
+template <int KIND, int DIL>
+cudaError_t dispatch_se(int ball, int r, const Morph16Params& P, const CUtensorMap& map,
+                        int64_t tiles, int64_t cz, cudaStream_t s) {
+  return ball ? dispatch16<1, KIND, DIL>(r, P, map, tiles, cz, s)
+              : dispatch16<0, KIND, DIL>(r, P, map, tiles, cz, s);
 }
 
 }  // namespace
@@ -427,13 +468,14 @@ cudaError_t launch_morph16(const Job& job, int se, int rad, int is_dilate, cudaS
   P.job = job;
   P.tiles_x = (int)((cx + kPX - 1) / kPX);
   P.zchunk = 0;
-  P.flip = is_dilate ? 0xFFFFFFFFu : 0u;
   P.err = device_error_word();
   const int64_t tiles = (int64_t)P.tiles_x * ((cy + kPY - 1) / kPY);
   const int ball = se == HP_SE_BALL;
   if (dt == HP_U16)
-    return ball ? dispatch16<1, 0>(rad, P, map, tiles, cz, s) : dispatch16<0, 0>(rad, P, map, tiles, cz, s);
-  return ball ? dispatch16<1, 1>(rad, P, map, tiles, cz, s) : dispatch16<0, 1>(rad, P, map, tiles, cz, s);
+    return is_dilate ? dispatch_se<0, 1>(ball, rad, P, map, tiles, cz, s)
+                     : dispatch_se<0, 0>(ball, rad, P, map, tiles, cz, s);
+  return is_dilate ? dispatch_se<1, 1>(ball, rad, P, map, tiles, cz, s)
+                   : dispatch_se<1, 0>(ball, rad, P, map, tiles, cz, s);
 }
 
 }  // namespace hp

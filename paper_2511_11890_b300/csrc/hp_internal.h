@@ -81,6 +81,7 @@ int* device_error_word();
 
 // Launchers (enqueue only). Return a cudaError_t.
 cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s);
+cudaError_t launch_gauss_zr(const Job& job, const Taps& taps, cudaStream_t s);
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
 cudaError_t launch_morph16(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
 cudaError_t launch_threshold(const Job& job, double t, cudaStream_t s);

@@ -661,6 +661,9 @@ cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
 
 cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s) {
   const int r = taps.r;
+  // register z-march (k_gauss_zr.cu) wherever its layout rules hold
+  const cudaError_t ezr = launch_gauss_zr(job, taps, s);
+  if (ezr != cudaErrorNotSupported) return ezr;
   bool tiled = r >= 1 && r <= kMaxR && job.gdims[2] >= r && job.gdims[1] >= r;
   if (!tiled) return launch_generic(job, taps, s);
 

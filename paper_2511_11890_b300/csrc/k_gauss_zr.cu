@@ -20,8 +20,10 @@
 //          output q-2R+i, whose slot is (q+1+i) mod (2R+1); the slot of
 //          output q-2R is then complete, stored and cleared. The slot
 //          rotation is a switch on q mod (2R+1) over compile-time slot maps.
-// Phase j runs P1 on plane group j, P2 on group j-1 and Z on group j-2 (X and
-// Zb double-buffered); P1 and P2 items of a group are spread over all threads.
+// Phase j runs P1 on plane group j and Z on group j-1, then (after a
+// barrier) P2 on group j; X and Zb are single-buffered (each is written and
+// read on opposite sides of a barrier), and the P1 and P2 items of a group
+// are spread over all threads.
 //
 // Every output is accumulated in FP32 with fma, starting from 0, over the
 // taps of each axis in increasing input coordinate (x, then y, then z). That
@@ -44,7 +46,7 @@ namespace {
 typedef unsigned long long u64;
 
 constexpr int kKP = 4;   // input planes per pipeline phase (= TMA box depth)
-constexpr int kNSG = 2;  // plane groups in flight (stage ring depth)
+constexpr int kNSG = 3;  // plane groups in flight (stage ring depth)
 constexpr int kFixC = 4; // face cells a thread patches from its register list
 
 struct ZrParams {
@@ -65,13 +67,14 @@ inline uint32_t f32_bits(float f) {
 }
 
 // Tile and thread shape per radius: wide, short tiles for small radii (the x
-// pass repeats 2R halo rows; two CTAs per SM), square tiles for larger ones
-// (one CTA of 512 threads per SM, one x pair of z state per thread).
+// pass repeats 2R halo rows; two CTAs of 256 threads per SM, two x pairs of
+// z state per thread), square tiles for larger ones (one CTA of 512 threads
+// per SM, one x pair per thread).
 template <int R>
 struct ZrShape {
-  static constexpr int TX = R <= 4 ? 64 : 32;
-  static constexpr int TY = R <= 4 ? 16 : 32;
-  static constexpr int ZP = R <= 4 ? 2 : 1;
+  static constexpr int TX = R <= 6 ? 64 : 32;
+  static constexpr int TY = R <= 6 ? 16 : 32;
+  static constexpr int ZP = R <= 6 ? 2 : 1;
   static constexpr int NT = TX * TY / (2 * ZP);
   static constexpr int NY = 8;
   static constexpr int MINB = NT >= 512 ? 1 : 2;
@@ -103,7 +106,7 @@ struct ZrGeom {
   static constexpr int NI1 = 8 * GH * ((RPN + 1) / 2);  // P1 slots per plane
   static constexpr int NI2 = ZW * (TY / NY);             // P2 items per plane
   static constexpr int NC = TX + 2 * R;       // raw columns P1 reads
-  static constexpr int SMEM = 128 + kNSG * GB + 2 * kKP * XP * 4 + 2 * kKP * ZPL * 8;
+  static constexpr int SMEM = 128 + kNSG * GB + kKP * XP * 4 + kKP * ZPL * 8;
   static_assert(BH % 2 == 0 && TY % NY == 0 && G1 % 4 == 0 && NI1 % 8 == 0, "tile shape");
   static_assert(PB % 128 == 0, "stage planes on 128-byte boundaries");
   static_assert((8 + 2 * RA) * ES % 16 == 0, "P1 window in whole 16-byte words");
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   unsigned char* stages = smem + 128;
   float* Xb = reinterpret_cast<float*>(stages + NSG * G::GB);
-  u64* Zb = reinterpret_cast<u64*>(Xb + 2 * KP * G::XP);
+  u64* Zb = reinterpret_cast<u64*>(Xb + KP * G::XP);
 
   // Face tiles: stage cells outside the volume (TMA zero fill) take the
   // value of their reflected source, which lies inside the volume and the
@@ -366,15 +369,17 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
     for (int i = 0; i < L; ++i) acc[zp][i] = 0ull;
   int ph = 0;  // z input plane index mod L
 
+  // Phase j, part 1: P1 (x pass) of group j into X, Z of group j-1 from Zb;
+  // part 2 (after a barrier): P2 (y pass) of group j from X into Zb, and the
+  // face patch of group j+1. The TMA refill of stage j%NSG is issued at the
+  // mid-phase barrier, right after P1 has read it.
   int j = 0;
-  for (; j < ngroups + 2; ++j) {
+  for (; j < ngroups + 1; ++j) {
     if (j < ngroups) {
-      // P1: x pass of group j; slot -> (row pair rp, 8-column group g); 8
-      // consecutive threads cover 4 groups of 2 row pairs (conflict-free
-      // stage loads)
+      // P1: slot -> (row pair rp, 8-column group g); 8 consecutive threads
+      // cover 4 groups of 2 row pairs (conflict-free stage loads)
       if (!face && tid < KP * G::NI1) wait_group(j);
       const unsigned char* sg = stages + (j % NSG) * G::GB;
-      float* xg = Xb + (j & 1) * KP * G::XP;
       const int nv = min(KP, total - j * KP);
 #pragma unroll 1
       for (int i1 = tid; i1 < KP * G::NI1; i1 += NT) {
@@ -403,7 +408,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
             if (t >= 0 && t <= 2 * R) o[i] = ffma2(P.w2[2][t], v, o[i]);
           }
         }
-        float* x0 = xg + k * G::XP + (2 * rp) * XS + 8 * g;
+        float* x0 = Xb + k * G::XP + (2 * rp) * XS + 8 * g;
         float2 u[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) u[i] = unpack2(o[i]);
@@ -413,57 +418,33 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
         reinterpret_cast<float4*>(x0 + XS)[1] = make_float4(u[4].y, u[5].y, u[6].y, u[7].y);
       }
     }
-    if (face && j + 1 < ngroups) fix_group(j + 1);
-    if (j >= 1 && j - 1 < ngroups) {
-      // P2: y pass of group j-1; item -> (plane k, x pair xp, row block b)
-      const float* xg = Xb + ((j - 1) & 1) * KP * G::XP;
-      u64* zg = Zb + ((j - 1) & 1) * KP * G::ZPL;
-      const int nv = min(KP, total - (j - 1) * KP);
-#pragma unroll 1
-      for (int i2 = tid; i2 < KP * G::NI2; i2 += NT) {
-        const int k = i2 / G::NI2, t2 = i2 - k * G::NI2;
-        if (k >= nv) continue;
-        const int xp = t2 % ZW, b = t2 / ZW;
-        // rows NY*b .. NY*b+NY-1 of x pair xp; X row j' <-> y - R
-        const float* xs = xg + k * G::XP + (NY * b) * XS + 2 * xp;
-        u64 o[NY];
+    if (j >= 1) {
+      // Z: planes of group j-1 (inputs loaded up front)
+      const int q0 = (j - 1) * KP;
+      const int nv = min(KP, total - q0);
+      const u64* zg = Zb + zy * ZW + ZP * zxg;
+      u64 v[KP][ZP];
 #pragma unroll
-        for (int i = 0; i < NY; ++i) o[i] = 0ull;
-#pragma unroll
-        for (int jj = 0; jj < NY + 2 * R; ++jj) {
-          const u64 v = *reinterpret_cast<const u64*>(xs + jj * XS);
-#pragma unroll
-          for (int i = 0; i < NY; ++i) {
-            const int t = 2 * R + i - jj;
-            if (t >= 0 && t <= 2 * R) o[i] = ffma2(P.w2[1][t], v, o[i]);
+      for (int k = 0; k < KP; ++k) {
+        if (k < nv) {
+          if constexpr (ZP == 2) {
+            const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(zg + k * G::ZPL);
+            v[k][0] = t.x;
+            v[k][1] = t.y;
+          } else {
+            v[k][0] = zg[k * G::ZPL];
           }
         }
-        u64* zd = zg + k * G::ZPL + (NY * b) * ZW + xp;
-#pragma unroll
-        for (int i = 0; i < NY; ++i) zd[i * ZW] = o[i];
       }
-    }
-    if (j >= 2) {
-      // Z: planes of group j-2
-      const u64* zg = Zb + (j & 1) * KP * G::ZPL + zy * ZW + ZP * zxg;  // (j-2)&1 == j&1
-      const int q0 = (j - 2) * KP;
-      const int nv = min(KP, total - q0);
-#pragma unroll 1
-      for (int k = 0; k < nv; ++k) {
-        const u64* zs = zg + k * G::ZPL;
-        u64 v[ZP];
-        if constexpr (ZP == 2) {
-          const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(zs);
-          v[0] = t.x;
-          v[1] = t.y;
-        } else {
-          v[0] = zs[0];
-        }
+      unsigned char* ob = obase + (int64_t)(q0 - 2 * R) * pstride_b;
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        if (k >= nv) break;
         u64 done[ZP];
         switch (ph) {
-#define HP_ZC(kk)                                                             \
-  case kk:                                                                    \
-    if constexpr (kk < L) zstep<(kk < L ? kk : 0), L, ZP>(acc, v, P, done); \
+#define HP_ZC(kk)                                                                \
+  case kk:                                                                       \
+    if constexpr (kk < L) zstep<(kk < L ? kk : 0), L, ZP>(acc, v[k], P, done); \
     break;
           HP_ZC(0) HP_ZC(1) HP_ZC(2) HP_ZC(3) HP_ZC(4) HP_ZC(5) HP_ZC(6) HP_ZC(7) HP_ZC(8)
           HP_ZC(9) HP_ZC(10) HP_ZC(11) HP_ZC(12) HP_ZC(13) HP_ZC(14) HP_ZC(15) HP_ZC(16)
@@ -474,7 +455,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
         ph = ph + 1 == L ? 0 : ph + 1;
         const int oz = q0 + k - 2 * R;  // completed output plane (relative)
         if (oz >= 0 && zrow) {
-          unsigned char* dstb = obase + (int64_t)oz * pstride_b;
+          unsigned char* dstb = ob + k * pstride_b;
           if (ovec) {
             if (of32) {
               if constexpr (ZP == 2)
@@ -510,12 +491,42 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
     __syncthreads();
     if (s_abort) break;
     if (tid == 0 && j + NSG < ngroups) issue(j + NSG);
+    if (j < ngroups) {
+      // P2: y pass of group j; item -> (plane k, x pair xp, row block b)
+      u64* zg = Zb;
+      const int nv = min(KP, total - j * KP);
+#pragma unroll 1
+      for (int i2 = tid; i2 < KP * G::NI2; i2 += NT) {
+        const int k = i2 / G::NI2, t2 = i2 - k * G::NI2;
+        if (k >= nv) continue;
+        const int xp = t2 % ZW, b = t2 / ZW;
+        // rows NY*b .. NY*b+NY-1 of x pair xp; X row j' <-> y - R
+        const float* xs = Xb + k * G::XP + (NY * b) * XS + 2 * xp;
+        u64 o[NY];
+#pragma unroll
+        for (int i = 0; i < NY; ++i) o[i] = 0ull;
+#pragma unroll
+        for (int jj = 0; jj < NY + 2 * R; ++jj) {
+          const u64 v = *reinterpret_cast<const u64*>(xs + jj * XS);
+#pragma unroll
+          for (int i = 0; i < NY; ++i) {
+            const int t = 2 * R + i - jj;
+            if (t >= 0 && t <= 2 * R) o[i] = ffma2(P.w2[1][t], v, o[i]);
+          }
+        }
+        u64* zd = zg + k * G::ZPL + (NY * b) * ZW + xp;
+#pragma unroll
+        for (int i = 0; i < NY; ++i) zd[i * ZW] = o[i];
+      }
+    }
+    if (face && j + 1 < ngroups) fix_group(j + 1);
+    __syncthreads();
   }
   if (s_abort) {
     set_device_error(P.err, kErrTimeout);
     // drain TMA loads still in flight into this CTA's shared memory
     if (tid == 0)
-      for (int g = j; g < min(j + NSG, ngroups); ++g)
+      for (int g = j + 1; g < min(j + NSG, ngroups); ++g)
         (void)mbar_wait(&bars[g % NSG], (g / NSG) & 1);
     __syncthreads();
   }

@@ -1,0 +1,12 @@
+// Register z-march Gaussian kernels for __half input, radii 1..12.
+#include "k_gauss_zr.cuh"
+
+namespace hp {
+namespace zr {
+
+cudaError_t dispatch_f16(int r, const ZrParams& P, const Job& job, cudaStream_t s) {
+  return dispatch_zr_t<__half>(r, P, job, s);
+}
+
+}  // namespace zr
+}  // namespace hp

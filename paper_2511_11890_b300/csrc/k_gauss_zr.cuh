@@ -108,6 +108,8 @@ struct ZrGeom {
   static constexpr int NI1 = 8 * GH * ((RPN + 1) / 2);  // P1 slots per plane
   static constexpr int NI2 = ZW * (TY / NY);             // P2 items per plane
   static constexpr int NC = TX + 2 * R;       // raw columns P1 reads
+  static constexpr int MI1 = (kKP * NI1 + NT - 1) / NT;  // P1 items per thread and group
+  static constexpr int MI2 = (kKP * NI2 + NT - 1) / NT;  // P2 items per thread and group
   static constexpr int SMEM = 128 + kNSG * GB + kKP * XP * 4 + kKP * ZPL * 8;
   static_assert(BH % 2 == 0 && TY % NY == 0 && G1 % 4 == 0 && NI1 % 8 == 0, "tile shape");
   static_assert(PB % 128 == 0, "stage planes on 128-byte boundaries");
@@ -253,6 +255,37 @@ __device__ __forceinline__ void zgroup_from(u64 (&acc)[ZP][L], const u64* zs, in
       zstore<ZP>(S, oz0 + K, done);
       zgroup_from<C, K + 1, L, ZP, KP>(acc, zs, zpl, P, S, oz0, nv);
     }
+  }
+}
+
+// Steady-state group: all kKP planes present, every output complete and
+// stored as one aligned FP32 vector at ob + K * pstride.
+template <int C, int L, int ZP, int KP>
+__device__ __forceinline__ void zgroup_fast(u64 (&acc)[ZP][L], const u64* zs, int zpl,
+                                           const ZrParams& P, unsigned char* ob,
+                                           int64_t pstride) {
+  static_assert(KP == 4, "four spelled-out slot maps");
+#pragma unroll
+  for (int K = 0; K < KP; ++K) {
+    u64 v[ZP];
+    if constexpr (ZP == 2) {
+      const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(zs + K * zpl);
+      v[0] = t.x;
+      v[1] = t.y;
+    } else {
+      v[0] = zs[K * zpl];
+    }
+    u64 done[ZP];
+    // (C + K) % L for a loop index K: spelled out per K so it stays constant
+    if (K == 0) zstep<(C + 0) % L, L, ZP>(acc, v, P, done);
+    if (K == 1) zstep<(C + 1) % L, L, ZP>(acc, v, P, done);
+    if (K == 2) zstep<(C + 2) % L, L, ZP>(acc, v, P, done);
+    if (K == 3) zstep<(C + 3) % L, L, ZP>(acc, v, P, done);
+    unsigned char* d = ob + K * pstride;
+    if constexpr (ZP == 2)
+      *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(done[0], done[1]);
+    else
+      *reinterpret_cast<u64*>(d) = done[0];
   }
 }
 
@@ -435,6 +468,39 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
               (uintptr_t)(2 * ZP * oes - 1)) == 0 && S.xrem == 2 * ZP;
   }
 
+  // Per-thread work items, decoded once. P1 slot -> (row pair rp, 8-column
+  // group g): 8 consecutive threads cover 4 groups of 2 row pairs
+  // (conflict-free stage loads). P2 item -> (x pair xp, row block b).
+  // Offsets: stage bytes and X floats (P1), X floats and Zb pairs (P2);
+  // plane index KP marks an empty slot.
+  int p1_k[G::MI1], p1_s[G::MI1], p1_x[G::MI1];
+  bool p1_any = false;  // the thread reads stages (and so waits for them)
+#pragma unroll
+  for (int m = 0; m < G::MI1; ++m) {
+    const int i1 = tid + m * NT;
+    const int k = i1 / G::NI1, sl = i1 - k * G::NI1;
+    const int g = ((sl >> 3) % G::GH) * 4 + (sl & 3);
+    const int rp = ((sl >> 3) / G::GH) * 2 + ((sl >> 2) & 1);
+    const bool ok = i1 < KP * G::NI1 && rp < G::RPN;
+    p1_any |= ok;
+    p1_k[m] = ok ? k : KP;
+    p1_s[m] = ok ? k * G::PB + (2 * rp * BW + 8 * g) * ES : 0;
+    p1_x[m] = ok ? k * G::XP + (2 * rp) * XS + 8 * g : 0;
+  }
+  int p2_k[G::MI2], p2_x[G::MI2], p2_z[G::MI2];
+#pragma unroll
+  for (int m = 0; m < G::MI2; ++m) {
+    const int i2 = tid + m * NT;
+    const int k = i2 / G::NI2, t2 = i2 - k * G::NI2;
+    const int xp = t2 % ZW, b = t2 / ZW;
+    const bool ok = i2 < KP * G::NI2;
+    p2_k[m] = ok ? k : KP;
+    p2_x[m] = ok ? k * G::XP + (NY * b) * XS + 2 * xp : 0;
+    p2_z[m] = ok ? k * G::ZPL + (NY * b) * ZW + xp : 0;
+  }
+  const bool zfast = S.zrow && S.ovec && S.of32;  // full aligned FP32 stores
+  const u64* zsrc = Zb + zy * ZW + ZP * zxg;
+
   u64 acc[ZP][L];
 #pragma unroll
   for (int zp = 0; zp < ZP; ++zp)
@@ -449,20 +515,16 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
   int j = 0;
   for (; j < ngroups + 1; ++j) {
     if (j < ngroups) {
-      // P1: slot -> (row pair rp, 8-column group g); 8 consecutive threads
-      // cover 4 groups of 2 row pairs (conflict-free stage loads)
-      if (!face && tid < KP * G::NI1) wait_group(j);
+      // P1: x pass of the thread's items of group j
+      if (!face && p1_any) wait_group(j);
       const unsigned char* sg = stages + (j % NSG) * G::GB;
       const int nv = min(KP, total - j * KP);
-#pragma unroll 1
-      for (int i1 = tid; i1 < KP * G::NI1; i1 += NT) {
-        const int k = i1 / G::NI1, sl = i1 - k * G::NI1;
-        const int g = ((sl >> 3) % G::GH) * 4 + (sl & 3);
-        const int rp = ((sl >> 3) / G::GH) * 2 + ((sl >> 2) & 1);
-        if (k >= nv || rp >= G::RPN) continue;
+#pragma unroll
+      for (int m = 0; m < G::MI1; ++m) {
+        if (p1_k[m] >= nv) continue;
         // outputs x = 8g+i (raw column RA+8g+i) of rows 2rp, 2rp+1; window
         // raw columns [8g, 8g + 8 + 2RA)
-        const unsigned char* s0 = sg + k * G::PB + (2 * rp * BW + 8 * g) * ES;
+        const unsigned char* s0 = sg + p1_s[m];
         uint4 a[G::NV], b[G::NV];
 #pragma unroll
         for (int q = 0; q < G::NV; ++q) {
@@ -481,7 +543,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
             if (t >= 0 && t <= 2 * R) o[i] = ffma2(P.w2[2][t], v, o[i]);
           }
         }
-        float* x0 = Xb + k * G::XP + (2 * rp) * XS + 8 * g;
+        float* x0 = Xb + p1_x[m];
         float2 u[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) u[i] = unpack2(o[i]);
@@ -492,23 +554,36 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
       }
     }
     if (j >= 1) {
-      // Z: planes of group j-1
+      // Z: planes of group j-1; one dispatch per group: ph = q0 mod L
+      // selects the slot maps of all its planes
       const int q0 = (j - 1) * KP;
       const int nv = min(KP, total - q0);
-      const u64* zg = Zb + zy * ZW + ZP * zxg;
-      // one dispatch per group: ph = q0 mod L selects the slot maps of all
-      // its planes
       const int oz0 = q0 - 2 * R;  // output plane completed by plane q0
-      switch (ph) {
+      if (zfast && nv == KP && oz0 >= 0) {
+        unsigned char* ob = S.ob + (int64_t)oz0 * S.pstride_b;
+        switch (ph) {
+#define HP_ZC(kk)                                                                              \
+  case kk:                                                                                     \
+    if constexpr (kk < L) zgroup_fast<(kk < L ? kk : 0), L, ZP, KP>(acc, zsrc, G::ZPL, P, ob, S.pstride_b); \
+    break;
+          HP_ZC(0) HP_ZC(1) HP_ZC(2) HP_ZC(3) HP_ZC(4) HP_ZC(5) HP_ZC(6) HP_ZC(7) HP_ZC(8)
+          HP_ZC(9) HP_ZC(10) HP_ZC(11) HP_ZC(12) HP_ZC(13) HP_ZC(14) HP_ZC(15) HP_ZC(16)
+          HP_ZC(17) HP_ZC(18) HP_ZC(19) HP_ZC(20) HP_ZC(21) HP_ZC(22) HP_ZC(23) HP_ZC(24)
+#undef HP_ZC
+          default: break;
+        }
+      } else {
+        switch (ph) {
 #define HP_ZC(kk)                                                                       \
   case kk:                                                                              \
-    if constexpr (kk < L) zgroup_from<(kk < L ? kk : 0), 0, L, ZP, KP>(acc, zg, G::ZPL, P, S, oz0, nv); \
+    if constexpr (kk < L) zgroup_from<(kk < L ? kk : 0), 0, L, ZP, KP>(acc, zsrc, G::ZPL, P, S, oz0, nv); \
     break;
-        HP_ZC(0) HP_ZC(1) HP_ZC(2) HP_ZC(3) HP_ZC(4) HP_ZC(5) HP_ZC(6) HP_ZC(7) HP_ZC(8)
-        HP_ZC(9) HP_ZC(10) HP_ZC(11) HP_ZC(12) HP_ZC(13) HP_ZC(14) HP_ZC(15) HP_ZC(16)
-        HP_ZC(17) HP_ZC(18) HP_ZC(19) HP_ZC(20) HP_ZC(21) HP_ZC(22) HP_ZC(23) HP_ZC(24)
+          HP_ZC(0) HP_ZC(1) HP_ZC(2) HP_ZC(3) HP_ZC(4) HP_ZC(5) HP_ZC(6) HP_ZC(7) HP_ZC(8)
+          HP_ZC(9) HP_ZC(10) HP_ZC(11) HP_ZC(12) HP_ZC(13) HP_ZC(14) HP_ZC(15) HP_ZC(16)
+          HP_ZC(17) HP_ZC(18) HP_ZC(19) HP_ZC(20) HP_ZC(21) HP_ZC(22) HP_ZC(23) HP_ZC(24)
 #undef HP_ZC
-        default: break;
+          default: break;
+        }
       }
       ph = (ph + KP) % L;
     }
@@ -516,16 +591,13 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
     if (s_abort) break;
     if (tid == 0 && j + NSG < ngroups) issue(j + NSG);
     if (j < ngroups) {
-      // P2: y pass of group j; item -> (plane k, x pair xp, row block b)
-      u64* zg = Zb;
+      // P2: y pass of the thread's items of group j
       const int nv = min(KP, total - j * KP);
-#pragma unroll 1
-      for (int i2 = tid; i2 < KP * G::NI2; i2 += NT) {
-        const int k = i2 / G::NI2, t2 = i2 - k * G::NI2;
-        if (k >= nv) continue;
-        const int xp = t2 % ZW, b = t2 / ZW;
+#pragma unroll
+      for (int m = 0; m < G::MI2; ++m) {
+        if (p2_k[m] >= nv) continue;
         // rows NY*b .. NY*b+NY-1 of x pair xp; X row j' <-> y - R
-        const float* xs = Xb + k * G::XP + (NY * b) * XS + 2 * xp;
+        const float* xs = Xb + p2_x[m];
         u64 o[NY];
 #pragma unroll
         for (int i = 0; i < NY; ++i) o[i] = 0ull;
@@ -538,7 +610,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
             if (t >= 0 && t <= 2 * R) o[i] = ffma2(P.w2[1][t], v, o[i]);
           }
         }
-        u64* zd = zg + k * G::ZPL + (NY * b) * ZW + xp;
+        u64* zd = Zb + p2_z[m];
 #pragma unroll
         for (int i = 0; i < NY; ++i) zd[i * ZW] = o[i];
       }

@@ -100,6 +100,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _traffic(kernel: str, nvox: int):
+    """DRAM bytes per launch of the dominant kernel from its committed ncu
+    capture (a smaller volume of the same generator, scaled by the voxel
+    count); None when that kernel is not the captured one or its sources
+    changed since the capture."""
+    if kernel != "gauss_s4":
+        return None
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic_gauss_zr_r12_porous.json")) as fh:
+            rec = json.load(fh)
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * nvox / rec["captured_voxels"]
+    except Exception:
+        return None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -263,6 +285,7 @@ def run_hp(args):
     else:
         roof = {"bound": "hbm", "achieved": dk["GB/s"], "peak": hbm_gbs, "unit": "GB/s",
                 "frac": dk["hbm_frac"], "traffic": None, "kernel": dom, "peak_kind": peak_kind}
+    roof["traffic"] = _traffic(dom, nvox)
     step_bytes = nvox * (3 * 6 + 2 * 4)
     hbm_step_frac = step_bytes / (total_ms / args.steps) / 1e6 / hbm_gbs
 

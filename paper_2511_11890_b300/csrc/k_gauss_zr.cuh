@@ -13,7 +13,7 @@
 //          of use, from a per-thread list of (cell, source) offsets;
 //   P1     x pass on row pairs read straight from the raw stage (element ->
 //          FP32 inline), packed f32x2 FMAs over the row pair, into X;
-//   P2     y pass on x pairs (packed f32x2 over the two columns), NY rows
+//   P2     y pass on x pairs (packed f32x2 over the two columns), NY = 16 rows
 //          per item, into the z feed buffer Zb;
 //   Z      each thread owns ZP x pairs of one row and keeps 2R+1 partial
 //          outputs per pair in registers: input plane q adds tap i to the
@@ -78,7 +78,7 @@ struct ZrShape {
   static constexpr int TY = R <= 6 ? 16 : 32;
   static constexpr int ZP = R <= 6 ? 2 : 1;
   static constexpr int NT = TX * TY / (2 * ZP);
-  static constexpr int NY = 8;
+  static constexpr int NY = 16;
   static constexpr int MINB = NT >= 512 ? 1 : 2;
 };
 
@@ -98,8 +98,12 @@ struct ZrGeom {
   static constexpr int PB = BW * BHP * ES;    // bytes per stage plane (multiple of 128)
   static constexpr int GB = kKP * PB;         // bytes per stage group
   static constexpr int RPN = BH / 2;          // row pairs
-  static constexpr int XS = TX + 4;           // X row stride (floats)
-  static constexpr int XP = BH * XS;          // X floats per plane
+  // X holds row pairs: row r at (r/2)*RPS + (r%2)*XS floats. XS keeps rows
+  // 16-byte aligned; RPS/4 odd puts the float4 stores of the 8 threads of a
+  // quarter warp (4 column groups x 2 row pairs) in 8 distinct bank groups.
+  static constexpr int XS = TX + 4;           // row stride within a pair (floats)
+  static constexpr int RPS = 2 * XS + ((2 * XS / 4) % 2 == 0 ? 4 : 0);  // row-pair stride
+  static constexpr int XP = (BH / 2) * RPS;   // X floats per plane
   static constexpr int ZW = TX / 2;           // x pairs per row
   static constexpr int ZPL = TY * ZW;         // Zb pairs per plane
   static constexpr int NV = (8 + 2 * RA) * ES / 16;  // 16-byte loads per P1 row
@@ -111,7 +115,8 @@ struct ZrGeom {
   static constexpr int MI1 = (kKP * NI1 + NT - 1) / NT;  // P1 items per thread and group
   static constexpr int MI2 = (kKP * NI2 + NT - 1) / NT;  // P2 items per thread and group
   static constexpr int SMEM = 128 + kNSG * GB + kKP * XP * 4 + kKP * ZPL * 8;
-  static_assert(BH % 2 == 0 && TY % NY == 0 && G1 % 4 == 0 && NI1 % 8 == 0, "tile shape");
+  static_assert(BH % 2 == 0 && TY % NY == 0 && NY % 2 == 0 && G1 % 4 == 0 && NI1 % 8 == 0, "tile shape");
+  static_assert((RPS / 4) % 2 == 1 && XS % 4 == 0, "X layout");
   static_assert(PB % 128 == 0, "stage planes on 128-byte boundaries");
   static_assert((8 + 2 * RA) * ES % 16 == 0, "P1 window in whole 16-byte words");
   static_assert(BW <= 256 && BHP <= 256, "TMA box");
@@ -485,7 +490,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
     p1_any |= ok;
     p1_k[m] = ok ? k : KP;
     p1_s[m] = ok ? k * G::PB + (2 * rp * BW + 8 * g) * ES : 0;
-    p1_x[m] = ok ? k * G::XP + (2 * rp) * XS + 8 * g : 0;
+    p1_x[m] = ok ? k * G::XP + rp * G::RPS + 8 * g : 0;
   }
   int p2_k[G::MI2], p2_x[G::MI2], p2_z[G::MI2];
 #pragma unroll
@@ -495,7 +500,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
     const int xp = t2 % ZW, b = t2 / ZW;
     const bool ok = i2 < KP * G::NI2;
     p2_k[m] = ok ? k : KP;
-    p2_x[m] = ok ? k * G::XP + (NY * b) * XS + 2 * xp : 0;
+    p2_x[m] = ok ? k * G::XP + (NY * b / 2) * G::RPS + 2 * xp : 0;
     p2_z[m] = ok ? k * G::ZPL + (NY * b) * ZW + xp : 0;
   }
   const bool zfast = S.zrow && S.ovec && S.of32;  // full aligned FP32 stores
@@ -603,7 +608,8 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
         for (int i = 0; i < NY; ++i) o[i] = 0ull;
 #pragma unroll
         for (int jj = 0; jj < NY + 2 * R; ++jj) {
-          const u64 v = *reinterpret_cast<const u64*>(xs + jj * XS);
+          // X row NY*b + jj (NY even: the pair parity is that of jj)
+          const u64 v = *reinterpret_cast<const u64*>(xs + (jj >> 1) * G::RPS + (jj & 1) * XS);
 #pragma unroll
           for (int i = 0; i < NY; ++i) {
             const int t = 2 * R + i - jj;

@@ -82,7 +82,8 @@ def test_bank_512_37_bricks_sampled():
             refs.append(_oracle_bank(part, [(k, s)], gdims=f.shape, in_lo=ilo, out_lo=lo,
                                      out_shape=(8, 8, 8))[0])
             gots.append(outs[i][lo[0]:lo[0] + 8, lo[1]:lo[1] + 8, lo[2]:lo[2] + 8].cpu().numpy())
-        assert_filter_close(np.stack(gots), np.stack(refs), f"512^3 kind {k} sigma {s}")
+        err, rng_ = assert_filter_close(np.stack(gots), np.stack(refs), f"512^3 kind {k} sigma {s}")
+        print(f"bank 512^3 f16 kind {k} sigma {s}: max |err| {err:.3e} (range {rng_:.3e})")
     whole = hp.filterbank3d(x, BANK)
     for a, b in zip(outs, whole):
         assert torch.equal(a.view(torch.int16), b.view(torch.int16))

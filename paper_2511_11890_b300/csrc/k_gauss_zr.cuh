@@ -90,7 +90,11 @@ struct ZrGeom {
   static constexpr int ES = (int)sizeof(TIN);
   static constexpr int AL = 16 / ES;          // elements per 16 bytes
   static constexpr int RA = rup(R, AL);       // left halo of the raw patch
-  static constexpr int BW = TX + 2 * RA;      // raw patch width (elements)
+  // Raw patch width (elements): TX + 2RA, widened until a row is 32 mod 64
+  // bytes, so that the x-pass loads of 8 consecutive threads (4 column groups
+  // x 2 row pairs, rows 2 apart) fall in 8 distinct 16-byte bank groups.
+  static constexpr int bw_pad(int w) { return (w * ES) % 64 == 32 ? w : bw_pad(w + AL); }
+  static constexpr int BW = bw_pad(TX + 2 * RA);
   static constexpr int BH = TY + 2 * R;       // raw patch rows used
   // rows loaded: BH rounded up so that stage planes (written by one deep
   // box or by single-plane loads) start on 128-byte boundaries

@@ -83,6 +83,9 @@ struct PG {
   static constexpr int SB = rup(BW * BH * 2, 128);  // bytes per TMA stage
   static constexpr int SMEM = 128 + kPS * SB + 2 * MSZ * 4;
   static_assert(W0 >= 0 && RA / 2 + kPC + HP <= BWW, "x window inside the TMA box");
+  static_assert((BWW * 4) % 16 == 0 &&
+                    (W0 - W0 % 4) + 4 * (kPX / kXI - 1) + 4 * ((W0 % 4 + NW + 3) / 4) <= BWW,
+                "aligned x windows inside the stage row");
 };
 
 // 16-bit keys of a word holding two elements. float16: positive values get
@@ -124,19 +127,24 @@ __device__ __forceinline__ void xpass_item(uint32_t* Mb, const uint32_t* S, int 
   using G = PG<R, BALL>;
   using O = Op<DIL>;
   constexpr int NW = G::NW;
-  const uint32_t* src = S + row * G::BWW + G::W0 + 4 * g;
-  uint32_t lv[R + 1][NW];
-  if constexpr (G::W0 % 2 == 0) {
+  // The window is read as whole 16-byte words starting at the aligned word
+  // below it: the 8 items of a quarter warp (one row, consecutive groups)
+  // then read one contiguous 128-byte line per load, free of bank conflicts.
+  constexpr int A0 = G::W0 % 4;
+  constexpr int NQ = (A0 + NW + 3) / 4;
+  const uint4* src = reinterpret_cast<const uint4*>(S + row * G::BWW + (G::W0 - A0) + 4 * g);
+  uint32_t t[4 * NQ];
 #pragma unroll
-    for (int k = 0; k < NW; k += 2) {
-      const uint2 v = *reinterpret_cast<const uint2*>(src + k);
-      lv[0][k] = to_keys<KIND>(v.x);
-      lv[0][k + 1] = to_keys<KIND>(v.y);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < NW; ++k) lv[0][k] = to_keys<KIND>(src[k]);
+  for (int q = 0; q < NQ; ++q) {
+    const uint4 v = src[q];
+    t[4 * q] = v.x;
+    t[4 * q + 1] = v.y;
+    t[4 * q + 2] = v.z;
+    t[4 * q + 3] = v.w;
   }
+  uint32_t lv[R + 1][NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k) lv[0][k] = to_keys<KIND>(t[A0 + k]);
   // q[k] = (v at pair k high half, pair k+1 low half): the odd shift
   uint32_t q[NW - 1];
 #pragma unroll

@@ -43,7 +43,28 @@ struct AxisTaps {
   float g[kMaxTaps];
 };
 
-// dst = (axis transpose of src); dst += when accumulate.
+// Transpose at one output i of a line (elements line[j * stride], length
+// n): the sum over the pre-images j of i under the reflection of
+// t[j] = sum_k g(k) w[j + k], w zero outside the line.
+__device__ __forceinline__ float adjoint_at(const float* line, int64_t i, int64_t n,
+                                            int64_t stride, const AxisTaps& taps, int r) {
+  float acc = 0.0f;
+  // pre-images j of i in [-r, n-1+r]: i + 2n m and -1 - i + 2n m
+  for (int64_t m = -((r + 2 * n) / (2 * n)); m <= (r + 2 * n) / (2 * n); ++m) {
+    for (int s = 0; s < 2; ++s) {
+      const int64_t j = (s == 0 ? i : -1 - i) + 2 * n * m;
+      if (j < -r || j > n - 1 + r) continue;
+      if (reflect(j, n) != i) continue;
+      for (int k = -r; k <= r; ++k) {
+        const int64_t s2 = j + k;
+        if (s2 >= 0 && s2 < n) acc = fmaf(taps.g[k + r], line[s2 * stride], acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// dst = (axis transpose of src); dst += when accumulate. Any radius.
 __global__ void k_axis_adjoint(const float* __restrict__ src, float* __restrict__ dst, int64_t n0,
                                int64_t n1, int64_t n2, int axis, const AxisTaps taps, int r,
                                int accumulate) {
@@ -54,23 +75,84 @@ __global__ void k_axis_adjoint(const float* __restrict__ src, float* __restrict_
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
     const int64_t i = axis == 0 ? z : (axis == 1 ? y : x);
-    const float* line = src + (q - i * stride);
-    float acc = 0.0f;
-    // pre-images j of i in [-r, n-1+r]: i + 2n m and -1 - i + 2n m
-    for (int64_t m = -((r + 2 * n) / (2 * n)); m <= (r + 2 * n) / (2 * n); ++m) {
-      for (int s = 0; s < 2; ++s) {
-        const int64_t j = (s == 0 ? i : -1 - i) + 2 * n * m;
-        if (j < -r || j > n - 1 + r) continue;
-        if (reflect(j, n) != i) continue;
-        // t[j] = sum_k g(k) w[j + k]
-        for (int k = -r; k <= r; ++k) {
-          const int64_t s2 = j + k;
-          if (s2 >= 0 && s2 < n) acc = fmaf(taps.g[k + r], line[s2 * stride], acc);
-        }
-      }
-    }
+    const float acc = adjoint_at(src + (q - i * stride), i, n, stride, taps, r);
     dst[q] = accumulate ? dst[q] + acc : acc;
   }
+}
+
+// Same transpose, radius R known at compile time: each thread takes kAC
+// consecutive outputs of one line. Away from the faces (R <= i < n - R) the
+// only pre-image of i is i itself and t[i] needs no zero extension, so the
+// chunk is a plain correlation over a register window, with the same
+// per-output FMA order as adjoint_at; chunks that touch a face use
+// adjoint_at. Lines along z and y put consecutive threads on consecutive x
+// (coalesced); lines along x give each thread a contiguous run.
+constexpr int kAC = 16;
+
+template <int R, int AXIS>
+__global__ void __launch_bounds__(kBlock)
+    k_axis_adjoint_r(const float* __restrict__ src, float* __restrict__ dst, int n0, int n1,
+                     int n2, const AxisTaps taps, int accumulate) {
+  const int n = AXIS == 0 ? n0 : (AXIS == 1 ? n1 : n2);
+  const int64_t stride = AXIS == 2 ? 1 : (AXIS == 1 ? (int64_t)n2 : (int64_t)n1 * n2);
+  const int nch = (n + kAC - 1) / kAC;
+  int64_t base;  // element of i = 0 on this thread's line
+  int c;         // chunk of the line
+  if (AXIS == 2) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n0 * n1 * nch) return;
+    c = (int)(t % nch);
+    base = (t / nch) * n2;
+  } else {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n2) return;
+    c = blockIdx.z;
+    base = AXIS == 0 ? (int64_t)blockIdx.y * n2 + x : (int64_t)blockIdx.y * n1 * n2 + x;
+  }
+  const float* line = src + base;
+  float* dl = dst + base;
+  const int i0 = c * kAC;
+  if (i0 >= R && i0 + kAC <= n - R) {
+    float w[kAC + 2 * R];
+#pragma unroll
+    for (int j = 0; j < kAC + 2 * R; ++j) w[j] = line[(int64_t)(i0 - R + j) * stride];
+#pragma unroll
+    for (int i = 0; i < kAC; ++i) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = -R; k <= R; ++k) acc = fmaf(taps.g[k + R], w[i + k + R], acc);
+      float* d = dl + (int64_t)(i0 + i) * stride;
+      *d = accumulate ? *d + acc : acc;
+    }
+  } else {
+    const int i1 = min(i0 + kAC, n);
+    for (int i = i0; i < i1; ++i) {
+      const float acc = adjoint_at(line, i, n, stride, taps, R);
+      float* d = dl + (int64_t)i * stride;
+      *d = accumulate ? *d + acc : acc;
+    }
+  }
+}
+
+template <int R>
+cudaError_t launch_axis_r(const float* src, float* dst, const int64_t dims[3], int ax,
+                          const AxisTaps& a, int accumulate, cudaStream_t s) {
+  const int n0 = (int)dims[0], n1 = (int)dims[1], n2 = (int)dims[2];
+  const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
+  const int nch = (n + kAC - 1) / kAC;
+  if (ax == 2) {
+    const int64_t t = (int64_t)n0 * n1 * nch;
+    k_axis_adjoint_r<R, 2><<<(unsigned)((t + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        src, dst, n0, n1, n2, a, accumulate);
+  } else {
+    const dim3 grid((unsigned)((n2 + kBlock - 1) / kBlock), (unsigned)(ax == 0 ? n1 : n0),
+                    (unsigned)nch);
+    if (ax == 0)
+      k_axis_adjoint_r<R, 0><<<grid, kBlock, 0, s>>>(src, dst, n0, n1, n2, a, accumulate);
+    else
+      k_axis_adjoint_r<R, 1><<<grid, kBlock, 0, s>>>(src, dst, n0, n1, n2, a, accumulate);
+  }
+  return cudaGetLastError();
 }
 
 // v = w * D_a / GM (0 where GM = 0), GM = sqrt(Dx^2 + Dy^2 + Dz^2) formed
@@ -163,8 +245,24 @@ cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3]
     for (int k = 0; k < kMaxTaps; ++k) a.g[k] = taps.w[ax][k];
     const float* src = ax == 0 ? w : (ax == 1 ? t1 : t2);
     float* out = ax == 0 ? t1 : (ax == 1 ? t2 : dst);
-    k_axis_adjoint<<<grid_for(total), kBlock, 0, s>>>(src, out, dims[0], dims[1], dims[2], ax, a,
-                                                     taps.r, ax == 2 ? accumulate : 0);
+    const int acc = ax == 2 ? accumulate : 0;
+    // compile-time radius where the grid fits (lines and planes below 65536)
+    const bool fits = taps.r >= 1 && taps.r <= kMaxR && dims[0] < 65536 && dims[1] < 65536 &&
+                      dims[2] < (1LL << 31) / 4;
+    if (fits) {
+      cudaError_t e = cudaErrorInvalidValue;
+      switch (taps.r) {
+#define HP_AR(RR) \
+  case RR: e = launch_axis_r<RR>(src, out, dims, ax, a, acc, s); break;
+        HP_AR(1) HP_AR(2) HP_AR(3) HP_AR(4) HP_AR(5) HP_AR(6)
+        HP_AR(7) HP_AR(8) HP_AR(9) HP_AR(10) HP_AR(11) HP_AR(12)
+#undef HP_AR
+      }
+      if (e != cudaSuccess) return e;
+    } else {
+      k_axis_adjoint<<<grid_for(total), kBlock, 0, s>>>(src, out, dims[0], dims[1], dims[2], ax,
+                                                       a, taps.r, acc);
+    }
   }
   return cudaGetLastError();
 }

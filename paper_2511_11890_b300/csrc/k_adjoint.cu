@@ -86,7 +86,7 @@ __global__ void k_axis_adjoint(const float* __restrict__ src, float* __restrict_
 // chunk is a plain correlation over a register window, with the same
 // per-output FMA order as adjoint_at; chunks that touch a face use
 // adjoint_at. Lines along z and y put consecutive threads on consecutive x
-// (coalesced); lines along x give each thread a contiguous run.
+// (coalesced); along x each thread takes a single output instead.
 constexpr int kAC = 16;
 
 template <int R, int AXIS>
@@ -99,10 +99,22 @@ __global__ void __launch_bounds__(kBlock)
   int64_t base;  // element of i = 0 on this thread's line
   int c;         // chunk of the line
   if (AXIS == 2) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n0 * n1 * nch) return;
-    c = (int)(t % nch);
-    base = (t / nch) * n2;
+    // one output per thread, consecutive threads on consecutive x: every tap
+    // is one coalesced row read
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n2) return;
+    const float* line = src + ((int64_t)blockIdx.z * n1 + blockIdx.y) * n2;
+    float* d = dst + ((int64_t)blockIdx.z * n1 + blockIdx.y) * n2 + x;
+    float acc;
+    if (x >= R && x < n - R) {
+      acc = 0.0f;
+#pragma unroll
+      for (int k = -R; k <= R; ++k) acc = fmaf(taps.g[k + R], line[x + k], acc);
+    } else {
+      acc = adjoint_at(line, x, n, 1, taps, R);
+    }
+    *d = accumulate ? *d + acc : acc;
+    return;
   } else {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n2) return;
@@ -141,9 +153,8 @@ cudaError_t launch_axis_r(const float* src, float* dst, const int64_t dims[3], i
   const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
   const int nch = (n + kAC - 1) / kAC;
   if (ax == 2) {
-    const int64_t t = (int64_t)n0 * n1 * nch;
-    k_axis_adjoint_r<R, 2><<<(unsigned)((t + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-        src, dst, n0, n1, n2, a, accumulate);
+    const dim3 grid((unsigned)((n2 + kBlock - 1) / kBlock), (unsigned)n1, (unsigned)n0);
+    k_axis_adjoint_r<R, 2><<<grid, kBlock, 0, s>>>(src, dst, n0, n1, n2, a, accumulate);
   } else {
     const dim3 grid((unsigned)((n2 + kBlock - 1) / kBlock), (unsigned)(ax == 0 ? n1 : n0),
                     (unsigned)nch);

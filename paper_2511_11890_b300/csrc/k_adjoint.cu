@@ -218,6 +218,107 @@ __global__ void k_morph_arg(const void* __restrict__ in, int dt, int64_t n0, int
   }
 }
 
+// Cube structuring element: the extreme over the cube is the extreme over z
+// of the extremes over y of the extremes over x, and the linear index is
+// lexicographic in (z, y, x), so the smallest-index tie rule also separates:
+// per row keep the smallest source x among the extremes, per plane the
+// smallest (source y, that x), over planes the smallest (source z, ...).
+// A CTA stages the reflected input box of a 4 x 8 x 32 output tile in shared
+// memory and runs the three passes there; arg[] equals k_morph_arg's.
+constexpr int kCZ = 4, kCY = 8, kCX = 32;
+
+template <int RAD>
+constexpr int cube_arg_smem() {
+  constexpr int VZ = kCZ + 2 * RAD, VY = kCY + 2 * RAD, VX = kCX + 2 * RAD;
+  return 4 * (VZ * (VY * (VX + 2 * kCX) + 2 * kCY * kCX) + VX + VY + VZ);
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(kBlock)
+    k_morph_arg_cube(const void* __restrict__ in, int dt, int n0, int n1, int n2, int is_dilate,
+                     int32_t* __restrict__ arg) {
+  constexpr int VZ = kCZ + 2 * RAD, VY = kCY + 2 * RAD, VX = kCX + 2 * RAD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // reflected input box, x pass (value, source x), y pass (value, source
+  // y * n2 + x), reflected coordinates; sizes in cube_arg_smem<RAD>()
+  auto v0 = reinterpret_cast<float(*)[VY][VX]>(smem_raw);
+  auto v1 = reinterpret_cast<float(*)[VY][kCX]>(smem_raw + 4 * VZ * VY * VX);
+  auto i1 = reinterpret_cast<int32_t(*)[VY][kCX]>(smem_raw + 4 * VZ * VY * (VX + kCX));
+  auto v2 = reinterpret_cast<float(*)[kCY][kCX]>(smem_raw + 4 * VZ * VY * (VX + 2 * kCX));
+  auto i2 = reinterpret_cast<int32_t(*)[kCY][kCX]>(smem_raw + 4 * VZ * (VY * (VX + 2 * kCX) + kCY * kCX));
+  int32_t* sx = reinterpret_cast<int32_t*>(smem_raw + 4 * VZ * (VY * (VX + 2 * kCX) + 2 * kCY * kCX));
+  int32_t* sy = sx + VX;
+  int32_t* sz = sy + VY;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kCX, y0 = blockIdx.y * kCY, z0 = blockIdx.z * kCZ;
+  const int sg = is_dilate ? -1 : 1;
+  for (int c = tid; c < VX; c += kBlock) sx[c] = (int)reflect(x0 - RAD + c, n2);
+  for (int c = tid; c < VY; c += kBlock) sy[c] = (int)reflect(y0 - RAD + c, n1);
+  for (int c = tid; c < VZ; c += kBlock) sz[c] = (int)reflect(z0 - RAD + c, n0);
+  __syncthreads();
+  for (int e = tid; e < VZ * VY * VX; e += kBlock) {
+    const int c = e % VX, b = (e / VX) % VY, a = e / (VX * VY);
+    v0[a][b][c] = load_as_f32(in, dt, ((int64_t)sz[a] * n1 + sy[b]) * n2 + sx[c]);
+  }
+  __syncthreads();
+  auto better = [&](float v, int64_t q, float best, int64_t bq) {
+    return (is_dilate ? v > best : v < best) || (v == best && q < bq);
+  };
+  // x pass over every staged row; window offset sg*dx from the output column
+  for (int e = tid; e < VZ * VY * kCX; e += kBlock) {
+    const int x = e % kCX, b = (e / kCX) % VY, a = e / (kCX * VY);
+    float best = 0.0f;
+    int bq = -1;
+#pragma unroll
+    for (int d = -RAD; d <= RAD; ++d) {
+      const int c = x + RAD + sg * d;
+      const float v = v0[a][b][c];
+      if (bq < 0 || better(v, sx[c], best, bq)) {
+        best = v;
+        bq = sx[c];
+      }
+    }
+    v1[a][b][x] = best;
+    i1[a][b][x] = bq;
+  }
+  __syncthreads();
+  for (int e = tid; e < VZ * kCY * kCX; e += kBlock) {
+    const int x = e % kCX, y = (e / kCX) % kCY, a = e / (kCX * kCY);
+    float best = 0.0f;
+    int64_t bq = -1;
+#pragma unroll
+    for (int d = -RAD; d <= RAD; ++d) {
+      const int b = y + RAD + sg * d;
+      const float v = v1[a][b][x];
+      const int64_t q = (int64_t)sy[b] * n2 + i1[a][b][x];
+      if (bq < 0 || better(v, q, best, bq)) {
+        best = v;
+        bq = q;
+      }
+    }
+    v2[a][y][x] = best;
+    i2[a][y][x] = (int32_t)bq;
+  }
+  __syncthreads();
+  for (int e = tid; e < kCZ * kCY * kCX; e += kBlock) {
+    const int x = e % kCX, y = (e / kCX) % kCY, z = e / (kCX * kCY);
+    if (z0 + z >= n0 || y0 + y >= n1 || x0 + x >= n2) continue;
+    float best = 0.0f;
+    int64_t bq = -1;
+#pragma unroll
+    for (int d = -RAD; d <= RAD; ++d) {
+      const int a = z + RAD + sg * d;
+      const int64_t q = (int64_t)sz[a] * n1 * n2 + i2[a][y][x];
+      const float v = v2[a][y][x];
+      if (bq < 0 || better(v, q, best, bq)) {
+        best = v;
+        bq = q;
+      }
+    }
+    arg[((int64_t)(z0 + z) * n1 + (y0 + y)) * n2 + (x0 + x)] = (int32_t)bq;
+  }
+}
+
 // gin[q] (+)= sum of gout[p] over p in q + [-rad, rad]^3 with arg[p] == q,
 // p in increasing linear order.
 __global__ void k_morph_gather(const int32_t* __restrict__ arg, const float* __restrict__ gout,
@@ -287,6 +388,26 @@ cudaError_t launch_gm_chain(const float* w, const float* dz, const float* dy, co
 cudaError_t launch_morph_arg(const void* in, int dt, const int64_t dims[3], int ball, int rad,
                              int is_dilate, int32_t* arg, cudaStream_t s) {
   const int64_t total = dims[0] * dims[1] * dims[2];
+  if (!ball && rad >= 1 && rad <= 4 && dims[0] < 65536 * kCZ && dims[1] < 65536 * kCY) {
+    const dim3 grid((unsigned)((dims[2] + kCX - 1) / kCX), (unsigned)((dims[1] + kCY - 1) / kCY),
+                    (unsigned)((dims[0] + kCZ - 1) / kCZ));
+    const int n0 = (int)dims[0], n1 = (int)dims[1], n2 = (int)dims[2];
+    cudaError_t e = cudaSuccess;
+    switch (rad) {
+#define HP_CA(RR)                                                                              \
+  case RR:                                                                                     \
+    e = cudaFuncSetAttribute(k_morph_arg_cube<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             cube_arg_smem<RR>());                                             \
+    if (e == cudaSuccess)                                                                      \
+      k_morph_arg_cube<RR><<<grid, kBlock, cube_arg_smem<RR>(), s>>>(in, dt, n0, n1, n2,       \
+                                                                     is_dilate, arg);          \
+    break;
+      HP_CA(1) HP_CA(2) HP_CA(3) HP_CA(4)
+#undef HP_CA
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   k_morph_arg<<<grid_for(total), kBlock, 0, s>>>(in, dt, dims[0], dims[1], dims[2], ball, rad,
                                                  is_dilate, arg);
   return cudaGetLastError();

@@ -131,3 +131,18 @@ def test_dot_product_identity_256():
     gin = hp.filterbank3d_adjoint(v, w, filt)
     rhs = float((v.double() * gin.double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1.0), (lhs, rhs)
+
+
+@pytest.mark.parametrize("rad", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("dilate", [False, True])
+def test_cube_subgradient_many_ties(rad, dilate):
+    """Cube subgradient on a low-cardinality volume (ties everywhere, also at
+    the faces): radii 1..4 take the separable shared-memory argmin, 5 the
+    per-output scan; both route every output gradient to the smallest linear
+    source index among the extremes, as the oracle does."""
+    shape = (13, 21, 70)
+    f = np.random.default_rng(rad).integers(0, 4, shape).astype(np.uint8)
+    w = synth.normal_field(shape, 100 + rad)
+    g = to_np(hp.morph3d_backward(to_dev(f), to_dev(w), dilate, "cube", rad))
+    ref = oracle.morph3d_vjp(f, oracle.SE_CUBE, rad, dilate, w.astype(np.float64))
+    assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()

@@ -339,6 +339,52 @@ __global__ void k_morph_gather(const int32_t* __restrict__ arg, const float* __r
   }
 }
 
+// The same gather with the reach of a 4 x 8 x 32 tile of sources staged in
+// shared memory (arg and gout of every p within rad of the tile; -1 outside
+// the volume): each q scans its cube of p in increasing linear order, as
+// k_morph_gather does.
+template <int RAD>
+constexpr int gather_smem() {
+  return 8 * (kCZ + 2 * RAD) * (kCY + 2 * RAD) * (kCX + 2 * RAD);
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(kBlock)
+    k_morph_gather_tile(const int32_t* __restrict__ arg, const float* __restrict__ gout,
+                        float* __restrict__ gin, int n0, int n1, int n2, int accumulate) {
+  constexpr int VZ = kCZ + 2 * RAD, VY = kCY + 2 * RAD, VX = kCX + 2 * RAD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto sa = reinterpret_cast<int32_t(*)[VY][VX]>(smem_raw);
+  auto sg = reinterpret_cast<float(*)[VY][VX]>(smem_raw + 4 * VZ * VY * VX);
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * kCX, y0 = blockIdx.y * kCY, z0 = blockIdx.z * kCZ;
+  for (int e = tid; e < VZ * VY * VX; e += kBlock) {
+    const int c = e % VX, b = (e / VX) % VY, a = e / (VX * VY);
+    const int z = z0 - RAD + a, y = y0 - RAD + b, x = x0 - RAD + c;
+    const bool in = z >= 0 && z < n0 && y >= 0 && y < n1 && x >= 0 && x < n2;
+    const int64_t p = ((int64_t)z * n1 + y) * n2 + x;
+    sa[a][b][c] = in ? arg[p] : -1;
+    sg[a][b][c] = in ? gout[p] : 0.0f;
+  }
+  __syncthreads();
+  for (int e = tid; e < kCZ * kCY * kCX; e += kBlock) {
+    const int x = e % kCX, y = (e / kCX) % kCY, z = e / (kCX * kCY);
+    const int gz = z0 + z, gy = y0 + y, gx = x0 + x;
+    if (gz >= n0 || gy >= n1 || gx >= n2) continue;
+    const int32_t q = (int32_t)(((int64_t)gz * n1 + gy) * n2 + gx);
+    float acc = 0.0f;
+#pragma unroll
+    for (int dz = 0; dz <= 2 * RAD; ++dz)
+#pragma unroll
+      for (int dy = 0; dy <= 2 * RAD; ++dy)
+#pragma unroll
+        for (int dx = 0; dx <= 2 * RAD; ++dx)
+          if (sa[z + dz][y + dy][x + dx] == q) acc += sg[z + dz][y + dy][x + dx];
+    float* d = gin + q;
+    *d = accumulate ? *d + acc : acc;
+  }
+}
+
 unsigned grid_for(int64_t total) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + kBlock - 1) / kBlock,
                                                           (int64_t)num_sms() * 16));
@@ -416,6 +462,26 @@ cudaError_t launch_morph_arg(const void* in, int dt, const int64_t dims[3], int 
 cudaError_t launch_morph_gather(const int32_t* arg, const float* gout, float* gin,
                                 const int64_t dims[3], int rad, int accumulate, cudaStream_t s) {
   const int64_t total = dims[0] * dims[1] * dims[2];
+  if (rad >= 1 && rad <= 4 && dims[0] < 65536 * kCZ && dims[1] < 65536 * kCY) {
+    const dim3 grid((unsigned)((dims[2] + kCX - 1) / kCX), (unsigned)((dims[1] + kCY - 1) / kCY),
+                    (unsigned)((dims[0] + kCZ - 1) / kCZ));
+    const int n0 = (int)dims[0], n1 = (int)dims[1], n2 = (int)dims[2];
+    cudaError_t e = cudaSuccess;
+    switch (rad) {
+#define HP_GT(RR)                                                                                 \
+  case RR:                                                                                        \
+    e = cudaFuncSetAttribute(k_morph_gather_tile<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             gather_smem<RR>());                                                  \
+    if (e == cudaSuccess)                                                                         \
+      k_morph_gather_tile<RR><<<grid, kBlock, gather_smem<RR>(), s>>>(arg, gout, gin, n0, n1, n2, \
+                                                                     accumulate);                 \
+    break;
+      HP_GT(1) HP_GT(2) HP_GT(3) HP_GT(4)
+#undef HP_GT
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   k_morph_gather<<<grid_for(total), kBlock, 0, s>>>(arg, gout, gin, dims[0], dims[1], dims[2],
                                                     rad, accumulate);
   return cudaGetLastError();

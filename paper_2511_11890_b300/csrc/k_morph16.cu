@@ -446,6 +446,351 @@ cudaError_t dispatch_se(int ball, int r, const Morph16Params& P, const CUtensorM
               : dispatch16<0, KIND, DIL>(r, P, map, tiles, cz, s);
 }
 
+// --------------------------------------------------------------------------
+// Strip variant (radius <= 3): no line-minimum buffer in shared memory. A
+// thread owns one pair column and kSS consecutive output rows of a 64 x 32
+// tile; for each input plane it reads its (1 + 2HP)-word window of the
+// kSS + 2R stage rows it needs, forms the x-line minima of its pair per row,
+// the disk minima of its rows from the last 2R + 1 rows (registers), and
+// pushes them into its z ring. Four input planes per phase arrive in one
+// four-deep TMA box (single-plane loads where z reflects), two groups in
+// flight; face tiles patch the out-of-volume stage cells from a per-thread
+// list of (cell, source) offsets before the barrier that precedes use.
+constexpr int kSS = 8;                       // output rows per thread
+constexpr int kSKP = 4;                      // input planes per phase (TMA box depth)
+constexpr int kSNSG = 2;                     // plane groups in flight
+constexpr int kSThreads = kPC * (kPY / kSS);  // 128
+constexpr int kSFix = 8;                     // face cells per thread in registers
+
+__host__ __device__ constexpr int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
+
+template <int R>
+struct SG {
+  static constexpr int BH = kPY + 2 * R;                      // stage rows used
+  static constexpr int RA = rup(R, 8);
+  static constexpr int BW = rup(kPX + RA + R, 8);             // stage row, elements
+  static constexpr int BWW = BW / 2;                          // stage row, words
+  static constexpr int BHP = rup(BH, 128 / gcd_i(BW * 2, 128));  // rows loaded
+  static constexpr int PB = BW * BHP * 2;                     // bytes per stage plane
+  static constexpr int GB = kSKP * PB;
+  static constexpr int HP = (R + 1) / 2;
+  static constexpr int NW = 1 + 2 * HP;                       // window words per row
+  static constexpr int NR = kSS + 2 * R;                      // stage rows per strip
+  static constexpr int NC = kPX + 2 * R;                      // stage columns read
+  static constexpr int SMEM = 128 + kSNSG * GB;
+  static_assert(PB % 128 == 0, "stage planes on 128-byte boundaries");
+  static_assert(RA / 2 - HP >= 0 && RA / 2 + kPC - 1 + HP < BWW, "windows inside the row");
+};
+
+// x-line minima M[L] (L = 0..R) of one pair from its window w[0..NW) of keys
+// (pair at w[HP]).
+template <int R, int DIL>
+__device__ __forceinline__ void xline1(const uint32_t (&w)[SG<R>::NW], uint32_t (&M)[R + 1]) {
+  using O = Op<DIL>;
+  constexpr int NW = SG<R>::NW, H = SG<R>::HP;
+  uint32_t lv[R + 1][NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k) lv[0][k] = w[k];
+  uint32_t q[NW - 1];
+#pragma unroll
+  for (int k = 0; k + 1 < NW; ++k) q[k] = __byte_perm(w[k], w[k + 1], 0x5432);
+#pragma unroll
+  for (int k = 1; k + 1 < NW; ++k) lv[1][k] = O::f3(q[k - 1], w[k], q[k]);
+  if constexpr (R >= 2) {
+#pragma unroll
+    for (int k = 1; k + 1 < NW; ++k) lv[2][k] = O::f3(w[k - 1], lv[1][k], w[k + 1]);
+  }
+#pragma unroll
+  for (int L = 3; L <= R; ++L) {
+    const int c = (L + 1) / 2;
+#pragma unroll
+    for (int k = c; k < NW - c; ++k) lv[L][k] = O::f3(lv[L - 2][k - 1], lv[L - 2][k], lv[L - 2][k + 1]);
+  }
+#pragma unroll
+  for (int L = 0; L <= R; ++L) M[L] = lv[L][H];
+}
+
+template <int R, int BALL, int KIND, int DIL>
+__global__ void __launch_bounds__(kSThreads, 4)
+    k_morph16s(const __grid_constant__ Morph16Params P, const __grid_constant__ CUtensorMap tmap_deep,
+               const __grid_constant__ CUtensorMap tmap_one) {
+  using G = SG<R>;
+  using O = Op<DIL>;
+  constexpr int NDZ = BALL ? R + 1 : 1;
+  constexpr int KP = kSKP, NSG = kSNSG, NT = kSThreads;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int s_abort, s_fixovf;
+  __shared__ int s_frow[G::BH], s_fcol[G::BW], s_brow[G::BH], s_bcol[G::BW];
+  __shared__ int s_nbr, s_nbc;
+
+  const Job& J = P.job;
+  const int tid = threadIdx.x;
+  const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
+  const int64_t cx0 = J.core_lo[2] + (int64_t)tx * kPX;
+  const int64_t cy0 = J.core_lo[1] + (int64_t)ty * kPY;
+  const int64_t cz0 = J.core_lo[0] + (int64_t)blockIdx.y * P.zchunk;
+  const int64_t cz1 = min(cz0 + (int64_t)P.zchunk, J.core_hi[0]);
+  if (cz0 >= cz1) return;
+  const int nout = (int)(cz1 - cz0);
+  const int total = nout + 2 * R;  // input planes cz0-R .. cz1+R-1
+  const int ngroups = (total + KP - 1) / KP;
+  const int64_t Gz = J.gdims[0], Gy = J.gdims[1], Gx = J.gdims[2];
+  const bool face = (cx0 - R < 0) || (cx0 + kPX + R > Gx) || (cy0 - R < 0) || (cy0 + kPY + R > Gy);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* stages = smem + 128;
+
+  // face patch list: stage row r <-> y = cy0 - R + r, col c <-> x = cx0 - RA + c
+  int fix_d[kSFix], fix_s[kSFix];
+  int nfix = 0;
+  if (face) {
+    for (int r = tid; r < G::BH; r += NT) {
+      const int64_t sr = reflect(cy0 - R + r, Gy) - (cy0 - R);
+      s_frow[r] = (sr >= 0 && sr < G::BH) ? (int)sr : -1;
+    }
+    for (int c = tid; c < G::BW; c += NT) {
+      const int64_t sc = reflect(cx0 - G::RA + c, Gx) - (cx0 - G::RA);
+      s_fcol[c] = (sc >= 0 && sc < G::BW) ? (int)sc : -1;
+    }
+    if (tid == 0) s_fixovf = 0;
+    __syncthreads();
+    if (tid == 0) {
+      int nr = 0, nc = 0;
+      for (int r = 0; r < G::BH; ++r)
+        if (s_frow[r] != r) s_brow[nr++] = r;
+      for (int c = G::RA - R; c < G::RA + kPX + R; ++c)
+        if (s_fcol[c] != c) s_bcol[nc++] = c;
+      s_nbr = nr;
+      s_nbc = nc;
+    }
+    __syncthreads();
+    const int ncell = s_nbr * G::NC + s_nbc * G::BH;
+    for (int i = tid; i < ncell; i += NT) {
+      int r, c;
+      if (i < s_nbr * G::NC) {
+        r = s_brow[i / G::NC];
+        c = G::RA - R + i % G::NC;
+      } else {
+        const int k = i - s_nbr * G::NC;
+        c = s_bcol[k / G::BH];
+        r = k % G::BH;
+      }
+      const int sr = s_frow[r], sc = s_fcol[c];
+      if (sr < 0 || sc < 0) continue;
+      if (nfix < kSFix) {
+#pragma unroll
+        for (int m = 0; m < kSFix; ++m)
+          if (m == nfix) {
+            fix_d[m] = r * G::BW + c;
+            fix_s[m] = sr * G::BW + sc;
+          }
+        ++nfix;
+      } else {
+        s_fixovf = 1;
+      }
+    }
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    prefetch_tmap(&tmap_deep);
+    prefetch_tmap(&tmap_one);
+    for (int b = 0; b < NSG; ++b) mbar_init(&bars[b], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool fixovf = face && s_fixovf;
+
+  const int xl = (int)(cx0 - G::RA - J.in.lo[2]);
+  const int yl = (int)(cy0 - R - J.in.lo[1]);
+  auto issue = [&](int g) {
+    uint64_t* bar = &bars[g % NSG];
+    unsigned char* dst = stages + (g % NSG) * G::GB;
+    const int n0 = g * KP;
+    const int nv = min(KP, total - n0);
+    const int64_t z0 = cz0 - R + n0;
+    if (z0 >= 0 && z0 + nv <= Gz) {
+      mbar_arrive_expect_tx(bar, G::GB);
+      tma_load_3d(dst, &tmap_deep, xl, yl, (int)(z0 - J.in.lo[0]), bar);
+    } else {
+      mbar_arrive_expect_tx(bar, nv * G::PB);
+      for (int k = 0; k < nv; ++k)
+        tma_load_3d(dst + k * G::PB, &tmap_one, xl, yl, (int)(reflect(z0 + k, Gz) - J.in.lo[0]), bar);
+    }
+  };
+  if (tid == 0)
+    for (int g = 0; g < min(NSG, ngroups); ++g) issue(g);
+
+  // this thread: pair column xp, output rows ys .. ys + kSS - 1 of the tile
+  const int xp = tid % kPC, ys = (tid / kPC) * kSS;
+  uint32_t acc[2 * R + 1][kSS];
+#pragma unroll
+  for (int j = 0; j <= 2 * R; ++j)
+#pragma unroll
+    for (int i = 0; i < kSS; ++i) acc[j][i] = O::id;
+  const DevOut& Ob = J.out;
+  const int64_t gx = cx0 + 2 * xp;
+  const int64_t pstride = Ob.dims[1] * Ob.dims[2], rstride = Ob.dims[2];
+  uint16_t* optr = static_cast<uint16_t*>(Ob.ptr) +
+                   ((cz0 - Ob.lo[0]) * Ob.dims[1] + (cy0 + ys - Ob.lo[1])) * Ob.dims[2] + (gx - Ob.lo[2]);
+  const bool xok = gx < J.core_hi[2], xpair = gx + 1 < J.core_hi[2];
+  const int nrow = xok ? (int)max((int64_t)0, min((int64_t)kSS, J.core_hi[1] - (cy0 + ys))) : 0;
+  const bool full = xpair && nrow == kSS;
+  // word of this thread's window in a stage row
+  const int wofs = G::RA / 2 + xp - G::HP;
+
+  int j = 0;
+  for (; j < ngroups; ++j) {
+    if (!mbar_wait(&bars[j % NSG], (j / NSG) & 1)) atomicOr(&s_abort, 1);
+    unsigned char* sg = stages + (j % NSG) * G::GB;
+    const int nv = min(KP, total - j * KP);
+    if (face) {
+      for (int k = 0; k < nv; ++k) {
+        uint16_t* pl = reinterpret_cast<uint16_t*>(sg + k * G::PB);
+#pragma unroll
+        for (int c = 0; c < kSFix; ++c)
+          if (c < nfix) pl[fix_d[c]] = pl[fix_s[c]];
+        if (fixovf) {
+          int seen = 0;
+          const int ncell = s_nbr * G::NC + s_nbc * G::BH;
+          for (int i = tid; i < ncell; i += NT) {
+            int r, c;
+            if (i < s_nbr * G::NC) {
+              r = s_brow[i / G::NC];
+              c = G::RA - R + i % G::NC;
+            } else {
+              const int q = i - s_nbr * G::NC;
+              c = s_bcol[q / G::BH];
+              r = q % G::BH;
+            }
+            const int sr = s_frow[r], sc = s_fcol[c];
+            if (sr < 0 || sc < 0) continue;
+            if (seen++ < kSFix) continue;
+            pl[r * G::BW + c] = pl[sr * G::BW + sc];
+          }
+        }
+      }
+      fence_proxy_async();
+      __syncthreads();
+    }
+#pragma unroll 1
+    for (int k = 0; k < nv; ++k) {
+      const uint32_t* S = reinterpret_cast<const uint32_t*>(sg + k * G::PB) + ys * G::BWW + wofs;
+      // x-line minima of the strip's stage rows; disks of output row i once
+      // rows i .. i + 2R are in
+      uint32_t Mw[G::NR][R + 1];
+      uint32_t D[NDZ][kSS];
+#pragma unroll
+      for (int rr = 0; rr < G::NR; ++rr) {
+        uint32_t w[G::NW];
+#pragma unroll
+        for (int q = 0; q < G::NW; ++q) w[q] = to_keys<KIND>(S[rr * G::BWW + q]);
+        xline1<R, DIL>(w, Mw[rr]);
+        if (rr >= 2 * R) {
+          const int i = rr - 2 * R;
+          // row i + R + dy holds dy
+#pragma unroll
+          for (int dz = 0; dz < NDZ; ++dz) {
+            uint32_t d = O::id;
+#pragma unroll
+            for (int dy = -R; dy <= R; ++dy) {
+              const int L = BALL ? line_len(R, dz, dy) : R;
+              if (L >= 0) d = O::f2(d, Mw[i + R + dy][L]);
+            }
+            D[dz][i] = d;
+          }
+        }
+      }
+      // z ring: plane n = j*KP + k completes output plane cz0 + n - 2R
+      uint32_t out[kSS];
+#pragma unroll
+      for (int i = 0; i < kSS; ++i) {
+        out[i] = O::f2(acc[0][i], D[BALL ? R : 0][i]);
+#pragma unroll
+        for (int jj = 1; jj <= 2 * R; ++jj) {
+          const int d = jj > R ? jj - R : R - jj;
+          acc[jj - 1][i] = O::f2(acc[jj][i], D[BALL ? d : 0][i]);
+        }
+        acc[2 * R][i] = O::id;
+      }
+      const int n = j * KP + k;
+      if (n >= 2 * R) {
+        uint16_t* o = optr + (int64_t)(n - 2 * R) * pstride;
+        if (full) {
+#pragma unroll
+          for (int i = 0; i < kSS; ++i)
+            *reinterpret_cast<uint32_t*>(o + i * rstride) = from_keys<KIND>(out[i]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < kSS; ++i) {
+            if (i < nrow) {
+              const uint32_t v = from_keys<KIND>(out[i]);
+              if (xpair)
+                *reinterpret_cast<uint32_t*>(o + i * rstride) = v;
+              else
+                o[i * rstride] = (uint16_t)v;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (tid == 0 && j + NSG < ngroups) issue(j + NSG);
+  }
+  if (s_abort) {
+    set_device_error(P.err, kErrTimeout);
+    if (tid == 0)
+      for (int g = j + 1; g < min(j + NSG, ngroups); ++g)
+        (void)mbar_wait(&bars[g % NSG], (g / NSG) & 1);
+    __syncthreads();
+  }
+}
+
+template <int R, int BALL, int KIND, int DIL>
+cudaError_t launch_s(const Morph16Params& P0, const Job& job, int64_t tiles, int64_t cz,
+                     cudaStream_t s) {
+  using G = SG<R>;
+  static int slots_per_sm = 0;
+  if (!slots_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_morph16s<R, BALL, KIND, DIL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_morph16s<R, BALL, KIND, DIL>,
+                                                      kSThreads, G::SMEM);
+    if (e != cudaSuccess) return e;
+    slots_per_sm = std::max(1, nb);
+  }
+  CUtensorMap deep, one;
+  memset(&deep, 0, sizeof(deep));
+  memset(&one, 0, sizeof(one));
+  const int64_t dims[3] = {job.in.dims[2], job.in.dims[1], job.in.dims[0]};
+  if (!make_tmap_3d(&deep, job.in.ptr, job.in.dtype, dims, G::BW, G::BHP, kSKP) ||
+      !make_tmap_3d(&one, job.in.ptr, job.in.dtype, dims, G::BW, G::BHP, 1))
+    return cudaErrorNotSupported;
+  Morph16Params P = P0;
+  P.zchunk = (int)pick_zchunk(cz, tiles, (int64_t)slots_per_sm * num_sms(), 2 * R + kSKP, kSKP);
+  dim3 grid((unsigned)tiles, (unsigned)((cz + P.zchunk - 1) / P.zchunk));
+  if (log_level() > 0)
+    fprintf(stderr, "[hp] morph16 strip r=%d ball=%d kind=%d dilate=%d grid=%ux%u zchunk=%d slots/SM=%d\n",
+            R, BALL, KIND, DIL, grid.x, grid.y, P.zchunk, slots_per_sm);
+  k_morph16s<R, BALL, KIND, DIL><<<grid, kSThreads, G::SMEM, s>>>(P, deep, one);
+  return cudaGetLastError();
+}
+
+template <int KIND, int DIL>
+cudaError_t dispatch_s(int ball, int r, const Morph16Params& P, const Job& job, int64_t tiles,
+                       int64_t cz, cudaStream_t s) {
+  switch (r) {
+#define HP_MS(RR)                                                                   \
+  case RR:                                                                          \
+    return ball ? launch_s<RR, 1, KIND, DIL>(P, job, tiles, cz, s)                  \
+                : launch_s<RR, 0, KIND, DIL>(P, job, tiles, cz, s);
+    HP_MS(1) HP_MS(2) HP_MS(3)
+#undef HP_MS
+  }
+  return cudaErrorNotSupported;
+}
+
 }  // namespace
 
 // Returns cudaErrorNotSupported (nothing enqueued) when the job does not fit
@@ -466,6 +811,24 @@ cudaError_t launch_morph16(const Job& job, int se, int rad, int is_dilate, cudaS
     return cudaErrorNotSupported;
   if ((uintptr_t)job.out.ptr % 4 || job.out.dims[2] % 2 || (job.core_lo[2] - job.out.lo[2]) % 2)
     return cudaErrorNotSupported;
+  if (rad <= 3) {
+    // strip kernel: no line-minimum buffer in shared memory
+    Morph16Params P;
+    P.job = job;
+    P.tiles_x = (int)((cx + kPX - 1) / kPX);
+    P.zchunk = 0;
+    P.err = device_error_word();
+    const int64_t tiles = (int64_t)P.tiles_x * ((cy + kPY - 1) / kPY);
+    const int ball = se == HP_SE_BALL;
+    cudaError_t e;
+    if (dt == HP_U16)
+      e = is_dilate ? dispatch_s<0, 1>(ball, rad, P, job, tiles, cz, s)
+                    : dispatch_s<0, 0>(ball, rad, P, job, tiles, cz, s);
+    else
+      e = is_dilate ? dispatch_s<1, 1>(ball, rad, P, job, tiles, cz, s)
+                    : dispatch_s<1, 0>(ball, rad, P, job, tiles, cz, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
   const int64_t dims[3] = {job.in.dims[2], job.in.dims[1], job.in.dims[0]};

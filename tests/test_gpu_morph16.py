@@ -1,5 +1,6 @@
-"""GPU parity of the packed 16-bit erosion / dilation kernel (uint16 and
-float16 volumes whose rows are 16-byte multiples): bit-exact against the
+"""GPU parity of the packed 16-bit erosion / dilation kernels (uint16 and
+float16 volumes whose rows are 16-byte multiples; the register strip kernel
+for radii 1..3, the buffered one above): bit-exact against the
 oracle over every radius it takes, both structuring elements, several x
 tiles with a partial last tile, y extents that are not multiples of the
 tile height, volumes thinner than the radius allows for a full halo, and
@@ -34,7 +35,7 @@ def test_radii_u16_ragged_tiles(se, rad):
     _check(f, se, rad)
 
 
-@pytest.mark.parametrize("rad", [1, 3, 6])
+@pytest.mark.parametrize("rad", [1, 2, 3, 6])
 @pytest.mark.parametrize("se", [oracle.SE_BALL, oracle.SE_CUBE])
 def test_radii_f16(se, rad):
     f = rand_volume(np.float16, (14, 40, 72), 20 + rad)
@@ -54,7 +55,7 @@ def test_f16_special_values():
 
 
 @pytest.mark.parametrize("shape", [(9, 6, 8), (7, 3, 16), (40, 6, 24)])
-@pytest.mark.parametrize("rad", [3, 6])
+@pytest.mark.parametrize("rad", [1, 2, 3, 6])
 def test_thin_volumes(shape, rad):
     # extents down to the radius itself: every tile is a face tile and the
     # reflected sources fold across the whole extent

@@ -128,6 +128,19 @@ def _traffic(kernel: str, nvox: int):
         return None
 
 
+def reduce_over_ranks(local_ms: float, ws: int, units_per_rank: float, device=None):
+    """Whole-job timing of N replicas: the slowest rank's time (max over
+    ranks) and the units all ranks processed per second. Uses the default
+    process group when ws > 1."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    return total_ms, ws * units_per_rank / (total_ms / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -261,11 +274,7 @@ def run_hp(args):
         for nm, e in zip(names, ev[i]):
             per[nm] += prev.elapsed_time(e) / args.steps
             prev = e
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = ws * args.steps * N ** 3 / (total_ms / 1000.0)
+    total_ms, value = reduce_over_ranks(total_ms, ws, args.steps * N ** 3, dev)
 
     # per-kernel rooflines: algorithmic bytes (u16 in + out) and FP32 FMAs
     nvox = N ** 3

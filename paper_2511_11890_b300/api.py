@@ -203,6 +203,16 @@ def plan_bricks(shape, halo: int, in_bytes: int, out_bytes: int, budget: int, st
     return to_np(cores), to_np(boxes)
 
 
+def shard_bricks(n: int, rank: int, world: int):
+    """Indices of the bricks rank `rank` of `world` processes: round-robin over
+    the plan (brick i goes to rank i mod world), as the paper's multi-GPU
+    chunk scheduling does (Sec. III-D). Bricks are independent given their
+    read-only halos, so ranks exchange no data."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("rank must be in [0, world)")
+    return list(range(rank, int(n), world))
+
+
 def set_memory_budget(nbytes: int):
     check(lib.hp_set_memory_budget(int(nbytes)))
 

@@ -210,6 +210,15 @@ int hp_plan_bricks(int64_t nx, int64_t ny, int64_t nz, int halo, size_t in_bytes
  * HP_ERR_CUDA. */
 int hp_stream_status(void* stream);
 
+/* Diagnostic for the failure path of bounded device-side waits (the paper
+ * has no counterpart): enqueues on `stream` one small kernel that waits, with
+ * the same bounded mbarrier wait the filtering kernels use, on a barrier that
+ * nothing ever completes. The wait gives up after its poll limit and sets the
+ * device error word, so a following hp_stream_status(stream) returns
+ * HP_ERR_TIMEOUT and clears it; the CUDA context stays usable. No fault, trap
+ * or unbounded spin is involved. Returns HP_OK or HP_ERR_CUDA (launch). */
+int hp_selftest_wait_timeout(void* stream);
+
 /* Free cached filter-bank launch plans (graphs and work lists). */
 int hp_release_cache(void);
 

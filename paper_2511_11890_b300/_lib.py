@@ -27,7 +27,7 @@ EXPORTS = [
     "hp_gaussian3d", "hp_filterbank3d", "hp_filterbank3d_bricks", "hp_erode3d", "hp_dilate3d",
     "hp_threshold3d", "hp_filterbank3d_adjoint", "hp_morph3d_backward",
     "hp_morph3d_backward_noalloc", "hp_plan_bricks",
-    "hp_stream_status", "hp_release_cache", "hp_get_stats", "hp_last_error", "hp_version",
+    "hp_stream_status", "hp_selftest_wait_timeout", "hp_release_cache", "hp_get_stats", "hp_last_error", "hp_version",
 ]
 
 
@@ -77,6 +77,7 @@ def _load() -> ctypes.CDLL:
         "hp_plan_bricks": [i64, i64, i64, i, sz, sz, sz, i, i, ctypes.POINTER(hp_box),
                            ctypes.POINTER(hp_box), i, ctypes.POINTER(i)],
         "hp_stream_status": [vp],
+        "hp_selftest_wait_timeout": [vp],
         "hp_release_cache": [],
         "hp_get_stats": [ctypes.POINTER(hp_stats)],
     }

@@ -228,6 +228,13 @@ def stream_status(stream=None):
     check(lib.hp_stream_status(ctypes.c_void_p(s.cuda_stream)))
 
 
+def selftest_wait_timeout(stream=None):
+    """Enqueue a kernel whose bounded device-side wait runs out (diagnostic of
+    the failure path); the next stream_status() raises HP_ERR_TIMEOUT."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    check(lib.hp_selftest_wait_timeout(ctypes.c_void_p(s.cuda_stream)))
+
+
 def stats() -> dict:
     s = hp_stats()
     check(lib.hp_get_stats(ctypes.byref(s)))

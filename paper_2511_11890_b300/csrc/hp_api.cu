@@ -29,6 +29,7 @@
 #include <thread>
 #include <vector>
 
+#include "hp_device.cuh"
 #include "hp_internal.h"
 
 struct hp_volume {
@@ -118,6 +119,18 @@ int* device_error_word() {
     g_err_ptr[dev] = static_cast<int*>(p);
   }
   return g_err_ptr[dev];
+}
+
+// A bounded mbarrier wait on a barrier that nothing completes: the wait
+// gives up after its poll limit and records a timeout in the error word.
+__global__ void k_wait_selftest(int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) set_device_error(err, kErrTimeout);
 }
 
 int log_level() {
@@ -759,6 +772,15 @@ int hp_plan_bricks(int64_t nx, int64_t ny, int64_t nz, int halo, size_t in_bytes
     if (cores) cores[i] = b[i].core;
     if (in_boxes) in_boxes[i] = b[i].in;
   }
+  return HP_OK;
+}
+
+int hp_selftest_wait_timeout(void* stream) {
+  int* ew = device_error_word();
+  if (!ew) return set_error(HP_ERR_CUDA, "no device error word");
+  k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(ew);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "wait self-test launch");
   return HP_OK;
 }
 

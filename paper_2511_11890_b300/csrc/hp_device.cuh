@@ -11,10 +11,11 @@
 
 namespace hp {
 
-// Poll limit of a bounded mbarrier wait. try_wait suspends the thread for a
-// hardware-defined interval per attempt, so this bounds the wait to well
-// under a second on a healthy GPU while never spinning forever.
-constexpr uint32_t kWaitLimit = 1u << 22;
+// Poll limit of a bounded mbarrier wait. A try_wait on an incomplete phase
+// suspends the thread for a few microseconds before it returns false
+// (measured on B300: 2^22 polls took 16 s), so 2^18 polls give up after about
+// one second, far above any TMA completion time of a healthy GPU.
+constexpr uint32_t kWaitLimit = 1u << 18;
 
 // Error word codes (OR-ed together).
 constexpr int kErrTimeout = 1;

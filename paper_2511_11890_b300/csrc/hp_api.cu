@@ -155,6 +155,20 @@ int num_sms() {
   return cached[dev];
 }
 
+int max_dyn_smem() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 227 * 1024 - 1024;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || n <= 0)
+      n = 227 * 1024;
+    cached[dev] = n - 1024;
+  }
+  return cached[dev];
+}
+
 int64_t pick_zchunk(int64_t cz, int64_t tiles, int64_t slots, int halo, int align) {
   if (cz <= 0) return align;
   slots = std::max<int64_t>(1, slots);

@@ -97,6 +97,10 @@ bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t d
 
 int num_sms();
 
+// Largest dynamic shared memory a block may opt into on the current device,
+// less 1 KB for the kernels' static shared variables.
+int max_dyn_smem();
+
 // z-chunk length for a z-march grid of `tiles` columns: CTAs run in waves
 // of `slots` (resident CTAs on the whole GPU) and each costs about its
 // planes plus `halo`; returns the multiple of `align` that minimises

@@ -31,6 +31,7 @@
 
 #include "hp_device.cuh"
 #include "hp_internal.h"
+#include "k_bank.cuh"
 
 namespace hp {
 
@@ -38,7 +39,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kNS = 4;
-constexpr int kMaxGroups = 8;
+constexpr int kMaxGroups = kBankMaxGroups;
 constexpr int kBZ = 8;
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -47,41 +48,6 @@ __host__ __device__ constexpr int patch_stride(int n) {
   while (f % 8 != 4) ++f;
   return f;
 }
-
-struct BankItem {
-  int group;    // sigma group
-  int tile_x0;  // tile origin (global)
-  int tile_y0;
-  int z0, z1;   // output z range (global)
-  int x1, y1;   // exclusive bounds of the brick core in x, y
-  int cfg;      // tile configuration (0: 16x16, 1: 32x16)
-};
-
-struct BankGroup {
-  int r;
-  float w[3][2 * kMaxR + 1];  // taps of orders 0, 1, 2
-  void* out[3];               // G, GM, LoG (nullptr when not requested)
-};
-
-struct BankParams {
-  const void* in;
-  int dtype;
-  int out_dtype;
-  int64_t G[3];  // (z, y, x)
-  int ngroups;
-  BankGroup grp[kMaxGroups];
-  const BankItem* items;
-  int nitems;
-  int* counter;
-  int* err;
-  int use_tma;
-};
-
-// One TMA map per sigma group (box width and height depend on the radius
-// and the tile configuration of that group).
-struct BankMaps {
-  CUtensorMap m[kMaxGroups];
-};
 
 template <int R, int TX, int TY>
 struct BGeom {
@@ -471,6 +437,7 @@ struct BankPlan {
   BankMaps maps;
   int smem = 0;
   int grid = 0;
+  const void* kernel = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   size_t bytes = 0;
@@ -561,15 +528,31 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
     if (slot) return set_error(HP_ERR_INVALID_ARG, "filter bank: duplicate (kind, sigma)");
     slot = q.outs[i];
   }
+  // Kernel choice. The four-plane kernel (k_bank2) takes uint16, float16
+  // and float32 inputs that TMA can address (16-byte aligned base and rows,
+  // brick x origins on multiples of 16) in volumes at least r_max + 1 wide in
+  // x and y (one reflection lands inside the staged box); the first kernel
+  // takes everything else.
+  const int es = (int)dtype_size(q.dtype);
+  int rmax = 0;
+  for (int g = 0; g < P.ngroups; ++g) rmax = std::max(rmax, P.grp[g].r);
+  bool tma = ((uintptr_t)q.in % 16 == 0) && ((q.G[2] * es) % 16 == 0) && getenv("HP_NO_TMA") == nullptr;
+  for (auto& b : q.bricks) tma = tma && (b.lo[2] % 16 == 0);
+  const bool v2 = tma && (q.dtype == HP_U16 || q.dtype == HP_F16 || q.dtype == HP_F32) &&
+                  q.G[1] > rmax && q.G[2] > rmax && getenv("HP_BANK_V1") == nullptr;
+  auto cfg_of = [&](int r) {
+    if (t.small_cfg != 1) return 0;
+    if (v2) return (r <= b2::kWideMaxR && b2::geo(r, 32, 16, es).SMEM <= max_dyn_smem()) ? 1 : 0;
+    return r <= 4 ? 1 : 0;
+  };
   // work list over bricks: groups (heaviest first) x bricks x tiles x z chunks
   std::vector<BankItem> items;
-  const int es = (int)dtype_size(q.dtype);
   int smem = 0;
   for (int g = 0; g < P.ngroups; ++g) {
     const int r = P.grp[g].r;
-    const int cfg = (t.small_cfg == 1 && r <= 4) ? 1 : 0;
+    const int cfg = cfg_of(r);
     const int TX = cfg == 1 ? 32 : 16, TY = 16;
-    smem = std::max(smem, cfg_smem(cfg, r, es));
+    smem = std::max(smem, v2 ? b2::geo(r, TX, TY, es).SMEM : cfg_smem(cfg, r, es));
     for (auto& b : q.bricks)
       for (int64_t y0 = b.lo[1]; y0 < b.hi[1]; y0 += TY)
         for (int64_t x0 = b.lo[2]; x0 < b.hi[2]; x0 += TX)
@@ -586,6 +569,7 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
             items.push_back(it);
           }
   }
+  if (smem > max_dyn_smem()) return set_error(HP_ERR_UNSUPPORTED, "filter bank: tile does not fit in shared memory");
   P.nitems = (int)items.size();
   cudaError_t e;
   if ((e = cudaMalloc(&plan->d_items, sizeof(BankItem) * std::max<size_t>(1, items.size()))) != cudaSuccess)
@@ -599,26 +583,32 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   P.items = plan->d_items;
   P.counter = plan->d_counter;
   P.err = device_error_word();
-  // TMA maps, one per sigma group: 16-byte rows, and tile x origins that
-  // are multiples of 16 elements (brick x origins must be).
-  bool tma = ((uintptr_t)q.in % 16 == 0) && ((q.G[2] * es) % 16 == 0) && getenv("HP_NO_TMA") == nullptr;
-  for (auto& b : q.bricks) tma = tma && (b.lo[2] % 16 == 0);
+  // TMA maps, per sigma group.
   memset(&plan->maps, 0, sizeof(plan->maps));
+  const int64_t dims[3] = {q.G[2], q.G[1], q.G[0]};
   for (int g = 0; g < P.ngroups && tma; ++g) {
     const int r = P.grp[g].r;
-    const int tx = (t.small_cfg == 1 && r <= 4) ? 32 : 16;
-    int ra = 0, bw = 0;
-    bbox_geom(r, tx, es, &ra, &bw);
-    const int64_t dims[3] = {q.G[2], q.G[1], q.G[0]};
-    tma = make_tmap_3d(&plan->maps.m[g], q.in, q.dtype, dims, bw, 16 + 2 * r);
+    const int tx = cfg_of(r) == 1 ? 32 : 16;
+    if (v2) {
+      const b2::Geo gm = b2::geo(r, tx, 16, es);
+      tma = make_tmap_3d(&plan->maps.m[g], q.in, q.dtype, dims, gm.BW, gm.BHP, b2::kKP) &&
+            make_tmap_3d(&plan->maps.m1[g], q.in, q.dtype, dims, gm.BW, gm.BHP, 1);
+    } else {
+      int ra = 0, bw = 0;
+      bbox_geom(r, tx, es, &ra, &bw);
+      tma = make_tmap_3d(&plan->maps.m[g], q.in, q.dtype, dims, bw, 16 + 2 * r);
+    }
   }
+  if (v2 && !tma) return set_error(HP_ERR_CUDA, "filter bank: TMA map encoding failed");
   P.use_tma = tma ? 1 : 0;
   plan->smem = smem;
+  const void* kfn = v2 ? bank2_kernel(q.dtype) : reinterpret_cast<const void*>(&k_bank);
+  plan->kernel = kfn;
   const int sms = num_sms();
-  if ((e = cudaFuncSetAttribute(k_bank, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-    return cuda_fail(e, "cudaFuncSetAttribute(k_bank)");
+  if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute(filter bank)");
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bank, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem);
   plan->grid = std::max(1, std::min(P.nitems, sms * std::max(1, per_sm)));
   // graph: reset the counter, then the persistent launch
   if ((e = cudaGraphCreate(&plan->graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
@@ -635,7 +625,7 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof(kp));
   void* args[2] = {&plan->P, &plan->maps};
-  kp.func = (void*)k_bank;
+  kp.func = const_cast<void*>(plan->kernel);
   kp.gridDim = dim3(plan->grid);
   kp.blockDim = dim3(kThreads);
   kp.sharedMemBytes = smem;
@@ -690,8 +680,10 @@ static int tune(const BankRequest& q, cudaStream_t s, BankTune* best) {
     float ms = 0;
     cudaEventElapsedTime(&ms, a, b);
     if (log_level() > 0)
-      fprintf(stderr, "[hp] bank tune cfg=%d zchunk=%d tma=%d grid=%d items=%d: %.3f ms\n",
-              c.small_cfg, c.zchunk, pl->P.use_tma, pl->grid, pl->P.nitems, ms);
+      fprintf(stderr, "[hp] bank tune cfg=%d zchunk=%d tma=%d kernel=%s grid=%d items=%d: %.3f ms\n",
+              c.small_cfg, c.zchunk, pl->P.use_tma,
+              pl->kernel == reinterpret_cast<const void*>(&k_bank) ? "k_bank" : "k_bank2", pl->grid,
+              pl->P.nitems, ms);
     if (ms < best_ms) {
       best_ms = ms;
       bt = c;
@@ -731,6 +723,19 @@ int run_filterbank(const BankRequest& q, cudaStream_t s) {
     g_plans[k] = std::move(np);
   }
   return launch_plan(*pl, s);
+}
+
+const void* bank2_kernel_u16();
+const void* bank2_kernel_f16();
+const void* bank2_kernel_f32();
+
+const void* bank2_kernel(int dtype) {
+  switch (dtype) {
+    case HP_U16: return bank2_kernel_u16();
+    case HP_F16: return bank2_kernel_f16();
+    case HP_F32: return bank2_kernel_f32();
+    default: return nullptr;
+  }
 }
 
 }  // namespace hp

@@ -1,0 +1,6 @@
+// Four-plane filter-bank kernel for float32 input.
+#include "k_bank.cuh"
+
+namespace hp {
+const void* bank2_kernel_f32() { return reinterpret_cast<const void*>(&b2::k_bank2<float>); }
+}  // namespace hp

@@ -1,6 +1,9 @@
 // Multi-sigma derivative-of-Gaussian filter bank (Harpia Sec. III-C:
 // Gaussian smoothing and "Hessian" texture features) in one persistent
-// launch.
+// launch: work list, autotuner, CUDA graph, and the single-plane kernel
+// k_bank for inputs the four-plane kernel (k_bank2, k_bank.cuh) does not
+// take (rows or brick origins TMA cannot address, uint8, volumes not wider
+// than the largest radius in x or y).
 //
 // Per sigma the bank needs seven separable filters that share
 // intermediates: the x pass applies g0, g1, g2 (3 planes), the y pass forms
@@ -12,8 +15,8 @@
 // The work list holds (sigma group, tile, z range) items over a set of
 // bricks; persistent CTAs take items from an atomic counter, heaviest sigma
 // first. Halos come from the whole device volume, so any brick set gives the
-// whole-volume result bit for bit. The item pipeline is the z-march of the
-// Gaussian kernel (TMA plane loads, one barrier per plane), widened to 3/5/7
+// whole-volume result bit for bit. The single-plane kernel is the z-march of
+// the Gaussian kernel (plane loads, one barrier per plane) widened to 3/5/7
 // planes; tile shape and z-chunk length come from the autotuner.
 #include <cuda_fp16.h>
 #include <stdio.h>
@@ -659,8 +662,8 @@ static int tune(const BankRequest& q, cudaStream_t s, BankTune* best) {
     }
   }
   const char* env = getenv("HP_BANK_TUNE");
-  std::vector<BankTune> cands = {{1, 32}, {1, 64}, {0, 32}, {0, 64}};
-  if (env && !strcmp(env, "0")) cands = {{1, 64}};
+  std::vector<BankTune> cands = {{1, 64}, {1, 128}, {1, 256}, {0, 128}, {0, 256}};
+  if (env && !strcmp(env, "0")) cands = {{1, 256}};
   float best_ms = 1e30f;
   BankTune bt = cands[0];
   cudaEvent_t a, b;

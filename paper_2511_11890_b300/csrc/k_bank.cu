@@ -429,18 +429,27 @@ struct BankRequest {
 // Tuning knobs picked by the autotuner: tile configuration for small radii
 // and z-chunk length.
 struct BankTune {
-  int small_cfg;  // 0: 16x16 tiles for all radii, 1: 32x16 tiles for r <= 4
+  // 0: 16x16 tiles for all radii; 1: 32x16 tiles for small radii (r <= 4 on
+  // the single-plane kernel, r <= 6 where it fits on the four-plane kernel);
+  // 2: four-plane kernel only: radii <= 6 in a second launch of 16x16 tiles
+  // at two CTAs per SM, beside the one-CTA-per-SM launch of the rest.
+  int small_cfg;
   int zchunk;
 };
 
 struct BankPlan {
   BankParams P;
   BankItem* d_items = nullptr;
-  int* d_counter = nullptr;
+  int* d_counter = nullptr;  // [2]: one per launch
   BankMaps maps;
   int smem = 0;
   int grid = 0;
   const void* kernel = nullptr;
+  // second launch (small radii at two CTAs per SM), when split
+  BankParams P2;
+  int smem2 = 0;
+  int grid2 = 0;
+  const void* kernel2 = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   size_t bytes = 0;
@@ -548,14 +557,33 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
     if (v2) return (r <= b2::kWideMaxR && b2::geo(r, 32, 16, es).SMEM <= max_dyn_smem()) ? 1 : 0;
     return r <= 4 ? 1 : 0;
   };
+  // split: radii <= kWideMaxR to the two-CTAs-per-SM launch when two of its
+  // CTAs fit an SM
+  const void* kfn2 = v2 ? bank2_kernel(q.dtype, 2) : nullptr;
+  bool split = false;
+  if (v2 && t.small_cfg == 2) {
+    int s2 = 0;
+    for (int g = 0; g < P.ngroups; ++g)
+      if (P.grp[g].r <= b2::kWideMaxR) s2 = std::max(s2, b2::geo(P.grp[g].r, 16, 16, es).SMEM);
+    int per_sm2 = 0;
+    if (s2 > 0 && cudaFuncSetAttribute(kfn2, cudaFuncAttributeMaxDynamicSharedMemorySize, s2) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kfn2, kThreads, s2) == cudaSuccess && per_sm2 >= 2) {
+      split = true;
+      plan->smem2 = s2;
+      plan->grid2 = num_sms() * per_sm2;
+    }
+    (void)cudaGetLastError();
+  }
   // work list over bricks: groups (heaviest first) x bricks x tiles x z chunks
-  std::vector<BankItem> items;
+  std::vector<BankItem> items, items2;
   int smem = 0;
   for (int g = 0; g < P.ngroups; ++g) {
     const int r = P.grp[g].r;
     const int cfg = cfg_of(r);
     const int TX = cfg == 1 ? 32 : 16, TY = 16;
-    smem = std::max(smem, v2 ? b2::geo(r, TX, TY, es).SMEM : cfg_smem(cfg, r, es));
+    const bool second = split && r <= b2::kWideMaxR;
+    if (!second) smem = std::max(smem, v2 ? b2::geo(r, TX, TY, es).SMEM : cfg_smem(cfg, r, es));
+    std::vector<BankItem>& list = second ? items2 : items;
     for (auto& b : q.bricks)
       for (int64_t y0 = b.lo[1]; y0 < b.hi[1]; y0 += TY)
         for (int64_t x0 = b.lo[2]; x0 < b.hi[2]; x0 += TX)
@@ -569,19 +597,21 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
             it.x1 = (int)b.hi[2];
             it.y1 = (int)b.hi[1];
             it.cfg = cfg;
-            items.push_back(it);
+            list.push_back(it);
           }
   }
   if (smem > max_dyn_smem()) return set_error(HP_ERR_UNSUPPORTED, "filter bank: tile does not fit in shared memory");
   P.nitems = (int)items.size();
   cudaError_t e;
-  if ((e = cudaMalloc(&plan->d_items, sizeof(BankItem) * std::max<size_t>(1, items.size()))) != cudaSuccess)
+  const size_t nall = items.size() + items2.size();
+  if ((e = cudaMalloc(&plan->d_items, sizeof(BankItem) * std::max<size_t>(1, nall))) != cudaSuccess)
     return cuda_fail(e, "cudaMalloc(work list)");
-  if ((e = cudaMalloc(&plan->d_counter, sizeof(int))) != cudaSuccess)
+  if ((e = cudaMalloc(&plan->d_counter, 2 * sizeof(int))) != cudaSuccess)
     return cuda_fail(e, "cudaMalloc(counter)");
-  plan->bytes = sizeof(BankItem) * items.size() + sizeof(int);
-  if ((e = cudaMemcpy(plan->d_items, items.data(), sizeof(BankItem) * items.size(),
-                      cudaMemcpyHostToDevice)) != cudaSuccess)
+  plan->bytes = sizeof(BankItem) * nall + 2 * sizeof(int);
+  items.insert(items.end(), items2.begin(), items2.end());
+  if (nall && (e = cudaMemcpy(plan->d_items, items.data(), sizeof(BankItem) * nall,
+                              cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "copy work list");
   P.items = plan->d_items;
   P.counter = plan->d_counter;
@@ -604,8 +634,16 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   }
   if (v2 && !tma) return set_error(HP_ERR_CUDA, "filter bank: TMA map encoding failed");
   P.use_tma = tma ? 1 : 0;
+  plan->P2 = P;
+  plan->P2.items = plan->d_items + P.nitems;
+  plan->P2.nitems = (int)items2.size();
+  plan->P2.counter = plan->d_counter + 1;
+  if (split && !items2.empty()) {
+    plan->kernel2 = kfn2;
+    plan->grid2 = std::max(1, std::min(plan->P2.nitems, plan->grid2));
+  }
   plan->smem = smem;
-  const void* kfn = v2 ? bank2_kernel(q.dtype) : reinterpret_cast<const void*>(&k_bank);
+  const void* kfn = v2 ? bank2_kernel(q.dtype, 1) : reinterpret_cast<const void*>(&k_bank);
   plan->kernel = kfn;
   const int sms = num_sms();
   if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
@@ -613,7 +651,8 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem);
   plan->grid = std::max(1, std::min(P.nitems, sms * std::max(1, per_sm)));
-  // graph: reset the counter, then the persistent launch
+  // graph: reset the counters, then the persistent launch(es); two launches
+  // are sibling nodes, so the second fills SMs as the first drains
   if ((e = cudaGraphCreate(&plan->graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
   cudaGraphNode_t mset, kern;
   cudaMemsetParams mp;
@@ -621,20 +660,34 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   mp.dst = plan->d_counter;
   mp.value = 0;
   mp.elementSize = 4;
-  mp.width = 1;
+  mp.width = 2;
   mp.height = 1;
   if ((e = cudaGraphAddMemsetNode(&mset, plan->graph, nullptr, 0, &mp)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphAddMemsetNode");
-  cudaKernelNodeParams kp;
-  memset(&kp, 0, sizeof(kp));
-  void* args[2] = {&plan->P, &plan->maps};
-  kp.func = const_cast<void*>(plan->kernel);
-  kp.gridDim = dim3(plan->grid);
-  kp.blockDim = dim3(kThreads);
-  kp.sharedMemBytes = smem;
-  kp.kernelParams = args;
-  if ((e = cudaGraphAddKernelNode(&kern, plan->graph, &mset, 1, &kp)) != cudaSuccess)
-    return cuda_fail(e, "cudaGraphAddKernelNode");
+  if (P.nitems > 0 || !plan->kernel2) {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    void* args[2] = {&plan->P, &plan->maps};
+    kp.func = const_cast<void*>(plan->kernel);
+    kp.gridDim = dim3(plan->grid);
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = smem;
+    kp.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&kern, plan->graph, &mset, 1, &kp)) != cudaSuccess)
+      return cuda_fail(e, "cudaGraphAddKernelNode");
+  }
+  if (plan->kernel2) {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    void* args[2] = {&plan->P2, &plan->maps};
+    kp.func = const_cast<void*>(plan->kernel2);
+    kp.gridDim = dim3(plan->grid2);
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = plan->smem2;
+    kp.kernelParams = args;
+    if ((e = cudaGraphAddKernelNode(&kern, plan->graph, &mset, 1, &kp)) != cudaSuccess)
+      return cuda_fail(e, "cudaGraphAddKernelNode");
+  }
   if ((e = cudaGraphInstantiate(&plan->exec, plan->graph, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphInstantiate");
   *out = std::move(plan);
@@ -662,7 +715,7 @@ static int tune(const BankRequest& q, cudaStream_t s, BankTune* best) {
     }
   }
   const char* env = getenv("HP_BANK_TUNE");
-  std::vector<BankTune> cands = {{1, 64}, {1, 128}, {1, 256}, {0, 128}, {0, 256}};
+  std::vector<BankTune> cands = {{1, 64}, {1, 128}, {1, 256}, {0, 256}, {2, 128}, {2, 256}};
   if (env && !strcmp(env, "0")) cands = {{1, 256}};
   float best_ms = 1e30f;
   BankTune bt = cands[0];
@@ -683,10 +736,10 @@ static int tune(const BankRequest& q, cudaStream_t s, BankTune* best) {
     float ms = 0;
     cudaEventElapsedTime(&ms, a, b);
     if (log_level() > 0)
-      fprintf(stderr, "[hp] bank tune cfg=%d zchunk=%d tma=%d kernel=%s grid=%d items=%d: %.3f ms\n",
+      fprintf(stderr, "[hp] bank tune cfg=%d zchunk=%d tma=%d kernel=%s grid=%d items=%d (+%d on %d CTAs at 2/SM): %.3f ms\n",
               c.small_cfg, c.zchunk, pl->P.use_tma,
               pl->kernel == reinterpret_cast<const void*>(&k_bank) ? "k_bank" : "k_bank2", pl->grid,
-              pl->P.nitems, ms);
+              pl->P.nitems, pl->kernel2 ? pl->P2.nitems : 0, pl->kernel2 ? pl->grid2 : 0, ms);
     if (ms < best_ms) {
       best_ms = ms;
       bt = c;
@@ -728,15 +781,15 @@ int run_filterbank(const BankRequest& q, cudaStream_t s) {
   return launch_plan(*pl, s);
 }
 
-const void* bank2_kernel_u16();
-const void* bank2_kernel_f16();
-const void* bank2_kernel_f32();
+const void* bank2_kernel_u16(int minb);
+const void* bank2_kernel_f16(int minb);
+const void* bank2_kernel_f32(int minb);
 
-const void* bank2_kernel(int dtype) {
+const void* bank2_kernel(int dtype, int minb) {
   switch (dtype) {
-    case HP_U16: return bank2_kernel_u16();
-    case HP_F16: return bank2_kernel_f16();
-    case HP_F32: return bank2_kernel_f32();
+    case HP_U16: return bank2_kernel_u16(minb);
+    case HP_F16: return bank2_kernel_f16(minb);
+    case HP_F32: return bank2_kernel_f32(minb);
     default: return nullptr;
   }
 }

@@ -77,8 +77,9 @@ __device__ __forceinline__ void bank_store(void* base, int dt, int64_t idx, floa
 }
 
 // Kernel entry of the four-plane bank for one input type (uint16, float16,
-// float32); defined in k_bank2_<type>.cu.
-const void* bank2_kernel(int dtype);
+// float32) and residency (1: all radii, one CTA per SM; 2: r <= 6 on 16 x 16
+// tiles, two CTAs per SM); defined in k_bank2_<type>.cu.
+const void* bank2_kernel(int dtype, int minb);
 
 namespace b2 {
 
@@ -237,10 +238,19 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
   const int ngr = (total + kKP - 1) / kKP;
   const bool xface = (cx0 - R < 0) || (cx0 + TX + R > Gx);
 
-  for (int row = tid; row < g.BH; row += kThreads)
-    srow[row] = (int)(reflect(cy0 - R + row, Gy) - (cy0 - R));
-  for (int c = tid; c < TX + 2 * R; c += kThreads)
-    scol[c] = (int)(reflect(cx0 - R + c, Gx) - (cx0 - g.RA));
+  // Staged row / column of each reflected input coordinate. Every input a
+  // stored output reads reflects into the staged box (the volume is wider
+  // than R in x and y); rows and columns that feed only outputs beyond the
+  // volume (a ragged last tile, reflected twice) are clamped into the box so
+  // that every shared-memory read stays in bounds.
+  for (int row = tid; row < g.BH; row += kThreads) {
+    const int64_t sr = reflect(cy0 - R + row, Gy) - (cy0 - R);
+    srow[row] = (int)(sr < 0 ? 0 : (sr >= g.BH ? g.BH - 1 : sr));
+  }
+  for (int c = tid; c < TX + 2 * R; c += kThreads) {
+    const int64_t sc = reflect(cx0 - R + c, Gx) - (cx0 - g.RA);
+    scol[c] = (int)(sc < 0 ? 0 : (sc >= g.BW ? g.BW - 1 : sc));
+  }
   Taps3<R> T;
 #pragma unroll
   for (int f = 0; f < 3; ++f)
@@ -443,8 +453,12 @@ __device__ __forceinline__ void dispatch2_wide(int r, const BankParams& P, const
 constexpr int kWideMaxR = 6;
 
 // Persistent kernel: CTAs take items from the counter until the list ends.
-template <typename TIN>
-__global__ void __launch_bounds__(kThreads, 1)
+// MINB = 1: every radius, 16 x 16 or 32 x 16 tiles, one CTA per SM.
+// MINB = 2: radii up to kWideMaxR on 16 x 16 tiles only (at most ~113 KB of
+// shared memory for 16-bit inputs), two CTAs per SM and at most 128
+// registers per thread.
+template <typename TIN, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     k_bank2(const __grid_constant__ BankParams P, const __grid_constant__ BankMaps maps) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_item;
@@ -463,10 +477,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (i >= P.nitems || s_abort) break;
     const BankItem it = P.items[i];
     const int r = P.grp[it.group].r;
-    if (it.cfg == 1)
-      dispatch2_wide<TIN>(r, P, maps, it, smem, gbase, &s_abort);
-    else
-      dispatch2<16, 16, TIN>(r, P, maps, it, smem, gbase, &s_abort);
+    if constexpr (MINB == 1) {
+      if (it.cfg == 1)
+        dispatch2_wide<TIN>(r, P, maps, it, smem, gbase, &s_abort);
+      else
+        dispatch2<16, 16, TIN>(r, P, maps, it, smem, gbase, &s_abort);
+    } else {
+      switch (r) {
+#define HP_B2(RR) \
+  case RR: run_item2<RR, 16, 16, TIN>(P, maps, it, smem, gbase, &s_abort); break;
+        HP_B2(1) HP_B2(2) HP_B2(3) HP_B2(4) HP_B2(5) HP_B2(6)
+#undef HP_B2
+      }
+    }
   }
   if (s_abort && threadIdx.x == 0) set_device_error(P.err, kErrTimeout);
 }

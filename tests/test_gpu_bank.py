@@ -87,3 +87,31 @@ def test_bank_512_37_bricks_sampled():
     whole = hp.filterbank3d(x, BANK)
     for a, b in zip(outs, whole):
         assert torch.equal(a.view(torch.int16), b.view(torch.int16))
+
+
+@pytest.mark.parametrize("r", list(range(1, 13)))
+def test_bank_every_radius(r):
+    """Each radius 1..12 of the four-plane kernel (16 x 16 tiles, and
+    32 x 16 where r <= 6 fits), all three outputs, against the oracle; the
+    x extent keeps 16-byte rows so that the TMA path is taken, the y extent
+    is ragged against both tile heights."""
+    sigma = r / 3.0
+    assert oracle.radius(sigma) == r
+    f = synth.porous_f16((22, 37, 64), 100 + r)
+    filt = [(hp.G, sigma), (hp.GM, sigma), (hp.LOG, sigma)]
+    outs = hp.filterbank3d(to_dev(f), filt, out_dtype=hp.HP_F32)
+    for (k, s), o, ref in zip(filt, outs, _oracle_bank(f, filt)):
+        assert_filter_close(to_np(o), ref, f"r={r} kind {k}")
+
+
+@pytest.mark.parametrize("dtype", [np.float16, np.uint16, np.float32])
+def test_bank_thin_z_and_partial_groups(dtype):
+    """Volumes thinner in z than the radius (reflection bounces more than
+    once; every plane group is loaded plane by plane) and z extents that end
+    in a partial group of four planes."""
+    for shape in [(5, 40, 64), (7, 24, 32), (30, 20, 48)]:
+        f = synth.porous_f16(shape, 7) if dtype == np.float16 else rand_volume(dtype, shape, 8)
+        filt = [(k, s) for s in (1.0, 4.0) for k in (hp.G, hp.GM, hp.LOG)]
+        outs = hp.filterbank3d(to_dev(f), filt, out_dtype=hp.HP_F32)
+        for (k, s), o, ref in zip(filt, outs, _oracle_bank(f, filt)):
+            assert_filter_close(to_np(o), ref, f"{dtype.__name__} {shape} kind {k} sigma {s}")

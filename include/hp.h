@@ -104,6 +104,7 @@ typedef struct {
   uint64_t h2d_bytes;         /* host-to-device bytes of the last call */
   uint64_t d2h_bytes;         /* device-to-host bytes of the last call */
   double wall_ms;             /* wall time of the last host-mode call */
+  uint64_t bank_kernels;      /* kernels one launch of the last filter-bank plan runs (1 or 2) */
 } hp_stats;
 
 /* Create a view of `data` (dtype, location) with extents nx (fastest), ny,

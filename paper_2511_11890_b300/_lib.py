@@ -50,7 +50,7 @@ class hp_stats(ctypes.Structure):
                 ("live_device_bytes", ctypes.c_size_t), ("cached_device_bytes", ctypes.c_size_t),
                 ("pinned_host_bytes", ctypes.c_size_t), ("bricks", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
-                ("wall_ms", ctypes.c_double)]
+                ("wall_ms", ctypes.c_double), ("bank_kernels", ctypes.c_uint64)]
 
 
 def _load() -> ctypes.CDLL:

@@ -108,6 +108,7 @@ static int* g_err_ptr[64];
 static std::mutex g_err_mu;
 
 int64_t bank_cache_bytes();
+int bank_last_kernels();
 
 int* device_error_word() {
   int dev = 0;
@@ -820,6 +821,7 @@ int hp_get_stats(hp_stats* s) {
   s->live_device_bytes = (size_t)std::max<int64_t>(0, g_live.load());
   s->peak_device_bytes = (size_t)std::max<int64_t>(0, g_peak.load());
   s->cached_device_bytes = (size_t)std::max<int64_t>(0, bank_cache_bytes());
+  s->bank_kernels = (uint64_t)bank_last_kernels();
   return HP_OK;
 }
 

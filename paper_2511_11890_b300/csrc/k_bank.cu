@@ -466,7 +466,10 @@ static std::map<std::string, std::unique_ptr<BankPlan>> g_plans;
 static std::map<std::string, BankTune> g_tuned;
 static std::atomic<int64_t> g_plan_bytes{0};
 
+static std::atomic<int> g_last_kernels{0};
+
 int64_t bank_cache_bytes() { return g_plan_bytes.load(); }
+int bank_last_kernels() { return g_last_kernels.load(); }
 
 void bank_release_cache() {
   std::lock_guard<std::mutex> lk(g_bank_mu);
@@ -697,6 +700,7 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
 static int launch_plan(BankPlan& pl, cudaStream_t s) {
   cudaError_t e = cudaGraphLaunch(pl.exec, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch(filter bank)");
+  g_last_kernels.store((pl.P.nitems > 0 || !pl.kernel2 ? 1 : 0) + (pl.kernel2 ? 1 : 0));
   return HP_OK;
 }
 

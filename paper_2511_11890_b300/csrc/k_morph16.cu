@@ -687,15 +687,41 @@ __global__ void __launch_bounds__(kSThreads, 4)
         if (rr >= 2 * R) {
           const int i = rr - 2 * R;
           // row i + R + dy holds dy
+          auto m = [&](int L, int dy) { return Mw[i + R + dy][L]; };
+          if constexpr (BALL && R == 3) {
+            // line lengths of the r = 3 ball: dz = 1 takes M_2 on dy -2..2;
+            // dz = 2 M_2 on -1..1 and M_1 at +-2; dz = 0 M_3 at 0, M_2 on
+            // +-1, +-2 and M_0 at +-3 (M_2 at 0 is no smaller than M_3); dz = 3
+            // M_0 at 0. The three-row minimum of M_2 is shared.
+            const uint32_t a = O::f3(m(2, -1), m(2, 0), m(2, 1));
+            const uint32_t d1 = O::f3(a, m(2, -2), m(2, 2));
+            D[1][i] = d1;
+            D[0][i] = O::f3(d1, m(3, 0), O::f2(m(0, -3), m(0, 3)));
+            D[2][i] = O::f3(a, m(1, -2), m(1, 2));
+            D[3][i] = m(0, 0);
+          } else {
 #pragma unroll
-          for (int dz = 0; dz < NDZ; ++dz) {
-            uint32_t d = O::id;
+            for (int dz = 0; dz < NDZ; ++dz) {
+              // extreme of the disk's lines, three operands per instruction
+              uint32_t d = O::id, pend = 0u;
+              int cnt = 0;
 #pragma unroll
-            for (int dy = -R; dy <= R; ++dy) {
-              const int L = BALL ? line_len(R, dz, dy) : R;
-              if (L >= 0) d = O::f2(d, Mw[i + R + dy][L]);
+              for (int dy = -R; dy <= R; ++dy) {
+                const int L = BALL ? line_len(R, dz, dy) : R;
+                if (L >= 0) {
+                  const uint32_t t = m(L, dy);
+                  if (cnt == 0)
+                    d = t;
+                  else if (cnt & 1)
+                    pend = t;
+                  else
+                    d = O::f3(d, pend, t);
+                  ++cnt;
+                }
+              }
+              if (cnt >= 2 && !(cnt & 1)) d = O::f2(d, pend);
+              D[dz][i] = d;
             }
-            D[dz][i] = d;
           }
         }
       }

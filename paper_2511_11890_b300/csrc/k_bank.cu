@@ -444,6 +444,7 @@ struct BankPlan {
   BankMaps maps;
   int smem = 0;
   int grid = 0;
+  int threads = 0;
   const void* kernel = nullptr;
   // second launch (small radii at two CTAs per SM), when split
   BankParams P2;
@@ -570,7 +571,7 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
       if (P.grp[g].r <= b2::kWideMaxR) s2 = std::max(s2, b2::geo(P.grp[g].r, 16, 16, es).SMEM);
     int per_sm2 = 0;
     if (s2 > 0 && cudaFuncSetAttribute(kfn2, cudaFuncAttributeMaxDynamicSharedMemorySize, s2) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kfn2, kThreads, s2) == cudaSuccess && per_sm2 >= 2) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kfn2, b2::kThreads2, s2) == cudaSuccess && per_sm2 >= 2) {
       split = true;
       plan->smem2 = s2;
       plan->grid2 = num_sms() * per_sm2;
@@ -647,12 +648,14 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   }
   plan->smem = smem;
   const void* kfn = v2 ? bank2_kernel(q.dtype, 1) : reinterpret_cast<const void*>(&k_bank);
+  const int nt1 = v2 ? b2::kThreads1 : kThreads;
   plan->kernel = kfn;
+  plan->threads = nt1;
   const int sms = num_sms();
   if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute(filter bank)");
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, nt1, smem);
   plan->grid = std::max(1, std::min(P.nitems, sms * std::max(1, per_sm)));
   // graph: reset the counters, then the persistent launch(es); two launches
   // are sibling nodes, so the second fills SMs as the first drains
@@ -673,7 +676,7 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
     void* args[2] = {&plan->P, &plan->maps};
     kp.func = const_cast<void*>(plan->kernel);
     kp.gridDim = dim3(plan->grid);
-    kp.blockDim = dim3(kThreads);
+    kp.blockDim = dim3(plan->threads);
     kp.sharedMemBytes = smem;
     kp.kernelParams = args;
     if ((e = cudaGraphAddKernelNode(&kern, plan->graph, &mset, 1, &kp)) != cudaSuccess)
@@ -685,7 +688,7 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
     void* args[2] = {&plan->P2, &plan->maps};
     kp.func = const_cast<void*>(plan->kernel2);
     kp.gridDim = dim3(plan->grid2);
-    kp.blockDim = dim3(kThreads);
+    kp.blockDim = dim3(b2::kThreads2);
     kp.sharedMemBytes = plan->smem2;
     kp.kernelParams = args;
     if ((e = cudaGraphAddKernelNode(&kern, plan->graph, &mset, 1, &kp)) != cudaSuccess)

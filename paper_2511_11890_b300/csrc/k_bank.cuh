@@ -85,7 +85,11 @@ namespace b2 {
 
 constexpr int kKP = 4;       // planes per phase (one TMA group)
 constexpr int kNSG = 2;      // TMA groups in flight
-constexpr int kThreads = 256;
+// Threads per CTA of the one-CTA-per-SM kernel (MINB = 1) and of the
+// two-CTAs-per-SM kernel (MINB = 2).
+constexpr int kThreads1 = 256;
+constexpr int kThreads2 = 256;
+__host__ __device__ constexpr int threads_of(int minb) { return minb == 2 ? kThreads2 : kThreads1; }
 
 __host__ __device__ constexpr int rup(int a, int b) { return (a + b - 1) / b * b; }
 __host__ __device__ constexpr int gcdi(int a, int b) { return b == 0 ? a : gcdi(b, a % b); }
@@ -217,7 +221,7 @@ __device__ __forceinline__ void x_task(const unsigned char* plane, int srow, int
 }
 
 // One item: z-march over a TX x TY tile column for one sigma group.
-template <int R, int TX, int TY, typename TIN>
+template <int R, int TX, int TY, typename TIN, int NT>
 __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankItem& it,
                           unsigned char* smem, int& gbase, int* s_abort) {
   constexpr Geo g = geo(R, TX, TY, sizeof(TIN));
@@ -243,11 +247,11 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
   // than R in x and y); rows and columns that feed only outputs beyond the
   // volume (a ragged last tile, reflected twice) are clamped into the box so
   // that every shared-memory read stays in bounds.
-  for (int row = tid; row < g.BH; row += kThreads) {
+  for (int row = tid; row < g.BH; row += NT) {
     const int64_t sr = reflect(cy0 - R + row, Gy) - (cy0 - R);
     srow[row] = (int)(sr < 0 ? 0 : (sr >= g.BH ? g.BH - 1 : sr));
   }
-  for (int c = tid; c < TX + 2 * R; c += kThreads) {
+  for (int c = tid; c < TX + 2 * R; c += NT) {
     const int64_t sc = reflect(cx0 - R + c, Gx) - (cx0 - g.RA);
     scol[c] = (int)(sc < 0 ? 0 : (sc >= g.BW ? g.BW - 1 : sc));
   }
@@ -287,7 +291,7 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
       if (!mbar_wait(&bars[b], (G / kNSG) & 1)) atomicOr(s_abort, 1);
       const unsigned char* sb = stg + b * g.GB;
       constexpr int NXT = kKP * (TX / 8) * g.BH;
-      for (int t = tid; t < NXT; t += kThreads) {
+      for (int t = tid; t < NXT; t += NT) {
         const int row = t % g.BH;
         const int rest = t / g.BH;
         const int seg = rest % (TX / 8), pl = rest / (TX / 8);
@@ -300,7 +304,7 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
     const int done = min(kKP * gi, total);
     while (zb < nout && done >= min(zb + kKP + 2 * R, total)) {
       const int s0 = zb % g.NR;
-      for (int pos = tid; pos < g.PL; pos += kThreads) {
+      for (int pos = tid; pos < g.PL; pos += NT) {
         float aG[kKP], aDz[kKP], aDzz[kKP], aDx[kKP], aDy[kKP], aL[kKP];
 #pragma unroll
         for (int j = 0; j < kKP; ++j) aG[j] = aDz[j] = aDzz[j] = aDx[j] = aDy[j] = aL[j] = 0.0f;
@@ -356,7 +360,7 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
       // y pass: four rows of one column of one plane per task
       constexpr int NYT = kKP * TX * (TY / 4);
       constexpr int OS = kKP * g.BH * g.XS;  // floats between x-pass orders
-      for (int t = tid; t < NYT; t += kThreads) {
+      for (int t = tid; t < NYT; t += NT) {
         const int x = t % TX;
         const int rest = t / TX;
         const int ys = rest % (TY / 4), pl = rest / (TY / 4);
@@ -424,26 +428,26 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
   gbase += ngr;
 }
 
-template <int TX, int TY, typename TIN>
+template <int TX, int TY, typename TIN, int NT>
 __device__ __forceinline__ void dispatch2(int r, const BankParams& P, const BankMaps& maps,
                                           const BankItem& it, unsigned char* smem, int& gb,
                                           int* s_abort) {
   switch (r) {
 #define HP_B2(RR) \
-  case RR: run_item2<RR, TX, TY, TIN>(P, maps, it, smem, gb, s_abort); break;
+  case RR: run_item2<RR, TX, TY, TIN, NT>(P, maps, it, smem, gb, s_abort); break;
     HP_B2(1) HP_B2(2) HP_B2(3) HP_B2(4) HP_B2(5) HP_B2(6)
     HP_B2(7) HP_B2(8) HP_B2(9) HP_B2(10) HP_B2(11) HP_B2(12)
 #undef HP_B2
   }
 }
 
-template <typename TIN>
+template <typename TIN, int NT>
 __device__ __forceinline__ void dispatch2_wide(int r, const BankParams& P, const BankMaps& maps,
                                                const BankItem& it, unsigned char* smem, int& gb,
                                                int* s_abort) {
   switch (r) {
 #define HP_B2(RR) \
-  case RR: run_item2<RR, 32, 16, TIN>(P, maps, it, smem, gb, s_abort); break;
+  case RR: run_item2<RR, 32, 16, TIN, NT>(P, maps, it, smem, gb, s_abort); break;
     HP_B2(1) HP_B2(2) HP_B2(3) HP_B2(4) HP_B2(5) HP_B2(6)
 #undef HP_B2
   }
@@ -458,7 +462,7 @@ constexpr int kWideMaxR = 6;
 // shared memory for 16-bit inputs), two CTAs per SM and at most 128
 // registers per thread.
 template <typename TIN, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB)
+__global__ void __launch_bounds__(threads_of(MINB), MINB)
     k_bank2(const __grid_constant__ BankParams P, const __grid_constant__ BankMaps maps) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_item;
@@ -479,13 +483,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
     const int r = P.grp[it.group].r;
     if constexpr (MINB == 1) {
       if (it.cfg == 1)
-        dispatch2_wide<TIN>(r, P, maps, it, smem, gbase, &s_abort);
+        dispatch2_wide<TIN, kThreads1>(r, P, maps, it, smem, gbase, &s_abort);
       else
-        dispatch2<16, 16, TIN>(r, P, maps, it, smem, gbase, &s_abort);
+        dispatch2<16, 16, TIN, kThreads1>(r, P, maps, it, smem, gbase, &s_abort);
     } else {
       switch (r) {
 #define HP_B2(RR) \
-  case RR: run_item2<RR, 16, 16, TIN>(P, maps, it, smem, gbase, &s_abort); break;
+  case RR: run_item2<RR, 16, 16, TIN, kThreads2>(P, maps, it, smem, gbase, &s_abort); break;
         HP_B2(1) HP_B2(2) HP_B2(3) HP_B2(4) HP_B2(5) HP_B2(6)
 #undef HP_B2
       }

@@ -13,7 +13,7 @@
 //          of use, from a per-thread list of (cell, source) offsets;
 //   P1     x pass on row pairs read straight from the raw stage (element ->
 //          FP32 inline), packed f32x2 FMAs over the row pair, into X;
-//   P2     y pass on x pairs (packed f32x2 over the two columns), NY = 16 rows
+//   P2     y pass on x pairs (packed f32x2 over the two columns), NY (8 or 16) rows
 //          per item, into the z feed buffer Zb;
 //   Z      each thread owns ZP x pairs of one row and keeps 2R+1 partial
 //          outputs per pair in registers: input plane q adds tap i to the
@@ -71,14 +71,17 @@ inline uint32_t f32_bits(float f) {
 // Tile and thread shape per radius: wide, short tiles for small radii (the x
 // pass repeats 2R halo rows; two CTAs of 256 threads per SM, two x pairs of
 // z state per thread), square tiles for larger ones (one CTA of 512 threads
-// per SM, one x pair per thread).
+// per SM, one x pair per thread). NY rows per y-pass item: 8 spreads the y
+// pass over twice the threads (measured at 1024^3: r = 3 and r = 12 3 %
+// faster than 16-row items, r = 6 1 % slower; 4-row items slower at all
+// three); the per-output sums are the same either way.
 template <int R>
 struct ZrShape {
   static constexpr int TX = R <= 6 ? 64 : 32;
   static constexpr int TY = R <= 6 ? 16 : 32;
   static constexpr int ZP = R <= 6 ? 2 : 1;
   static constexpr int NT = TX * TY / (2 * ZP);
-  static constexpr int NY = 16;
+  static constexpr int NY = (R <= 3 || R >= 7) ? 8 : 16;
   static constexpr int MINB = NT >= 512 ? 1 : 2;
 };
 

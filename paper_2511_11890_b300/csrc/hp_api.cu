@@ -170,6 +170,20 @@ int max_dyn_smem() {
   return cached[dev];
 }
 
+int max_smem_per_sm() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 228 * 1024;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || n <= 0)
+      n = 228 * 1024;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 int64_t pick_zchunk(int64_t cz, int64_t tiles, int64_t slots, int halo, int align) {
   if (cz <= 0) return align;
   slots = std::max<int64_t>(1, slots);

@@ -101,6 +101,9 @@ int num_sms();
 // less 1 KB for the kernels' static shared variables.
 int max_dyn_smem();
 
+// Shared memory of one SM on the current device (all resident CTAs).
+int max_smem_per_sm();
+
 // z-chunk length for a z-march grid of `tiles` columns: CTAs run in waves
 // of `slots` (resident CTAs on the whole GPU) and each costs about its
 // planes plus `halo`; returns the multiple of `align` that minimises

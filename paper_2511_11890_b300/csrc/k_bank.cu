@@ -561,14 +561,22 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
     if (v2) return (r <= b2::kWideMaxR && b2::geo(r, 32, 16, es).SMEM <= max_dyn_smem()) ? 1 : 0;
     return r <= 4 ? 1 : 0;
   };
-  // split: radii <= kWideMaxR to the two-CTAs-per-SM launch when two of its
-  // CTAs fit an SM
+  // split: the radii <= kWideMaxR whose 16 x 16 tiles fit two CTAs per SM
+  // go to the two-CTAs-per-SM launch
   const void* kfn2 = v2 ? bank2_kernel(q.dtype, 2) : nullptr;
   bool split = false;
+  bool second_of[kMaxGroups] = {false};
   if (v2 && t.small_cfg == 2) {
+    const int sm_smem = max_smem_per_sm();
     int s2 = 0;
-    for (int g = 0; g < P.ngroups; ++g)
-      if (P.grp[g].r <= b2::kWideMaxR) s2 = std::max(s2, b2::geo(P.grp[g].r, 16, 16, es).SMEM);
+    for (int g = 0; g < P.ngroups; ++g) {
+      const int r = P.grp[g].r;
+      const int need = b2::geo(r, 16, 16, es).SMEM;
+      if (r <= b2::kWideMaxR && 2 * (need + 1024) <= sm_smem) {
+        second_of[g] = true;
+        s2 = std::max(s2, need);
+      }
+    }
     int per_sm2 = 0;
     if (s2 > 0 && cudaFuncSetAttribute(kfn2, cudaFuncAttributeMaxDynamicSharedMemorySize, s2) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, kfn2, b2::kThreads2, s2) == cudaSuccess && per_sm2 >= 2) {
@@ -585,7 +593,7 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
     const int r = P.grp[g].r;
     const int cfg = cfg_of(r);
     const int TX = cfg == 1 ? 32 : 16, TY = 16;
-    const bool second = split && r <= b2::kWideMaxR;
+    const bool second = split && second_of[g];
     if (!second) smem = std::max(smem, v2 ? b2::geo(r, TX, TY, es).SMEM : cfg_smem(cfg, r, es));
     std::vector<BankItem>& list = second ? items2 : items;
     for (auto& b : q.bricks)
@@ -721,9 +729,15 @@ static int tune(const BankRequest& q, cudaStream_t s, BankTune* best) {
       return HP_OK;
     }
   }
+  // HP_BANK_TUNE=0 skips tuning (32 x 16 tiles where they fit, z chunks of
+  // 256); HP_BANK_TUNE=<cfg>,<zchunk> pins one candidate (cfg 0, 1 or 2 as
+  // in BankTune, zchunk >= 4).
   const char* env = getenv("HP_BANK_TUNE");
   std::vector<BankTune> cands = {{1, 64}, {1, 128}, {1, 256}, {0, 256}, {2, 128}, {2, 256}};
   if (env && !strcmp(env, "0")) cands = {{1, 256}};
+  int pin_cfg = -1, pin_z = 0;
+  if (env && sscanf(env, "%d,%d", &pin_cfg, &pin_z) == 2 && pin_cfg >= 0 && pin_cfg <= 2 && pin_z >= 4)
+    cands = {{pin_cfg, pin_z}};
   float best_ms = 1e30f;
   BankTune bt = cands[0];
   cudaEvent_t a, b;

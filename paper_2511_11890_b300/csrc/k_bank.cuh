@@ -177,6 +177,18 @@ struct Taps3 {
   float w[3][2 * R + 1];
 };
 
+// Ring word of tile position (y, x). With 16-column tiles the two half warps
+// of a y-pass task write rows 4 apart, which fall on the same banks; flipping
+// the half-row of rows with bit 2 of y set puts them on opposite halves, and
+// keeps the z pass's reads of 32 consecutive positions conflict-free.
+template <int TX>
+__device__ __forceinline__ int ring_pos(int y, int x) {
+  if constexpr (TX == 16)
+    return (y * 16 + x) ^ (((y >> 2) & 1) << 4);
+  else
+    return y * TX + x;
+}
+
 // x pass of one task: 8 outputs of one row of one plane, all three orders.
 template <int R, int TX, int TY, typename TIN>
 __device__ __forceinline__ void x_task(const unsigned char* plane, int srow, int seg, bool face,
@@ -305,13 +317,14 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
     while (zb < nout && done >= min(zb + kKP + 2 * R, total)) {
       const int s0 = zb % g.NR;
       for (int pos = tid; pos < g.PL; pos += NT) {
+        const int rpos = ring_pos<TX>(pos / TX, pos % TX);
         float aG[kKP], aDz[kKP], aDzz[kKP], aDx[kKP], aDy[kKP], aL[kKP];
 #pragma unroll
         for (int j = 0; j < kKP; ++j) aG[j] = aDz[j] = aDzz[j] = aDx[j] = aDy[j] = aL[j] = 0.0f;
         int slot = s0;
 #pragma unroll
         for (int m = 0; m < kKP + 2 * R; ++m) {
-          const float* rp = ring + slot * g.PL + pos;
+          const float* rp = ring + slot * g.PL + rpos;
           const float y00 = rp[0];
           const float y10 = rp[1 * g.NR * g.PL];
           const float y01 = rp[2 * g.NR * g.PL];
@@ -410,13 +423,14 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
           }
         }
         const int slot = (kKP * gi + pl) % g.NR;
-        float* rp = ring + slot * g.PL + (4 * ys) * TX + x;
+        float* rp = ring + slot * g.PL;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          rp[i * TX] = a00[i];
-          rp[1 * g.NR * g.PL + i * TX] = a10[i];
-          rp[2 * g.NR * g.PL + i * TX] = a01[i];
-          rp[3 * g.NR * g.PL + i * TX] = al[i];
+          const int o = ring_pos<TX>(4 * ys + i, x);
+          rp[o] = a00[i];
+          rp[1 * g.NR * g.PL + o] = a10[i];
+          rp[2 * g.NR * g.PL + o] = a01[i];
+          rp[3 * g.NR * g.PL + o] = al[i];
         }
       }
     }

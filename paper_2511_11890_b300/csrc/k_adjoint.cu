@@ -80,6 +80,27 @@ __global__ void k_axis_adjoint(const float* __restrict__ src, float* __restrict_
   }
 }
 
+// adjoint_at for a compile-time radius on a line at least R long: the
+// pre-images of i are then i, -1 - i (when i < R) and 2n - 1 - i (when
+// i >= n - R), visited in adjoint_at's order with the same taps, so the sum
+// is the same bit for bit, without its 64-bit divisions.
+template <int R>
+__device__ __forceinline__ float adjoint_face(const float* line, int i, int n, int64_t stride,
+                                              const AxisTaps& taps) {
+  float acc = 0.0f;
+  auto add = [&](int j) {
+#pragma unroll
+    for (int k = -R; k <= R; ++k) {
+      const int s2 = j + k;
+      if (s2 >= 0 && s2 < n) acc = fmaf(taps.g[k + R], line[(int64_t)s2 * stride], acc);
+    }
+  };
+  add(i);
+  if (i <= R - 1) add(-1 - i);
+  if (i >= n - R) add(2 * n - 1 - i);
+  return acc;
+}
+
 // Same transpose, radius R known at compile time: each thread takes kAC
 // consecutive outputs of one line. Away from the faces (R <= i < n - R) the
 // only pre-image of i is i itself and t[i] needs no zero extension, so the
@@ -110,6 +131,8 @@ __global__ void __launch_bounds__(kBlock)
       acc = 0.0f;
 #pragma unroll
       for (int k = -R; k <= R; ++k) acc = fmaf(taps.g[k + R], line[x + k], acc);
+    } else if (n >= R) {
+      acc = adjoint_face<R>(line, x, n, 1, taps);
     } else {
       acc = adjoint_at(line, x, n, 1, taps, R);
     }
@@ -139,11 +162,88 @@ __global__ void __launch_bounds__(kBlock)
   } else {
     const int i1 = min(i0 + kAC, n);
     for (int i = i0; i < i1; ++i) {
-      const float acc = adjoint_at(line, i, n, stride, taps, R);
+      const float acc = n >= R ? adjoint_face<R>(line, i, n, stride, taps)
+                               : adjoint_at(line, i, n, stride, taps, R);
       float* d = dl + (int64_t)i * stride;
       *d = accumulate ? *d + acc : acc;
     }
   }
+}
+
+// x-axis transpose in two kinds of thread: interior threads take kXW
+// consecutive outputs whose window of kXW + 2 R4 inputs (R4 = R rounded up to
+// 4) lies inside the row and is read as aligned float4 words (rows of a
+// multiple of 4 floats, 16-byte aligned buffers); face threads take one
+// output each of the chunks whose window would leave the row. The two kinds
+// occupy separate ranges of the grid, so no warp mixes them. Every output
+// sums its taps in the same order as k_axis_adjoint_r.
+constexpr int kXW = 16;
+
+template <int R>
+__global__ void __launch_bounds__(kBlock)
+    k_axis_adjoint_x(const float* __restrict__ src, float* __restrict__ dst, int64_t rows, int n,
+                     int c_lo, int c_hi, const AxisTaps taps, int accumulate) {
+  constexpr int R4 = (R + 3) / 4 * 4;
+  const int nin = c_hi - c_lo;             // interior chunks per row
+  const int nface = n - kXW * nin;         // face outputs per row
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ninner = rows * nin;
+  if (gt < ninner) {
+    const int64_t row = gt / nin;
+    const int x0 = (c_lo + (int)(gt - row * nin)) * kXW;
+    const float* line = src + row * n;
+    float* dl = dst + row * n;
+    float w[kXW + 2 * R4];
+    const float4* v = reinterpret_cast<const float4*>(line + x0 - R4);
+#pragma unroll
+    for (int q = 0; q < (kXW + 2 * R4) / 4; ++q) {
+      const float4 f = v[q];
+      w[4 * q] = f.x;
+      w[4 * q + 1] = f.y;
+      w[4 * q + 2] = f.z;
+      w[4 * q + 3] = f.w;
+    }
+    float o[kXW];
+#pragma unroll
+    for (int i = 0; i < kXW; ++i) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = -R; k <= R; ++k) acc = fmaf(taps.g[k + R], w[R4 + i + k], acc);
+      o[i] = acc;
+    }
+    float4* d = reinterpret_cast<float4*>(dl + x0);
+#pragma unroll
+    for (int q = 0; q < kXW / 4; ++q) {
+      float4 r = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      if (accumulate) {
+        const float4 p = d[q];
+        r.x = p.x + r.x;
+        r.y = p.y + r.y;
+        r.z = p.z + r.z;
+        r.w = p.w + r.w;
+      }
+      d[q] = r;
+    }
+    return;
+  }
+  const int64_t f = gt - ninner;
+  const int64_t row = f / nface;
+  if (row >= rows) return;
+  const int k = (int)(f - row * nface);
+  const int x = k < c_lo * kXW ? k : c_hi * kXW + (k - c_lo * kXW);
+  const float* line = src + row * n;
+  float acc;
+  if (x >= R && x < n - R) {
+    acc = 0.0f;
+#pragma unroll
+    for (int kk = -R; kk <= R; ++kk) acc = fmaf(taps.g[kk + R], line[x + kk], acc);
+  } else if (n >= R) {
+    acc = adjoint_face<R>(line, x, n, 1, taps);
+  } else {
+    acc = adjoint_at(line, x, n, 1, taps, R);
+  }
+  float* d = dst + row * n + x;
+  *d = accumulate ? *d + acc : acc;
 }
 
 template <int R>
@@ -152,7 +252,16 @@ cudaError_t launch_axis_r(const float* src, float* dst, const int64_t dims[3], i
   const int n0 = (int)dims[0], n1 = (int)dims[1], n2 = (int)dims[2];
   const int n = ax == 0 ? n0 : (ax == 1 ? n1 : n2);
   const int nch = (n + kAC - 1) / kAC;
-  if (ax == 2) {
+  if (ax == 2 && n2 % 4 == 0 && (uintptr_t)src % 16 == 0 && (uintptr_t)dst % 16 == 0) {
+    // interior chunks c: window [16c - R4, 16c + 16 + R4) inside [0, n2)
+    constexpr int R4 = (R + 3) / 4 * 4;
+    const int c_lo = (R4 + kXW - 1) / kXW;
+    const int c_hi = std::max(c_lo, (n2 - kXW - R4) / kXW + 1);
+    const int64_t rows = (int64_t)n0 * n1;
+    const int64_t threads = rows * (c_hi - c_lo) + rows * (n2 - kXW * (c_hi - c_lo));
+    const unsigned grid = (unsigned)((threads + kBlock - 1) / kBlock);
+    k_axis_adjoint_x<R><<<grid, kBlock, 0, s>>>(src, dst, rows, n2, c_lo, c_hi, a, accumulate);
+  } else if (ax == 2) {
     const dim3 grid((unsigned)((n2 + kBlock - 1) / kBlock), (unsigned)n1, (unsigned)n0);
     k_axis_adjoint_r<R, 2><<<grid, kBlock, 0, s>>>(src, dst, n0, n1, n2, a, accumulate);
   } else {

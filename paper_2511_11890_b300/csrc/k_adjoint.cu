@@ -159,6 +159,41 @@ __global__ void __launch_bounds__(kBlock)
       float* d = dl + (int64_t)(i0 + i) * stride;
       *d = accumulate ? *d + acc : acc;
     }
+  } else if (n % kAC == 0 && n >= kAC + R && (i0 == 0 || i0 == n - kAC)) {
+    // first or last chunk of a line of whole chunks: a register window of
+    // kAC + R inputs holds every term of adjoint_face (pre-images i and
+    // -1 - i at the low face, i and 2n - 1 - i at the high one), taken in
+    // its order
+    const bool low = i0 == 0;
+    const int b = low ? 0 : i0 - R;  // line element of w[0]
+    float w[kAC + R];
+#pragma unroll
+    for (int j = 0; j < kAC + R; ++j) w[j] = line[(int64_t)(b + j) * stride];
+#pragma unroll
+    for (int ii = 0; ii < kAC; ++ii) {
+      float acc = 0.0f;
+      if (low) {
+#pragma unroll
+        for (int k = -R; k <= R; ++k)
+          if (ii + k >= 0) acc = fmaf(taps.g[k + R], w[ii + k], acc);
+        if (ii <= R - 1) {
+#pragma unroll
+          for (int k = -R; k <= R; ++k)
+            if (-1 - ii + k >= 0) acc = fmaf(taps.g[k + R], w[-1 - ii + k], acc);
+        }
+      } else {
+#pragma unroll
+        for (int k = -R; k <= R; ++k)
+          if (ii + k < kAC) acc = fmaf(taps.g[k + R], w[ii + k + R], acc);
+        if (ii >= kAC - R) {
+#pragma unroll
+          for (int k = -R; k <= R; ++k)
+            if (k < ii - (kAC - 1)) acc = fmaf(taps.g[k + R], w[2 * kAC - 1 - ii + k + R], acc);
+        }
+      }
+      float* d = dl + (int64_t)(i0 + ii) * stride;
+      *d = accumulate ? *d + acc : acc;
+    }
   } else {
     const int i1 = min(i0 + kAC, n);
     for (int i = i0; i < i1; ++i) {

@@ -485,18 +485,31 @@ __global__ void k_morph_gather(const int32_t* __restrict__ arg, const float* __r
 
 // The same gather with the reach of a 4 x 8 x 32 tile of sources staged in
 // shared memory (arg and gout of every p within rad of the tile; -1 outside
-// the volume): each q scans its cube of p in increasing linear order, as
+// the volume; rows padded to a multiple of 4 words). A thread takes four
+// consecutive x outputs q: for each (dz, dy) it reads the 4 + 2 rad source
+// indices of the row as aligned 16-byte words and adds gout[p] only where
+// arg[p] == q, scanning each q's cube of p in increasing linear order as
 // k_morph_gather does.
 template <int RAD>
+struct GatherTile {
+  static constexpr int VZ = kCZ + 2 * RAD, VY = kCY + 2 * RAD;
+  static constexpr int VX = (kCX + 2 * RAD + 3) / 4 * 4;  // padded row (words)
+  static constexpr int NWIN = (4 + 2 * RAD + 3) / 4;       // 16-byte words per window
+  static constexpr int SMEM = 8 * VZ * VY * VX;
+  static_assert(kCZ * kCY * (kCX / 4) == kBlock, "one output quad per thread");
+};
+
+template <int RAD>
 constexpr int gather_smem() {
-  return 8 * (kCZ + 2 * RAD) * (kCY + 2 * RAD) * (kCX + 2 * RAD);
+  return GatherTile<RAD>::SMEM;
 }
 
 template <int RAD>
 __global__ void __launch_bounds__(kBlock)
     k_morph_gather_tile(const int32_t* __restrict__ arg, const float* __restrict__ gout,
                         float* __restrict__ gin, int n0, int n1, int n2, int accumulate) {
-  constexpr int VZ = kCZ + 2 * RAD, VY = kCY + 2 * RAD, VX = kCX + 2 * RAD;
+  using GT = GatherTile<RAD>;
+  constexpr int VZ = GT::VZ, VY = GT::VY, VX = GT::VX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto sa = reinterpret_cast<int32_t(*)[VY][VX]>(smem_raw);
   auto sg = reinterpret_cast<float(*)[VY][VX]>(smem_raw + 4 * VZ * VY * VX);
@@ -505,27 +518,42 @@ __global__ void __launch_bounds__(kBlock)
   for (int e = tid; e < VZ * VY * VX; e += kBlock) {
     const int c = e % VX, b = (e / VX) % VY, a = e / (VX * VY);
     const int z = z0 - RAD + a, y = y0 - RAD + b, x = x0 - RAD + c;
-    const bool in = z >= 0 && z < n0 && y >= 0 && y < n1 && x >= 0 && x < n2;
+    const bool in = c < kCX + 2 * RAD && z >= 0 && z < n0 && y >= 0 && y < n1 && x >= 0 && x < n2;
     const int64_t p = ((int64_t)z * n1 + y) * n2 + x;
     sa[a][b][c] = in ? arg[p] : -1;
     sg[a][b][c] = in ? gout[p] : 0.0f;
   }
   __syncthreads();
-  for (int e = tid; e < kCZ * kCY * kCX; e += kBlock) {
-    const int x = e % kCX, y = (e / kCX) % kCY, z = e / (kCX * kCY);
-    const int gz = z0 + z, gy = y0 + y, gx = x0 + x;
-    if (gz >= n0 || gy >= n1 || gx >= n2) continue;
-    const int32_t q = (int32_t)(((int64_t)gz * n1 + gy) * n2 + gx);
-    float acc = 0.0f;
+  const int xq = (tid % (kCX / 4)) * 4, y = (tid / (kCX / 4)) % kCY, z = tid / (kCX / 4 * kCY);
+  const int gz = z0 + z, gy = y0 + y;
+  if (gz >= n0 || gy >= n1) return;
+  const int64_t q0 = ((int64_t)gz * n1 + gy) * n2 + x0 + xq;  // q of output j: q0 + j
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int dz = 0; dz <= 2 * RAD; ++dz)
+  for (int dz = 0; dz <= 2 * RAD; ++dz)
 #pragma unroll
-      for (int dy = 0; dy <= 2 * RAD; ++dy)
+    for (int dy = 0; dy <= 2 * RAD; ++dy) {
+      int32_t w[4 * GT::NWIN];
+      const int4* src = reinterpret_cast<const int4*>(&sa[z + dz][y + dy][xq]);
+#pragma unroll
+      for (int v = 0; v < GT::NWIN; ++v) {
+        const int4 t = src[v];
+        w[4 * v] = t.x;
+        w[4 * v + 1] = t.y;
+        w[4 * v + 2] = t.z;
+        w[4 * v + 3] = t.w;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int dx = 0; dx <= 2 * RAD; ++dx)
-          if (sa[z + dz][y + dy][x + dx] == q) acc += sg[z + dz][y + dy][x + dx];
-    float* d = gin + q;
-    *d = accumulate ? *d + acc : acc;
+          if (w[j + dx] == (int32_t)(q0 + j)) acc[j] += sg[z + dz][y + dy][xq + j + dx];
+    }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (x0 + xq + j >= n2) break;
+    float* d = gin + q0 + j;
+    *d = accumulate ? *d + acc[j] : acc[j];
   }
 }
 

@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(kBlock)
     v0[a][b][c] = load_as_f32(in, dt, ((int64_t)sz[a] * n1 + sy[b]) * n2 + sx[c]);
   }
   __syncthreads();
-  auto better = [&](float v, int64_t q, float best, int64_t bq) {
+  // linear indices fit in int32 (the index array is int32)
+  auto better = [&](float v, int32_t q, float best, int32_t bq) {
     return (is_dilate ? v > best : v < best) || (v == best && q < bq);
   };
   // x pass over every staged row; window offset sg*dx from the output column
@@ -429,37 +430,38 @@ __global__ void __launch_bounds__(kBlock)
   for (int e = tid; e < VZ * kCY * kCX; e += kBlock) {
     const int x = e % kCX, y = (e / kCX) % kCY, a = e / (kCX * kCY);
     float best = 0.0f;
-    int64_t bq = -1;
+    int32_t bq = -1;
 #pragma unroll
     for (int d = -RAD; d <= RAD; ++d) {
       const int b = y + RAD + sg * d;
       const float v = v1[a][b][x];
-      const int64_t q = (int64_t)sy[b] * n2 + i1[a][b][x];
+      const int32_t q = sy[b] * n2 + i1[a][b][x];
       if (bq < 0 || better(v, q, best, bq)) {
         best = v;
         bq = q;
       }
     }
     v2[a][y][x] = best;
-    i2[a][y][x] = (int32_t)bq;
+    i2[a][y][x] = bq;
   }
   __syncthreads();
   for (int e = tid; e < kCZ * kCY * kCX; e += kBlock) {
     const int x = e % kCX, y = (e / kCX) % kCY, z = e / (kCX * kCY);
     if (z0 + z >= n0 || y0 + y >= n1 || x0 + x >= n2) continue;
     float best = 0.0f;
-    int64_t bq = -1;
+    int32_t bq = -1;
+    const int32_t plane = n1 * n2;
 #pragma unroll
     for (int d = -RAD; d <= RAD; ++d) {
       const int a = z + RAD + sg * d;
-      const int64_t q = (int64_t)sz[a] * n1 * n2 + i2[a][y][x];
+      const int32_t q = sz[a] * plane + i2[a][y][x];
       const float v = v2[a][y][x];
       if (bq < 0 || better(v, q, best, bq)) {
         best = v;
         bq = q;
       }
     }
-    arg[((int64_t)(z0 + z) * n1 + (y0 + y)) * n2 + (x0 + x)] = (int32_t)bq;
+    arg[((int64_t)(z0 + z) * n1 + (y0 + y)) * n2 + (x0 + x)] = bq;
   }
 }
 

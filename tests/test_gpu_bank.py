@@ -107,9 +107,10 @@ def test_bank_every_radius(r):
 @pytest.mark.parametrize("dtype", [np.float16, np.uint16, np.float32])
 def test_bank_thin_z_and_partial_groups(dtype):
     """Volumes thinner in z than the radius (reflection bounces more than
-    once; every plane group is loaded plane by plane) and z extents that end
-    in a partial group of four planes."""
-    for shape in [(5, 40, 64), (7, 24, 32), (30, 20, 48)]:
+    once; every plane group is loaded plane by plane), z extents that end in
+    a partial group of four planes, and x/y extents just above the radius
+    (13 rows at r = 12: rows of the tile beyond the volume reflect twice)."""
+    for shape in [(5, 40, 64), (7, 24, 32), (30, 20, 48), (3, 13, 16), (4, 16, 32)]:
         f = synth.porous_f16(shape, 7) if dtype == np.float16 else rand_volume(dtype, shape, 8)
         filt = [(k, s) for s in (1.0, 4.0) for k in (hp.G, hp.GM, hp.LOG)]
         outs = hp.filterbank3d(to_dev(f), filt, out_dtype=hp.HP_F32)

@@ -16,7 +16,8 @@ FP64 C) on bounded sub-boxes of the same workload.
 Other measured configurations, one JSON line each (not the benchmark step):
 `--workload ooc2048` (2048^3 uint16 out-of-core under an 8e9-byte budget,
 host-link efficiency), `spheres128` (128^3 float32 Gaussian -> threshold ->
-cube morphology), `bank512` (512^3 float16 12-filter bank over 37 bricks,
+cube morphology), `open1024` (1024^3 uint16 opening, closing and top-hat),
+`bank512` (512^3 float16 12-filter bank over 37 bricks,
 FMA roofline), `autograd256` (256^3 float32 forward + backward).
 """
 from __future__ import annotations
@@ -462,6 +463,40 @@ def _timed(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps, clk.summary()
 
 
+def run_open1024(args):
+    """1024^3 uint16 porous volume: opening, closing and white top-hat with
+    the r = 3 ball (compositions of the erosion and dilation kernels through
+    a scratch volume)."""
+    import torch
+
+    import paper_2511_11890_b300 as hp
+    import synth
+    n = N
+    f, _ = synth.porous(n, SEED)
+    x = torch.from_numpy(f).cuda()
+    o = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    hbm_gbs, _, peak_kind = _peaks()
+    nvox = n ** 3
+    res, clks = {}, {}
+    # algorithmic bytes per voxel: two passes of 2 B in + 2 B out; the
+    # top-hat adds its difference (2 B in, 2 B opening in, 2 B out)
+    for name, fn, bpv in (("open", hp.open3d, 8), ("close", hp.close3d, 8), ("tophat", hp.tophat3d, 14)):
+        ms, clk = _timed(lambda fn=fn: fn(x, "ball", BALL_R, out=o), args.steps, max(3, args.warmup), stream)
+        gbs = nvox * bpv / (ms / 1e3) / 1e9
+        res[name] = {"ms": ms, "GB/s": gbs, "hbm_frac": gbs / hbm_gbs}
+        clks[name] = clk
+    hp.stream_status(stream)
+    line = {"metric": "voxels/s, 1024^3 uint16 opening (ball r = 3)", "value": nvox / (res["open"]["ms"] / 1e3),
+            "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": res["open"]["ms"],
+            "higher_is_better": True, "dtype": "u16", "data": "synthetic porous tomogram (seeded)",
+            "config": {"workload": "porous 1024^3 u16: opening, closing, white top-hat, ball r = 3"},
+            "ops": res, "hbm_peak_kind": peak_kind, "gpu_launches": 2 * args.steps,
+            "clocks": clks["open"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_spheres128(args):
     """128^3 float32 spheres: Gaussian sigma 2 -> threshold 0.5 to uint8 ->
     erosion and dilation with the 3^3 cube (the unchunked pipeline)."""
@@ -593,7 +628,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="porous1024",
-                    choices=["porous1024", "ooc2048", "spheres128", "bank512", "autograd256"])
+                    choices=["porous1024", "ooc2048", "spheres128", "bank512", "autograd256",
+                             "open1024"])
     ap.add_argument("--size", type=int, default=N,
                     help="edge of the in-HBM volume (1024 is the benchmark; smaller sizes "
                          "are for profiling captures)")
@@ -606,6 +642,8 @@ def main():
         return run_bank512(args)
     if args.workload == "autograd256":
         return run_autograd256(args)
+    if args.workload == "open1024":
+        return run_open1024(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_hp(args)

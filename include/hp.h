@@ -150,6 +150,19 @@ int hp_filterbank3d_bricks(const hp_volume* in, hp_volume* const* outs, const hp
 int hp_erode3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
 int hp_dilate3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
 
+/* Opening (erosion, then dilation), closing (dilation, then erosion) and
+ * white top-hat (in - opening) with the same structuring elements and
+ * reflect boundaries as hp_erode3d / hp_dilate3d (Sec. III-C, label-editing
+ * morphology: compositions of the two). Device volumes only (in and out on
+ * the device, out may not alias in); the intermediate volume is library
+ * scratch, allocated and freed on `stream`. Output dtype equals input dtype;
+ * results are exact (the top-hat difference is taken in FP32 and rounded to
+ * the dtype). HP_ERR_UNSUPPORTED for host volumes, HP_ERR_BUDGET when the
+ * scratch volume exceeds the memory budget. */
+int hp_open3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
+int hp_close3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
+int hp_tophat3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
+
 /* Global threshold (Sec. III-C, threshold algorithms): out (u8) = in > t,
  * compared in the input's own precision (t is rounded to it). */
 int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream);

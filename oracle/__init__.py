@@ -167,6 +167,26 @@ def dilate3d(f, se, rad, **kw):
     return morph3d(f, se, rad, True, **kw)
 
 
+def open3d(f, se, rad):
+    """Opening (Sec. III-C morphology): dilation of the erosion, each with
+    reflect boundaries over the whole volume."""
+    return dilate3d(erode3d(f, se, rad), se, rad)
+
+
+def close3d(f, se, rad):
+    """Closing: erosion of the dilation."""
+    return erode3d(dilate3d(f, se, rad), se, rad)
+
+
+def tophat3d(f, se, rad):
+    """White top-hat: f minus its opening, the difference taken in FP32 (FP64
+    for float64 input) and rounded to f's dtype: exact for integer dtypes,
+    where f >= opening, and numpy's own float16 arithmetic for float16."""
+    wt = np.float64 if f.dtype == np.float64 else np.float32
+    d = f.astype(wt) - open3d(f, se, rad).astype(wt)
+    return d.astype(f.dtype)
+
+
 def threshold(f: np.ndarray, t: float = 0.5) -> np.ndarray:
     f = np.ascontiguousarray(f)
     out = np.empty(f.shape, np.uint8)

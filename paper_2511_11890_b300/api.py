@@ -113,6 +113,29 @@ def dilate3d(x, se="ball", radius: int = 1, out=None, stream=None):
     return out
 
 
+def _compose(fn, x, se, radius, out, stream):
+    if out is None:
+        out = _empty_like(x, _dtype_code(x))
+    with _ctx(x), _View(x) as vi, _View(out) as vo:
+        check(fn(vi, vo, SE[se], int(radius), _stream(x, stream)))
+    return out
+
+
+def open3d(x, se="ball", radius: int = 1, out=None, stream=None):
+    """Opening (erosion, then dilation); device tensors only."""
+    return _compose(lib.hp_open3d, x, se, radius, out, stream)
+
+
+def close3d(x, se="ball", radius: int = 1, out=None, stream=None):
+    """Closing (dilation, then erosion); device tensors only."""
+    return _compose(lib.hp_close3d, x, se, radius, out, stream)
+
+
+def tophat3d(x, se="ball", radius: int = 1, out=None, stream=None):
+    """White top-hat, x - opening(x); device tensors only."""
+    return _compose(lib.hp_tophat3d, x, se, radius, out, stream)
+
+
 def threshold3d(x, t: float = 0.5, out=None, stream=None):
     if out is None:
         out = _empty_like(x, HP_U8)

@@ -281,6 +281,50 @@ int hp_morph3d_backward(const hp_volume* in, const hp_volume* gout, int is_dilat
   return HP_OK;
 }
 
+// Opening / closing / white top-hat on device volumes: two morphology
+// passes through a scratch volume (and, for the top-hat, in - opening).
+static int morph_compose(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream,
+                         int kind /* 0 open, 1 close, 2 white top-hat */) {
+  if (!in || !in->data || !out || !out->data) return set_error(HP_ERR_INVALID_ARG, "null argument");
+  if (in->loc != HP_DEVICE || out->loc != HP_DEVICE)
+    return set_error(HP_ERR_UNSUPPORTED, "opening / closing / top-hat run on device volumes only");
+  if (in->data == out->data) return set_error(HP_ERR_INVALID_ARG, "output may not alias the input");
+  if (out->dtype != in->dtype || out->nx != in->nx || out->ny != in->ny || out->nz != in->nz)
+    return set_error(HP_ERR_INVALID_ARG, "output must match the input's dtype and extents");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vb = dtype_size(in->dtype) * (size_t)(in->nx * in->ny * in->nz);
+  int st = check_scratch_budget(vb);
+  if (st != HP_OK) return st;
+  Scratch sc(s);
+  void* tmp = nullptr;
+  cudaError_t e = sc.alloc(&tmp, vb);
+  if (e != cudaSuccess) return cuda_fail(e, "opening / closing scratch");
+  hp_volume t = *in;
+  t.data = tmp;
+  const bool erode_first = kind != 1;
+  st = erode_first ? hp_erode3d(in, &t, se, radius, stream) : hp_dilate3d(in, &t, se, radius, stream);
+  if (st != HP_OK) return st;
+  st = erode_first ? hp_dilate3d(&t, out, se, radius, stream) : hp_erode3d(&t, out, se, radius, stream);
+  if (st != HP_OK) return st;
+  if (kind == 2) {
+    e = launch_difference(in->data, out->data, in->dtype, (int64_t)(in->nx * in->ny * in->nz), s);
+    if (e != cudaSuccess) return cuda_fail(e, "top-hat difference");
+  }
+  return HP_OK;
+}
+
+int hp_open3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream) {
+  return morph_compose(in, out, se, radius, stream, 0);
+}
+
+int hp_close3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream) {
+  return morph_compose(in, out, se, radius, stream, 1);
+}
+
+int hp_tophat3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream) {
+  return morph_compose(in, out, se, radius, stream, 2);
+}
+
 int hp_release_cache(void) {
   bank_release_cache();
   return HP_OK;

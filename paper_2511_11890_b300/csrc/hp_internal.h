@@ -97,6 +97,10 @@ bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t d
 
 int num_sms();
 
+// out[i] = in[i] - out[i] over n elements of dtype (FP32 difference rounded
+// to the dtype), on stream s.
+cudaError_t launch_difference(const void* in, void* out, int dtype, int64_t n, cudaStream_t s);
+
 // Largest dynamic shared memory a block may opt into on the current device,
 // less 1 KB for the kernels' static shared variables.
 int max_dyn_smem();

@@ -27,6 +27,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "hp_device.cuh"
 #include "hp_internal.h"
 
@@ -562,6 +564,32 @@ cudaError_t dispatch_r(int r, const MorphParams& P, const CUtensorMap& map, dim3
 }
 
 }  // namespace
+
+template <typename T>
+__global__ void k_difference(const T* __restrict__ in, T* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = to_f32<T>(in[i]) - to_f32<T>(out[i]);
+    if constexpr (std::is_same<T, __half>::value)
+      out[i] = __float2half_rn(d);
+    else if constexpr (std::is_same<T, float>::value)
+      out[i] = d;
+    else
+      out[i] = (T)d;  // integers: in >= opening, the difference is exact
+  }
+}
+
+cudaError_t launch_difference(const void* in, void* out, int dtype, int64_t n, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 32));
+  switch (dtype) {
+    case HP_U8: k_difference<uint8_t><<<grid, 256, 0, s>>>(static_cast<const uint8_t*>(in), static_cast<uint8_t*>(out), n); break;
+    case HP_U16: k_difference<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(in), static_cast<uint16_t*>(out), n); break;
+    case HP_F16: k_difference<__half><<<grid, 256, 0, s>>>(static_cast<const __half*>(in), static_cast<__half*>(out), n); break;
+    case HP_F32: k_difference<float><<<grid, 256, 0, s>>>(static_cast<const float*>(in), static_cast<float*>(out), n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s) {
   const int64_t cx = job.core_hi[2] - job.core_lo[2];

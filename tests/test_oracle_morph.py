@@ -180,3 +180,30 @@ def test_vjp_tie_rule_constant_volume():
     # ball of radius 2: smallest linear index source is (z - 2, y, x)
     _, arg = oracle.morph3d_vjp(f, oracle.SE_BALL, 2, True, w, return_arg=True)
     assert arg[4, 4, 4] == np.ravel_multi_index((2, 4, 4), shape)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.float32, np.float64])
+@pytest.mark.parametrize("se,rad", [(oracle.SE_CUBE, 1), (oracle.SE_BALL, 2)])
+def test_open_close_tophat_vs_scipy(dtype, se, rad):
+    """Opening, closing and white top-hat against scipy.ndimage's own
+    compositions (grey_opening, grey_closing, white_tophat, reflect mode)."""
+    f = _vol(dtype, (9, 11, 13), 2)
+    fp = np.ones((2 * rad + 1,) * 3, bool) if se == oracle.SE_CUBE else _ball(rad)
+    assert np.array_equal(oracle.open3d(f, se, rad), nd.grey_opening(f, footprint=fp, mode="reflect"))
+    assert np.array_equal(oracle.close3d(f, se, rad), nd.grey_closing(f, footprint=fp, mode="reflect"))
+    assert np.array_equal(oracle.tophat3d(f, se, rad), nd.white_tophat(f, footprint=fp, mode="reflect"))
+
+
+@pytest.mark.parametrize("se,rad", [(oracle.SE_CUBE, 2), (oracle.SE_BALL, 3)])
+def test_open_close_invariants(se, rad):
+    """Opening is anti-extensive and idempotent, closing extensive and
+    idempotent, the top-hat non-negative and zero on a constant volume."""
+    f = _vol(np.uint16, (10, 12, 14), 3)
+    o, c = oracle.open3d(f, se, rad), oracle.close3d(f, se, rad)
+    assert (o <= f).all() and (c >= f).all()
+    assert np.array_equal(oracle.open3d(o, se, rad), o)
+    assert np.array_equal(oracle.close3d(c, se, rad), c)
+    t = oracle.tophat3d(f, se, rad)
+    assert np.array_equal(t.astype(np.int64), f.astype(np.int64) - o.astype(np.int64))
+    k = np.full((6, 7, 8), 1234, np.uint16)
+    assert not oracle.tophat3d(k, se, rad).any()

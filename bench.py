@@ -17,6 +17,7 @@ Other measured configurations, one JSON line each (not the benchmark step):
 `--workload ooc2048` (2048^3 uint16 out-of-core under an 8e9-byte budget,
 host-link efficiency), `spheres128` (128^3 float32 Gaussian -> threshold ->
 cube morphology), `open1024` (1024^3 uint16 opening, closing and top-hat),
+`sweep` (out-of-core Gaussian on 1 to 16 GiB slabs under an 8e9-byte budget),
 `bank512` (512^3 float16 12-filter bank over 37 bricks,
 FMA roofline), `autograd256` (256^3 float32 forward + backward).
 """
@@ -444,6 +445,48 @@ def run_outofcore(args):
     return 0
 
 
+def run_sweep(args):
+    """Size sweep of the out-of-core Gaussian (sigma 3, f32 out) under an
+    8e9-byte budget: uint16 slabs of 2048 x 2048 x nz for nz = 128 .. 2048
+    (1 to 16 GiB of input), as in the paper's time-versus-size and
+    memory-versus-budget figures. Per size: time, bricks, peak library
+    device bytes during the call and library device bytes left after it."""
+    import torch
+
+    import paper_2511_11890_b300 as hp
+    import synth
+    n, budget = 2048, 8_000_000_000
+    f, _ = synth.porous(n, 2511118900 + 2)
+    xh = torch.from_numpy(f).pin_memory()
+    del f
+    og = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    hp.set_memory_budget(budget)
+    rows = []
+    for nz in (128, 256, 512, 1024, 2048):
+        x, o = xh[:nz], og[:nz]
+        hp.gaussian3d(x, 3.0, out=o)  # warm-up
+        times = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hp.gaussian3d(x, 3.0, out=o)
+            times.append(time.perf_counter() - t0)
+        st = hp.stats()
+        dt = min(times)
+        rows.append({"nz": nz, "input_GiB": nz * n * n * 2 / 2 ** 30, "s": dt,
+                     "voxels_per_s": nz * n * n / dt, "bricks": st["bricks"],
+                     "link_GBps": (st["h2d_bytes"] + st["d2h_bytes"]) / dt / 1e9,
+                     "peak_device_bytes": st["peak_device_bytes"],
+                     "live_device_bytes_after": st["live_device_bytes"]})
+    line = {"metric": "seconds per out-of-core Gaussian (sigma 3) vs input size, 8e9-byte budget",
+            "value": rows[-1]["s"], "unit": "s", "n_gpus": 1, "steps": args.steps,
+            "higher_is_better": False, "data": "synthetic porous tomogram (seeded)",
+            "config": {"workload": "porous u16 slabs 2048 x 2048 x nz, pinned host buffers, budget 8e9 B"},
+            "sizes": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _timed(fn, steps, warmup, stream):
     """CUDA-event time (ms per call) of fn() over `steps` calls after
     `warmup` untimed ones, with clocks sampled during the timed region."""
@@ -629,7 +672,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="porous1024",
                     choices=["porous1024", "ooc2048", "spheres128", "bank512", "autograd256",
-                             "open1024"])
+                             "open1024", "sweep"])
     ap.add_argument("--size", type=int, default=N,
                     help="edge of the in-HBM volume (1024 is the benchmark; smaller sizes "
                          "are for profiling captures)")
@@ -644,6 +687,8 @@ def main():
         return run_autograd256(args)
     if args.workload == "open1024":
         return run_open1024(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_hp(args)

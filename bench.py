@@ -16,7 +16,8 @@ FP64 C) on bounded sub-boxes of the same workload.
 Other measured configurations, one JSON line each (not the benchmark step):
 `--workload ooc2048` (2048^3 uint16 out-of-core under an 8e9-byte budget,
 host-link efficiency), `spheres128` (128^3 float32 Gaussian -> threshold ->
-cube morphology), `open1024` (1024^3 uint16 opening, closing and top-hat),
+cube morphology), `open1024` (1024^3 uint16 opening, closing, top-hat and
+unsharp mask),
 `sweep` (out-of-core Gaussian on 1 to 16 GiB slabs under an 8e9-byte budget),
 `bank512` (512^3 float16 12-filter bank over 37 bricks,
 FMA roofline), `autograd256` (256^3 float32 forward + backward).
@@ -509,7 +510,7 @@ def _timed(fn, steps, warmup, stream):
 def run_open1024(args):
     """1024^3 uint16 porous volume: opening, closing and white top-hat with
     the r = 3 ball (compositions of the erosion and dilation kernels through
-    a scratch volume)."""
+    a scratch volume), and the unsharp mask (sigma 2, amount 1)."""
     import torch
 
     import paper_2511_11890_b300 as hp
@@ -529,6 +530,12 @@ def run_open1024(args):
         gbs = nvox * bpv / (ms / 1e3) / 1e9
         res[name] = {"ms": ms, "GB/s": gbs, "hbm_frac": gbs / hbm_gbs}
         clks[name] = clk
+    # unsharp mask sigma 2, amount 1 (float32 out): the Gaussian (2 B in, 4 B
+    # out) and the epilogue (2 B in, 4 B in, 4 B out)
+    g = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    ms, _ = _timed(lambda: hp.unsharp3d(x, 2.0, 1.0, out=g), args.steps, max(3, args.warmup), stream)
+    res["unsharp_s2"] = {"ms": ms, "GB/s": nvox * 16 / (ms / 1e3) / 1e9,
+                         "hbm_frac": nvox * 16 / (ms / 1e3) / 1e9 / hbm_gbs}
     hp.stream_status(stream)
     line = {"metric": "voxels/s, 1024^3 uint16 opening (ball r = 3)", "value": nvox / (res["open"]["ms"] / 1e3),
             "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": res["open"]["ms"],

@@ -163,6 +163,14 @@ int hp_open3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* s
 int hp_close3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
 int hp_tophat3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream);
 
+/* Unsharp mask (Sec. III-C, Harpia filtering suite: edge enhancement on
+ * the Gaussian): out (f32) =
+ * in + amount * (in - G_sigma in), the Gaussian as hp_gaussian3d (truncate
+ * 3, reflect), the sum in FP32 as fma(amount, in - G, in). Device volumes
+ * only (in and out on the device, out f32 of the input's extents, no
+ * aliasing); HP_ERR_UNSUPPORTED for host volumes. */
+int hp_unsharp3d(const hp_volume* in, hp_volume* out, double sigma, double amount, void* stream);
+
 /* Global threshold (Sec. III-C, threshold algorithms): out (u8) = in > t,
  * compared in the input's own precision (t is rounded to it). */
 int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream);

@@ -187,6 +187,13 @@ def tophat3d(f, se, rad):
     return d.astype(f.dtype)
 
 
+def unsharp3d(f, sigma, amount):
+    """Unsharp mask f + amount * (f - G_sigma f) in FP64 (the Gaussian as
+    gaussian3d: truncate 3, reflect)."""
+    x = f.astype(np.float64)
+    return x + amount * (x - gaussian3d(f, sigma))
+
+
 def threshold(f: np.ndarray, t: float = 0.5) -> np.ndarray:
     f = np.ascontiguousarray(f)
     out = np.empty(f.shape, np.uint8)

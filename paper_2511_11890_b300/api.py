@@ -136,6 +136,15 @@ def tophat3d(x, se="ball", radius: int = 1, out=None, stream=None):
     return _compose(lib.hp_tophat3d, x, se, radius, out, stream)
 
 
+def unsharp3d(x, sigma: float, amount: float = 1.0, out=None, stream=None):
+    """Unsharp mask x + amount * (x - G_sigma x) as float32; device tensors only."""
+    if out is None:
+        out = _empty_like(x, HP_F32)
+    with _ctx(x), _View(x) as vi, _View(out) as vo:
+        check(lib.hp_unsharp3d(vi, vo, float(sigma), float(amount), _stream(x, stream)))
+    return out
+
+
 def threshold3d(x, t: float = 0.5, out=None, stream=None):
     if out is None:
         out = _empty_like(x, HP_U8)

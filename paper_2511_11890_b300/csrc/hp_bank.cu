@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -323,6 +325,20 @@ int hp_close3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* 
 
 int hp_tophat3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void* stream) {
   return morph_compose(in, out, se, radius, stream, 2);
+}
+
+int hp_unsharp3d(const hp_volume* in, hp_volume* out, double sigma, double amount, void* stream) {
+  if (!in || !in->data || !out || !out->data) return set_error(HP_ERR_INVALID_ARG, "null argument");
+  if (in->loc != HP_DEVICE || out->loc != HP_DEVICE)
+    return set_error(HP_ERR_UNSUPPORTED, "unsharp mask runs on device volumes only");
+  if (out->dtype != HP_F32) return set_error(HP_ERR_UNSUPPORTED, "unsharp mask output must be f32");
+  if (!std::isfinite(amount)) return set_error(HP_ERR_INVALID_ARG, "amount must be finite");
+  int st = hp_gaussian3d(in, out, sigma, 3.0, nullptr, stream);
+  if (st != HP_OK) return st;
+  const cudaError_t e = launch_unsharp(in->data, in->dtype, static_cast<float*>(out->data), (float)amount,
+                                       (int64_t)(in->nx * in->ny * in->nz), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "unsharp mask epilogue");
+  return HP_OK;
 }
 
 int hp_release_cache(void) {

@@ -101,6 +101,10 @@ int num_sms();
 // to the dtype), on stream s.
 cudaError_t launch_difference(const void* in, void* out, int dtype, int64_t n, cudaStream_t s);
 
+// g[i] = fma(amount, f[i] - g[i], f[i]) over n elements (f of dtype, g f32),
+// on stream s.
+cudaError_t launch_unsharp(const void* f, int dtype, float* g, float amount, int64_t n, cudaStream_t s);
+
 // Largest dynamic shared memory a block may opt into on the current device,
 // less 1 KB for the kernels' static shared variables.
 int max_dyn_smem();

@@ -630,6 +630,27 @@ cudaError_t launch_difference(const void* in, void* out, int dtype, int64_t n, c
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_unsharp(const T* __restrict__ f, float* __restrict__ g, float amount, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = to_f32<T>(f[i]);
+    g[i] = fmaf(amount, v - g[i], v);
+  }
+}
+
+cudaError_t launch_unsharp(const void* f, int dtype, float* g, float amount, int64_t n, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 32));
+  switch (dtype) {
+    case HP_U8: k_unsharp<uint8_t><<<grid, 256, 0, s>>>(static_cast<const uint8_t*>(f), g, amount, n); break;
+    case HP_U16: k_unsharp<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(f), g, amount, n); break;
+    case HP_F16: k_unsharp<__half><<<grid, 256, 0, s>>>(static_cast<const __half*>(f), g, amount, n); break;
+    case HP_F32: k_unsharp<float><<<grid, 256, 0, s>>>(static_cast<const float*>(f), g, amount, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s) {
   const int64_t cx = job.core_hi[2] - job.core_lo[2];
   const int64_t cy = job.core_hi[1] - job.core_lo[1];

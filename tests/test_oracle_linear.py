@@ -232,3 +232,19 @@ def test_filterbank_vjp_linear_parts_equal_adjoint_sum():
     g = oracle.filterbank3d_vjp(f, [(oracle.LOG, 1.0)], [w])
     ref = sum(oracle.gaussian3d_adjoint(w, 1.0, o) for o in [(2, 0, 0), (0, 2, 0), (0, 0, 2)])
     assert np.abs(g - ref).max() < 1e-14
+
+
+def test_unsharp_mask_pins():
+    """Unsharp mask: amount 0 gives the input exactly, a constant volume stays
+    constant, and the definition against scipy's Gaussian (an independent
+    library) for the FP64 oracle."""
+    import scipy.ndimage as nd
+    rng = np.random.default_rng(12)
+    f = rng.standard_normal((9, 10, 11))
+    assert np.array_equal(oracle.unsharp3d(f, 1.3, 0.0), f)
+    c = np.full((7, 8, 9), 3.25)
+    assert np.allclose(oracle.unsharp3d(c, 2.0, 1.7), c, rtol=0, atol=1e-12)
+    for sigma, amount in ((1.0, 0.5), (2.0, 1.5)):
+        g = nd.gaussian_filter(f, sigma, mode="reflect", truncate=3.0)
+        ref = f + amount * (f - g)
+        assert np.allclose(oracle.unsharp3d(f, sigma, amount), ref, rtol=0, atol=1e-12)

@@ -510,7 +510,8 @@ def _timed(fn, steps, warmup, stream):
 def run_open1024(args):
     """1024^3 uint16 porous volume: opening, closing and white top-hat with
     the r = 3 ball (compositions of the erosion and dilation kernels through
-    a scratch volume), and the unsharp mask (sigma 2, amount 1)."""
+    a scratch volume), the unsharp mask (sigma 2, amount 1) and the Gaussian
+    local threshold (sigma 2)."""
     import torch
 
     import paper_2511_11890_b300 as hp
@@ -536,6 +537,12 @@ def run_open1024(args):
     ms, _ = _timed(lambda: hp.unsharp3d(x, 2.0, 1.0, out=g), args.steps, max(3, args.warmup), stream)
     res["unsharp_s2"] = {"ms": ms, "GB/s": nvox * 16 / (ms / 1e3) / 1e9,
                          "hbm_frac": nvox * 16 / (ms / 1e3) / 1e9 / hbm_gbs}
+    # Gaussian local threshold sigma 2 (uint8 out): the Gaussian into scratch
+    # (2 B in, 4 B out) and the comparison (2 B + 4 B in, 1 B out)
+    u = torch.empty((n, n, n), dtype=torch.uint8, device="cuda")
+    ms, _ = _timed(lambda: hp.threshold_local3d(x, 2.0, 0.0, out=u), args.steps, max(3, args.warmup), stream)
+    res["threshold_local_s2"] = {"ms": ms, "GB/s": nvox * 13 / (ms / 1e3) / 1e9,
+                                 "hbm_frac": nvox * 13 / (ms / 1e3) / 1e9 / hbm_gbs}
     hp.stream_status(stream)
     line = {"metric": "voxels/s, 1024^3 uint16 opening (ball r = 3)", "value": nvox / (res["open"]["ms"] / 1e3),
             "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": res["open"]["ms"],

@@ -171,6 +171,14 @@ int hp_tophat3d(const hp_volume* in, hp_volume* out, hp_se se, int radius, void*
  * aliasing); HP_ERR_UNSUPPORTED for host volumes. */
 int hp_unsharp3d(const hp_volume* in, hp_volume* out, double sigma, double amount, void* stream);
 
+/* Gaussian local threshold (Sec. III-C, threshold algorithms): out (u8) =
+ * in > G_sigma in - offset, the Gaussian as hp_gaussian3d (truncate 3,
+ * reflect, FP32) and the comparison in FP32. Device volumes only (out u8 of
+ * the input's extents); the local mean is library scratch on `stream`.
+ * HP_ERR_UNSUPPORTED for host volumes. */
+int hp_threshold_local3d(const hp_volume* in, hp_volume* out, double sigma, double offset,
+                         void* stream);
+
 /* Global threshold (Sec. III-C, threshold algorithms): out (u8) = in > t,
  * compared in the input's own precision (t is rounded to it). */
 int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream);

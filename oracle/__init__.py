@@ -194,6 +194,15 @@ def unsharp3d(f, sigma, amount):
     return x + amount * (x - gaussian3d(f, sigma))
 
 
+def threshold_local(f: np.ndarray, sigma: float, offset: float = 0.0):
+    """Gaussian local threshold (Sec. III-C threshold algorithms): the
+    decision f > T with T = G_sigma f - offset in FP64; returns (u8 decision,
+    T) so that a test can tell decisions that FP32 rounding may flip (f
+    within the Gaussian's error bar of T) from those it may not."""
+    t = gaussian3d(f, sigma) - offset
+    return (f.astype(np.float64) > t).astype(np.uint8), t
+
+
 def threshold(f: np.ndarray, t: float = 0.5) -> np.ndarray:
     f = np.ascontiguousarray(f)
     out = np.empty(f.shape, np.uint8)

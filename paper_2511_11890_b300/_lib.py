@@ -25,7 +25,7 @@ HP_FILTER_G, HP_FILTER_GM, HP_FILTER_LOG = 0, 1, 2
 EXPORTS = [
     "hp_volume_create", "hp_volume_destroy", "hp_set_memory_budget", "hp_get_memory_budget",
     "hp_gaussian3d", "hp_filterbank3d", "hp_filterbank3d_bricks", "hp_erode3d", "hp_dilate3d",
-    "hp_open3d", "hp_close3d", "hp_tophat3d", "hp_unsharp3d",
+    "hp_open3d", "hp_close3d", "hp_tophat3d", "hp_unsharp3d", "hp_threshold_local3d",
     "hp_threshold3d", "hp_filterbank3d_adjoint", "hp_morph3d_backward",
     "hp_morph3d_backward_noalloc", "hp_plan_bricks",
     "hp_stream_status", "hp_selftest_wait_timeout", "hp_release_cache", "hp_get_stats", "hp_last_error", "hp_version",
@@ -75,6 +75,7 @@ def _load() -> ctypes.CDLL:
         "hp_close3d": [vp, vp, i, i, vp],
         "hp_tophat3d": [vp, vp, i, i, vp],
         "hp_unsharp3d": [vp, vp, d, d, vp],
+        "hp_threshold_local3d": [vp, vp, d, d, vp],
         "hp_threshold3d": [vp, vp, d, vp],
         "hp_filterbank3d_adjoint": [vp, pvp, ctypes.POINTER(hp_filter), i, vp, vp],
         "hp_morph3d_backward": [vp, vp, i, i, i, vp, i, vp],

@@ -145,6 +145,15 @@ def unsharp3d(x, sigma: float, amount: float = 1.0, out=None, stream=None):
     return out
 
 
+def threshold_local3d(x, sigma: float, offset: float = 0.0, out=None, stream=None):
+    """Gaussian local threshold x > G_sigma x - offset as uint8; device tensors only."""
+    if out is None:
+        out = _empty_like(x, HP_U8)
+    with _ctx(x), _View(x) as vi, _View(out) as vo:
+        check(lib.hp_threshold_local3d(vi, vo, float(sigma), float(offset), _stream(x, stream)))
+    return out
+
+
 def threshold3d(x, t: float = 0.5, out=None, stream=None):
     if out is None:
         out = _empty_like(x, HP_U8)

@@ -341,6 +341,34 @@ int hp_unsharp3d(const hp_volume* in, hp_volume* out, double sigma, double amoun
   return HP_OK;
 }
 
+int hp_threshold_local3d(const hp_volume* in, hp_volume* out, double sigma, double offset,
+                         void* stream) {
+  if (!in || !in->data || !out || !out->data) return set_error(HP_ERR_INVALID_ARG, "null argument");
+  if (in->loc != HP_DEVICE || out->loc != HP_DEVICE)
+    return set_error(HP_ERR_UNSUPPORTED, "local threshold runs on device volumes only");
+  if (out->dtype != HP_U8) return set_error(HP_ERR_UNSUPPORTED, "local threshold output must be u8");
+  if (out->nx != in->nx || out->ny != in->ny || out->nz != in->nz || out->data == in->data)
+    return set_error(HP_ERR_INVALID_ARG, "output must match the input's extents and not alias it");
+  if (!std::isfinite(offset)) return set_error(HP_ERR_INVALID_ARG, "offset must be finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = in->nx * in->ny * in->nz;
+  int st = check_scratch_budget(4 * (size_t)n);
+  if (st != HP_OK) return st;
+  Scratch sc(s);
+  void* m = nullptr;
+  cudaError_t e = sc.alloc(&m, 4 * (size_t)n);
+  if (e != cudaSuccess) return cuda_fail(e, "local threshold scratch");
+  hp_volume mv = *in;
+  mv.data = m;
+  mv.dtype = HP_F32;
+  st = hp_gaussian3d(in, &mv, sigma, 3.0, nullptr, stream);
+  if (st != HP_OK) return st;
+  e = launch_local_threshold(in->data, in->dtype, static_cast<const float*>(m), (float)offset,
+                             static_cast<uint8_t*>(out->data), n, s);
+  if (e != cudaSuccess) return cuda_fail(e, "local threshold");
+  return HP_OK;
+}
+
 int hp_release_cache(void) {
   bank_release_cache();
   return HP_OK;

@@ -105,6 +105,10 @@ cudaError_t launch_difference(const void* in, void* out, int dtype, int64_t n, c
 // on stream s.
 cudaError_t launch_unsharp(const void* f, int dtype, float* g, float amount, int64_t n, cudaStream_t s);
 
+// out[i] = f[i] > m[i] - offset (FP32 comparison), over n elements.
+cudaError_t launch_local_threshold(const void* f, int dtype, const float* m, float offset,
+                                   uint8_t* out, int64_t n, cudaStream_t s);
+
 // Largest dynamic shared memory a block may opt into on the current device,
 // less 1 KB for the kernels' static shared variables.
 int max_dyn_smem();

@@ -651,6 +651,27 @@ cudaError_t launch_unsharp(const void* f, int dtype, float* g, float amount, int
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_local_threshold(const T* __restrict__ f, const float* __restrict__ m, float offset,
+                                  uint8_t* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = to_f32<T>(f[i]) > m[i] - offset ? 1 : 0;
+}
+
+cudaError_t launch_local_threshold(const void* f, int dtype, const float* m, float offset,
+                                   uint8_t* out, int64_t n, cudaStream_t s) {
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 32));
+  switch (dtype) {
+    case HP_U8: k_local_threshold<uint8_t><<<grid, 256, 0, s>>>(static_cast<const uint8_t*>(f), m, offset, out, n); break;
+    case HP_U16: k_local_threshold<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(f), m, offset, out, n); break;
+    case HP_F16: k_local_threshold<__half><<<grid, 256, 0, s>>>(static_cast<const __half*>(f), m, offset, out, n); break;
+    case HP_F32: k_local_threshold<float><<<grid, 256, 0, s>>>(static_cast<const float*>(f), m, offset, out, n); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s) {
   const int64_t cx = job.core_hi[2] - job.core_lo[2];
   const int64_t cy = job.core_hi[1] - job.core_lo[1];

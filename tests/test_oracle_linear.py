@@ -248,3 +248,19 @@ def test_unsharp_mask_pins():
         g = nd.gaussian_filter(f, sigma, mode="reflect", truncate=3.0)
         ref = f + amount * (f - g)
         assert np.allclose(oracle.unsharp3d(f, sigma, amount), ref, rtol=0, atol=1e-12)
+
+
+def test_local_threshold_pins():
+    """Gaussian local threshold: on a constant volume T = c - offset, so the
+    decision is offset > 0 everywhere; against scipy's Gaussian elsewhere."""
+    import scipy.ndimage as nd
+    c = np.full((6, 7, 8), 100.0)
+    assert oracle.threshold_local(c, 1.5, 2.0)[0].all()
+    assert not oracle.threshold_local(c, 1.5, -2.0)[0].any()
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((9, 10, 11))
+    u, t = oracle.threshold_local(f, 2.0, 0.1)
+    ref = nd.gaussian_filter(f, 2.0, mode="reflect", truncate=3.0) - 0.1
+    assert np.allclose(t, ref, rtol=0, atol=1e-12)
+    sure = np.abs(f - ref) > 1e-9
+    assert np.array_equal(u[sure], (f > ref)[sure].astype(np.uint8))

@@ -180,7 +180,10 @@ int hp_threshold_local3d(const hp_volume* in, hp_volume* out, double sigma, doub
                          void* stream);
 
 /* Global threshold (Sec. III-C, threshold algorithms): out (u8) = in > t,
- * compared in the input's own precision (t is rounded to it). */
+ * decided exactly for every input dtype: the kernels compare against the
+ * largest value of the input's type that is <= t, so a t that is not
+ * representable in that type (0.1 for f32, 7499.7 for u16) is never rounded
+ * up. NaN inputs give 0. HP_ERR_INVALID_ARG when t is NaN. */
 int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream);
 
 /* Adjoint of the filter bank (device mode, f32): gin = sum_i J_i^T gouts[i],
@@ -211,8 +214,10 @@ int hp_morph3d_backward(const hp_volume* in, const hp_volume* gout, int is_dilat
  * process exits. Larger volumes return HP_ERR_UNSUPPORTED; use
  * hp_morph3d_backward for them.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress), which may also load the library's device code;
- *     make that first call before any stream capture.
+ *     (cudaGetSymbolAddress, with that device current), which may also load
+ *     the library's device code; make that first call before any stream
+ *     capture. The address is cached per device; after cudaDeviceReset call
+ *     hp_release_cache() so that the next call looks it up again.
  *   - Every call uses the same array: calls that overlap on the GPU (other
  *     streams, other host threads) race and give wrong results. Order them.
  *   - No state needs clearing between calls: each call rewrites every index
@@ -249,7 +254,9 @@ int hp_stream_status(void* stream);
  * or unbounded spin is involved. Returns HP_OK or HP_ERR_CUDA (launch). */
 int hp_selftest_wait_timeout(void* stream);
 
-/* Free cached filter-bank launch plans (graphs and work lists). */
+/* Free cached filter-bank launch plans (graphs and work lists) and forget
+ * cached per-device addresses of library device variables (call it after a
+ * cudaDeviceReset). */
 int hp_release_cache(void);
 
 /* Counters of the last call; see hp_stats. */

@@ -179,12 +179,16 @@ def close3d(f, se, rad):
 
 
 def tophat3d(f, se, rad):
-    """White top-hat: f minus its opening, the difference taken in FP32 (FP64
-    for float64 input) and rounded to f's dtype: exact for integer dtypes,
-    where f >= opening, and numpy's own float16 arithmetic for float16."""
-    wt = np.float64 if f.dtype == np.float64 else np.float32
-    d = f.astype(wt) - open3d(f, se, rad).astype(wt)
-    return d.astype(f.dtype)
+    """White top-hat: f minus its opening, rounded once (to nearest, ties to
+    even) to f's dtype. Integers: exact, since f >= its opening. float16:
+    the difference of two float16 values is exact in FP64 (both are
+    multiples of 2^-24 below 2^16 in magnitude, so it needs at most 41
+    significant bits), then one rounding to float16. float32: the FP32
+    subtraction itself (correctly rounded). float64: the FP64 subtraction."""
+    o = open3d(f, se, rad)
+    if f.dtype == np.float32:
+        return f - o
+    return (f.astype(np.float64) - o.astype(np.float64)).astype(f.dtype)
 
 
 def unsharp3d(f, sigma, amount):

@@ -22,12 +22,16 @@
  *   - Erosion eps(f)(p) = min over o in B of f(R(p + o)); dilation
  *     delta(f)(p) = max over o in B of f(R(p - o)). Cube of half-width rho:
  *     max(|dz|,|dy|,|dx|) <= rho. Ball of radius r: dz^2+dy^2+dx^2 <= r^2.
+ *     Min and max follow IEEE 754 totalOrder: integers by value; floating
+ *     point by value with -0 below +0, a NaN whose sign bit is clear above
+ *     +inf, one whose sign bit is set below -inf, and NaNs of one sign by
+ *     their trailing significand field (see total_cmp).
  *   - Threshold: u8 = (f > t).
  *   - Adjoint of a 1D filter: t[j] = sum_k g(k) w[j + k] over the
  *     zero-extended w, j in [-r, n-1+r]; then gin[R(j)] += t[j].
  *   - Morphology subgradient: each output routes its weight to the source
- *     q = R(p +- o) holding the extreme value; ties go to the smallest
- *     linear index q.
+ *     q = R(p +- o) holding the extreme value (in totalOrder); ties (equal
+ *     elements) go to the smallest linear index q.
  *
  * Chunking (Sec. III-D): every forward function reads its input from a box
  * [in_lo, in_lo + in_dims) of a global volume of size gdims and writes the
@@ -99,6 +103,63 @@ static double load_elem(const void* p, int dt, int64_t i) {
     case ORC_F32: return (double)((const float*)p)[i];
     default: return ((const double*)p)[i];
   }
+}
+
+/* IEEE 754 totalOrder of elements i and j of p (<0, 0 or >0). Integers
+ * compare by value. A floating-point element is split into its sign bit,
+ * whether it is a NaN, its trailing significand field and its value; then:
+ *   - two non-NaNs compare by value, and equal values that are both zero
+ *     by sign (-0 < +0);
+ *   - a NaN with the sign bit clear is above every non-NaN, one with the
+ *     sign bit set below every non-NaN;
+ *   - NaNs of opposite signs: the negative one is below; NaNs of one sign
+ *     compare by significand field, ascending for +, descending for -. */
+typedef struct {
+  int sign, nan;
+  uint64_t sig;
+  double v;
+} orc_fp;
+
+static orc_fp fp_split(const void* p, int dt, int64_t i) {
+  orc_fp r;
+  uint64_t bits = 0, expmask = 0, sigmask = 0;
+  int sbit = 0;
+  if (dt == ORC_F16) {
+    bits = ((const uint16_t*)p)[i];
+    sbit = 15; expmask = 0x7C00u; sigmask = 0x03FFu;
+  } else if (dt == ORC_F32) {
+    uint32_t b;
+    memcpy(&b, (const char*)p + 4 * i, 4);
+    bits = b;
+    sbit = 31; expmask = 0x7F800000u; sigmask = 0x007FFFFFu;
+  } else {
+    memcpy(&bits, (const char*)p + 8 * i, 8);
+    sbit = 63; expmask = 0x7FF0000000000000ull; sigmask = 0x000FFFFFFFFFFFFFull;
+  }
+  r.sign = (int)((bits >> sbit) & 1u);
+  r.sig = bits & sigmask;
+  r.nan = (bits & expmask) == expmask && r.sig != 0;
+  r.v = load_elem(p, dt, i);
+  return r;
+}
+
+static int total_cmp(const void* p, int dt, int64_t i, int64_t j) {
+  if (dt == ORC_U8 || dt == ORC_U16) {
+    double a = load_elem(p, dt, i), b = load_elem(p, dt, j);
+    return a < b ? -1 : (a > b ? 1 : 0);
+  }
+  orc_fp a = fp_split(p, dt, i), b = fp_split(p, dt, j);
+  if (!a.nan && !b.nan) {
+    if (a.v < b.v) return -1;
+    if (a.v > b.v) return 1;
+    if (a.v == 0.0 && a.sign != b.sign) return a.sign ? -1 : 1;
+    return 0;
+  }
+  if (a.nan && !b.nan) return a.sign ? -1 : 1;
+  if (!a.nan && b.nan) return b.sign ? 1 : -1;
+  if (a.sign != b.sign) return a.sign ? -1 : 1;
+  if (a.sig == b.sig) return 0;
+  return (a.sig < b.sig) == (a.sign == 0) ? -1 : 1;
 }
 
 /* Index of global voxel (z, y, x) inside the input box, or -1. */
@@ -267,7 +328,6 @@ int orc_morph3d(const void* in, int dtype, const int64_t in_lo[3], const int64_t
       for (int64_t x = 0; x < out_dims[2]; ++x) {
         int64_t pz = out_lo[0] + z, py = out_lo[1] + y, px = out_lo[2] + x;
         int64_t best_q = -1;
-        double best = 0.0;
         for (int dz = -rad; dz <= rad; ++dz)
           for (int dy = -rad; dy <= rad; ++dy)
             for (int dx = -rad; dx <= rad; ++dx) {
@@ -284,11 +344,8 @@ int orc_morph3d(const void* in, int dtype, const int64_t in_lo[3], const int64_t
               }
               int64_t q = box_index(in_lo, in_dims, sz, sy, sx);
               if (q < 0) return ORC_ERR_HALO;
-              double v = load_elem(in, dtype, q);
-              if (best_q < 0 || (is_dilate ? v > best : v < best)) {
-                best = v;
-                best_q = q;
-              }
+              int c = best_q < 0 ? 0 : total_cmp(in, dtype, q, best_q);
+              if (best_q < 0 || (is_dilate ? c > 0 : c < 0)) best_q = q;
             }
         memcpy((char*)out + (size_t)((z * out_dims[1] + y) * out_dims[2] + x) * es,
                (const char*)in + (size_t)best_q * es, es);
@@ -429,7 +486,6 @@ int orc_morph3d_vjp(const void* in, int dtype, const int64_t dims[3], int se, in
     for (int64_t py = 0; py < dims[1]; ++py)
       for (int64_t px = 0; px < dims[2]; ++px) {
         int64_t best_q = -1;
-        double best = 0.0;
         for (int dz = -rad; dz <= rad; ++dz)
           for (int dy = -rad; dy <= rad; ++dy)
             for (int dx = -rad; dx <= rad; ++dx) {
@@ -438,10 +494,9 @@ int orc_morph3d_vjp(const void* in, int dtype, const int64_t dims[3], int se, in
               int64_t q = (orc_reflect(pz + sg * dz, dims[0]) * dims[1] +
                            orc_reflect(py + sg * dy, dims[1])) * dims[2] +
                           orc_reflect(px + sg * dx, dims[2]);
-              double v = load_elem(in, dtype, q);
-              int better = best_q < 0 || (is_dilate ? v > best : v < best) ||
-                           (v == best && q < best_q);
-              if (better) { best = v; best_q = q; }
+              int c = best_q < 0 ? 0 : total_cmp(in, dtype, q, best_q);
+              int better = best_q < 0 || (is_dilate ? c > 0 : c < 0) || (c == 0 && q < best_q);
+              if (better) best_q = q;
             }
         int64_t p = (pz * dims[1] + py) * dims[2] + px;
         gin[best_q] += w[p];

@@ -32,13 +32,6 @@
 #include "hp_device.cuh"
 #include "hp_internal.h"
 
-struct hp_volume {
-  void* data;
-  int dtype;
-  int loc;
-  int64_t nx, ny, nz;
-};
-
 namespace hp {
 
 // ------------------------------------------------------------------ errors
@@ -101,6 +94,17 @@ static int effective_budget(size_t* out) {
   return HP_OK;
 }
 
+int check_scratch_budget(size_t need) {
+  size_t b = 0;
+  const int st = effective_budget(&b);
+  if (st != HP_OK) return st;
+  if (need > b)
+    return set_error(HP_ERR_BUDGET, "scratch of " + std::to_string(need) +
+                                        " bytes exceeds the budget of " + std::to_string(b) +
+                                        " bytes");
+  return HP_OK;
+}
+
 // Device error word: one int per device, set by kernels whose bounded waits
 // give up. Its device address is looked up once per device.
 __device__ int g_error_word;
@@ -109,6 +113,13 @@ static std::mutex g_err_mu;
 
 int64_t bank_cache_bytes();
 int bank_last_kernels();
+
+// Drops the cached error-word addresses (hp_release_cache), so that after a
+// cudaDeviceReset the next call looks the word up in the new context.
+void error_word_forget() {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  for (auto& p : g_err_ptr) p = nullptr;
+}
 
 int* device_error_word() {
   int dev = 0;
@@ -311,20 +322,22 @@ struct Brick {
   hp_box in;
 };
 
+// Device bytes of one stage: its input box (in_b per voxel, plus scr_b per
+// voxel of kernel scratch) and its core output box.
 static size_t stage_bytes(const int64_t ext[3], const int64_t n[3], int halo, size_t in_b,
-                          size_t out_b) {
+                          size_t out_b, size_t scr_b) {
   size_t inv = 1, outv = 1;
   for (int a = 0; a < 3; ++a) {
     int64_t e = std::min<int64_t>(ext[a] + 2 * (int64_t)halo + (a == 2 ? 32 : 0), n[a]);
     inv *= (size_t)e;
     outv *= (size_t)ext[a];
   }
-  return inv * in_b + outv * out_b;
+  return inv * (in_b + scr_b) + outv * out_b;
 }
 
 // Plan bricks; returns HP_OK or HP_ERR_BUDGET / HP_ERR_INVALID_ARG.
-static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t budget, int stages,
-                int min_bricks, std::vector<Brick>* out) {
+static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t scr_b,
+                size_t budget, int stages, int min_bricks, std::vector<Brick>* out) {
   if (n[0] < 1 || n[1] < 1 || n[2] < 1 || halo < 0 || stages < 1)
     return set_error(HP_ERR_INVALID_ARG, "plan: bad extents, halo or stages");
   const size_t per = budget / (size_t)stages;
@@ -336,13 +349,13 @@ static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t 
     for (int b = 0; b < a; ++b) ext[b] = 1;
     for (int b = a; b < 3; ++b) ext[b] = n[b];
     ext[a] = 1;
-    if (stage_bytes(ext, n, halo, in_b, out_b) > per) continue;
+    if (stage_bytes(ext, n, halo, in_b, out_b, scr_b) > per) continue;
     // largest extent along a that fits
     int64_t lo = 1, hi = n[a];
     while (lo < hi) {
       int64_t mid = (lo + hi + 1) / 2;
       ext[a] = mid;
-      if (stage_bytes(ext, n, halo, in_b, out_b) <= per) lo = mid;
+      if (stage_bytes(ext, n, halo, in_b, out_b, scr_b) <= per) lo = mid;
       else hi = mid - 1;
     }
     ext[a] = lo;
@@ -383,7 +396,11 @@ static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t 
 struct Op {
   int halo;
   int out_dtype;
-  // enqueue the op for one job
+  // planning bound of the kernel scratch, bytes per voxel of the input box
+  size_t scratch_per_in_voxel = 0;
+  // exact scratch bytes of one job (null: none)
+  std::function<size_t(const Job&)> scratch_bytes;
+  // enqueue the op for one job (job.scratch set when scratch_bytes > 0)
   std::function<cudaError_t(const Job&, cudaStream_t)> launch;
 };
 
@@ -486,10 +503,26 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
   if (faults.budget) budget = 1;
   const int S = 3;
   std::vector<Brick> bricks;
-  st = plan(n, op.halo, ies, oes, budget, S, 8, &bricks);
+  st = plan(n, op.halo, ies, oes, op.scratch_per_in_voxel, budget, S, 8, &bricks);
   if (st != HP_OK) return st;
 
-  size_t max_in = 0, max_out = 0;
+  const int64_t vol_lo[3] = {0, 0, 0};
+  // the job of brick b with stage buffers din / dout
+  auto brick_job = [&](const Brick& b, void* din, void* dout) {
+    Job job;
+    job.in = DevBox{din, in->dtype, {b.in.lo[0], b.in.lo[1], b.in.lo[2]},
+                    {b.in.hi[0] - b.in.lo[0], b.in.hi[1] - b.in.lo[1], b.in.hi[2] - b.in.lo[2]}};
+    job.out = DevOut{dout, op.out_dtype, {b.core.lo[0], b.core.lo[1], b.core.lo[2]},
+                     {b.core.hi[0] - b.core.lo[0], b.core.hi[1] - b.core.lo[1],
+                      b.core.hi[2] - b.core.lo[2]}};
+    for (int a = 0; a < 3; ++a) {
+      job.gdims[a] = n[a];
+      job.core_lo[a] = b.core.lo[a];
+      job.core_hi[a] = b.core.hi[a];
+    }
+    return job;
+  };
+  size_t max_in = 0, max_out = 0, max_scr = 0;
   for (auto& b : bricks) {
     size_t vi = ies, vo = oes;
     for (int a = 0; a < 3; ++a) {
@@ -498,6 +531,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     }
     max_in = std::max(max_in, vi);
     max_out = std::max(max_out, vo);
+    if (op.scratch_bytes) max_scr = std::max(max_scr, op.scratch_bytes(brick_job(b, nullptr, nullptr)));
   }
   const int nst = (int)std::min<size_t>(S, bricks.size());
   const bool in_pinned = is_pinned(in->data), out_pinned = is_pinned(out->data);
@@ -505,6 +539,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
   struct Stage {
     void* din = nullptr;
     void* dout = nullptr;
+    void* dscr = nullptr;
     void* hin = nullptr;
     void* hout = nullptr;
     cudaStream_t s = nullptr;
@@ -533,6 +568,12 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     if ((e = cudaMalloc(&x.dout, max_out)) != cudaSuccess) { cfail(e, "cudaMalloc(out stage)"); break; }
     dev_bytes += (int64_t)max_out;
     track_alloc((int64_t)max_out);
+    if (max_scr > 0) {
+      if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
+      if ((e = cudaMalloc(&x.dscr, max_scr)) != cudaSuccess) { cfail(e, "cudaMalloc(scratch stage)"); break; }
+      dev_bytes += (int64_t)max_scr;
+      track_alloc((int64_t)max_scr);
+    }
     if (!in_pinned) {
       if ((e = cudaHostAlloc(&x.hin, max_in, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); break; }
       pinned += max_in;
@@ -545,7 +586,6 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     if ((e = cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming)) != cudaSuccess) { cfail(e, "cudaEventCreate"); break; }
   }
 
-  const int64_t vol_lo[3] = {0, 0, 0};
   // completes brick b of stage x: copy its staged output to the user array
   auto retire = [&](Stage& x) {
     if (x.brick < 0) return;
@@ -580,14 +620,9 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     }
     if (e != cudaSuccess) { cfail(e, "H2D copy"); break; }
     h2d += ies * (uint64_t)(idims[0] * idims[1] * idims[2]);
-    Job job;
-    job.in = DevBox{x.din, in->dtype, {b.in.lo[0], b.in.lo[1], b.in.lo[2]}, {idims[0], idims[1], idims[2]}};
-    job.out = DevOut{x.dout, op.out_dtype, {b.core.lo[0], b.core.lo[1], b.core.lo[2]}, {cdims[0], cdims[1], cdims[2]}};
-    for (int a = 0; a < 3; ++a) {
-      job.gdims[a] = n[a];
-      job.core_lo[a] = b.core.lo[a];
-      job.core_hi[a] = b.core.hi[a];
-    }
+    Job job = brick_job(b, x.din, x.dout);
+    job.scratch = x.dscr;
+    job.scratch_bytes = max_scr;
     if ((e = op.launch(job, x.s)) != cudaSuccess) { cfail(e, "kernel launch"); break; }
     if (faults.fail_copy()) { fail(HP_ERR_CUDA, "injected memcpy failure"); break; }
     if (out_pinned) {
@@ -620,6 +655,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     if (x.s) cudaStreamDestroy(x.s);
     if (x.din) { cudaFree(x.din); track_free((int64_t)max_in); }
     if (x.dout) { cudaFree(x.dout); track_free((int64_t)max_out); }
+    if (x.dscr) { cudaFree(x.dscr); track_free((int64_t)max_scr); }
     if (x.hin) cudaFreeHost(x.hin);
     if (x.hout) cudaFreeHost(x.hout);
   }
@@ -679,7 +715,17 @@ static int run(const Op& op, const hp_volume* in, hp_volume* out, void* stream) 
   begin_call();
   if (in->loc == HP_HOST) return run_host(op, in, out);
   Job j = whole_job(in, out, op.out_dtype);
-  cudaError_t e = op.launch(j, (cudaStream_t)stream);
+  const cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  const size_t need = op.scratch_bytes ? op.scratch_bytes(j) : 0;
+  if (need > 0) {
+    const int st = check_scratch_budget(need);
+    if (st != HP_OK) return st;
+    cudaError_t e = sc.alloc(&j.scratch, need);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel scratch");
+    j.scratch_bytes = need;
+  }
+  cudaError_t e = op.launch(j, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   std::lock_guard<std::mutex> lk(g_mu);
   g_stats.bricks = 1;
@@ -749,6 +795,14 @@ int hp_gaussian3d(const hp_volume* in, hp_volume* out, double sigma, double trun
   Op op;
   op.halo = taps->r;
   op.out_dtype = out->dtype;
+  const int r = taps->r;
+  {
+    Job probe = whole_job(in, out, out->dtype);
+    if (gauss_scratch_bytes(probe, r) > 0) {
+      op.scratch_per_in_voxel = 2 * sizeof(float);
+      op.scratch_bytes = [r](const Job& j) { return gauss_scratch_bytes(j, r); };
+    }
+  }
   op.launch = [taps](const Job& j, cudaStream_t s) { return launch_gauss(j, *taps, s); };
   return run(op, in, out, stream);
 }
@@ -781,6 +835,7 @@ int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream) 
   int st = check_pair(in, out);
   if (st != HP_OK) return st;
   if (out->dtype != HP_U8) return set_error(HP_ERR_UNSUPPORTED, "threshold output dtype must be u8");
+  if (std::isnan(t)) return set_error(HP_ERR_INVALID_ARG, "threshold must not be NaN");
   Op op;
   op.halo = 0;
   op.out_dtype = HP_U8;
@@ -794,7 +849,7 @@ int hp_plan_bricks(int64_t nx, int64_t ny, int64_t nz, int halo, size_t in_bytes
   if (!nbricks) return set_error(HP_ERR_INVALID_ARG, "null nbricks");
   const int64_t n[3] = {nz, ny, nx};
   std::vector<Brick> b;
-  int st = plan(n, halo, in_bytes, out_bytes, budget, stages, min_bricks, &b);
+  int st = plan(n, halo, in_bytes, out_bytes, 0, budget, stages, min_bricks, &b);
   if (st != HP_OK) return st;
   *nbricks = (int)b.size();
   for (int i = 0; i < (int)b.size() && i < max_bricks; ++i) {

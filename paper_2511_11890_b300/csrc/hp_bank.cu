@@ -3,19 +3,13 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include <string>
 #include <vector>
 
 #include "hp_internal.h"
-
-struct hp_volume {
-  void* data;
-  int dtype;
-  int loc;
-  int64_t nx, ny, nz;
-};
 
 namespace hp {
 
@@ -38,42 +32,8 @@ cudaError_t launch_morph_arg(const void* in, int dt, const int64_t dims[3], int 
                              int is_dilate, int32_t* arg, cudaStream_t s);
 cudaError_t launch_morph_gather(const int32_t* arg, const float* gout, float* gin,
                                 const int64_t dims[3], int rad, int accumulate, cudaStream_t s);
-size_t budget_setting();
-void note_scratch(int64_t bytes);
-
-// Stream-ordered scratch, counted against the memory budget.
-struct Scratch {
-  cudaStream_t s;
-  std::vector<std::pair<void*, size_t>> bufs;
-  explicit Scratch(cudaStream_t st) : s(st) {}
-  cudaError_t alloc(void** p, size_t bytes) {
-    cudaError_t e = cudaMallocAsync(p, bytes, s);
-    if (e == cudaSuccess) {
-      bufs.push_back({*p, bytes});
-      note_scratch((int64_t)bytes);
-    }
-    return e;
-  }
-  ~Scratch() {
-    for (auto& b : bufs) {
-      cudaFreeAsync(b.first, s);
-      note_scratch(-(int64_t)b.second);
-    }
-  }
-};
-
-static int check_scratch_budget(size_t need) {
-  size_t b = budget_setting();
-  if (b == 0) {
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return set_error(HP_ERR_CUDA, "cudaMemGetInfo failed");
-    b = (size_t)(0.8 * (double)fr);
-  }
-  if (need > b)
-    return set_error(HP_ERR_BUDGET, "scratch of " + std::to_string(need) + " bytes exceeds the budget of " +
-                                        std::to_string(b) + " bytes");
-  return HP_OK;
-}
+void noalloc_forget();
+void error_word_forget();
 
 static Job whole_job_of(const hp_volume* in, void* out, int out_dtype) {
   Job j;
@@ -201,11 +161,20 @@ int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
   const int64_t dims[3] = {in->nz, in->ny, in->nx};
   const int64_t total = dims[0] * dims[1] * dims[2];
   const size_t vb = sizeof(float) * (size_t)total;
-  int st = check_scratch_budget(vb * (any_gm ? 6 : 2));
+  // GM forms its derivatives with the Gaussian kernels; the generic path
+  // (large radii, thin volumes) needs scratch of its own
+  size_t gscr = 0;
+  for (int i = 0; i < n; ++i)
+    if (f[i].kind == HP_FILTER_GM)
+      gscr = std::max(gscr, gauss_scratch_bytes(whole_job_of(in, gin->data, HP_F32),
+                                                radius_of(f[i].sigma, 3.0)));
+  int st = check_scratch_budget(vb * (any_gm ? 6 : 2) + gscr);
   if (st != HP_OK) return st;
   Scratch sc(s);
   float *t1 = nullptr, *t2 = nullptr, *dz = nullptr, *dy = nullptr, *dx = nullptr, *v = nullptr;
+  void* gs = nullptr;
   cudaError_t e = sc.alloc((void**)&t1, vb);
+  if (e == cudaSuccess && gscr > 0) e = sc.alloc(&gs, gscr);
   if (e == cudaSuccess) e = sc.alloc((void**)&t2, vb);
   if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dz, vb);
   if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dy, vb);
@@ -235,7 +204,10 @@ int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
         int ord[3] = {0, 0, 0};
         ord[a] = 1;
         make_taps(sigma, 3.0, ord, &taps);
-        e = launch_gauss(whole_job_of(in, D[a], HP_F32), taps, s);
+        Job j = whole_job_of(in, D[a], HP_F32);
+        j.scratch = gs;
+        j.scratch_bytes = gscr;
+        e = launch_gauss(j, taps, s);
       }
       for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         int ord[3] = {0, 0, 0};
@@ -371,6 +343,8 @@ int hp_threshold_local3d(const hp_volume* in, hp_volume* out, double sigma, doub
 
 int hp_release_cache(void) {
   bank_release_cache();
+  noalloc_forget();
+  error_word_forget();
   return HP_OK;
 }
 

@@ -12,6 +12,15 @@
 
 #include "hp.h"
 
+// The opaque volume view of the C ABI (hp.h): a non-owning pointer to a
+// dense C-order volume with its dtype, location and extents.
+struct hp_volume {
+  void* data;
+  int dtype;
+  int loc;
+  int64_t nx, ny, nz;
+};
+
 namespace hp {
 
 constexpr int kMaxR = 12;        // largest radius with a tiled z-march kernel
@@ -56,13 +65,17 @@ struct DevOut {
   int64_t dims[3];
 };
 
-// One filtering job over a core box of the global volume.
+// One filtering job over a core box of the global volume. `scratch` is
+// device memory the caller provides for kernels that need it (the generic
+// Gaussian path: gauss_scratch_bytes); launchers never allocate.
 struct Job {
   DevBox in;
   DevOut out;
   int64_t gdims[3];
   int64_t core_lo[3];
   int64_t core_hi[3];
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
 };
 
 // FP32 taps per axis (z, y, x), index k + r for k in [-r, r].
@@ -80,6 +93,10 @@ void taps1d_f64(double sigma, int r, int order, double* w);
 int* device_error_word();
 
 // Launchers (enqueue only). Return a cudaError_t.
+// Scratch bytes launch_gauss needs in job.scratch for radius r (nonzero only
+// on the generic three-pass path: r > kMaxR, r = 0, or a volume thinner than
+// r in x or y); at most 8 bytes per voxel of the job's input box.
+size_t gauss_scratch_bytes(const Job& job, int r);
 cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s);
 cudaError_t launch_gauss_zr(const Job& job, const Taps& taps, cudaStream_t s);
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
@@ -124,5 +141,38 @@ int64_t pick_zchunk(int64_t cz, int64_t tiles, int64_t slots, int halo, int alig
 
 // HP_LOG >= 1 prints the kernel path chosen for each launch to stderr.
 int log_level();
+
+// Library device-byte counters (hp_stats): bytes > 0 on allocation, < 0 on
+// release.
+void note_scratch(int64_t bytes);
+size_t budget_setting();
+// HP_OK when `need` bytes fit the effective budget (the user value, or 0.8 x
+// free device memory), else HP_ERR_BUDGET with a message.
+int check_scratch_budget(size_t need);
+
+// Stream-ordered scratch of device-mode calls, counted in the library's
+// device-byte statistics and released in stream order when it goes out of
+// scope.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<std::pair<void*, size_t>> bufs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  cudaError_t alloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) {
+      bufs.push_back({*p, bytes});
+      note_scratch((int64_t)bytes);
+    }
+    return e;
+  }
+  ~Scratch() {
+    for (auto& b : bufs) {
+      cudaFreeAsync(b.first, s);
+      note_scratch(-(int64_t)b.second);
+    }
+  }
+};
 
 }  // namespace hp

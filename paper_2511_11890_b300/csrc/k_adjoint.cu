@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "hp_device.cuh"
@@ -30,12 +31,22 @@ namespace {
 
 constexpr int kBlock = 256;
 
-__device__ __forceinline__ float load_as_f32(const void* p, int dt, int64_t i) {
+// Element i as an unsigned key whose order is IEEE 754 totalOrder of the
+// values (the order the forward erosion / dilation uses): integers as they
+// are; floating point with the sign bit set complemented, else with the sign
+// bit set, so -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN.
+__device__ __forceinline__ uint32_t load_key(const void* p, int dt, int64_t i) {
   switch (dt) {
-    case HP_U8: return (float)static_cast<const uint8_t*>(p)[i];
-    case HP_U16: return (float)static_cast<const uint16_t*>(p)[i];
-    case HP_F16: return __half2float(static_cast<const __half*>(p)[i]);
-    default: return static_cast<const float*>(p)[i];
+    case HP_U8: return static_cast<const uint8_t*>(p)[i];
+    case HP_U16: return static_cast<const uint16_t*>(p)[i];
+    case HP_F16: {
+      const uint32_t b = static_cast<const uint16_t*>(p)[i];
+      return (b & 0x8000u) ? (~b & 0xFFFFu) : (b | 0x8000u);
+    }
+    default: {
+      const uint32_t b = static_cast<const uint32_t*>(p)[i];
+      return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+    }
   }
 }
 
@@ -339,7 +350,7 @@ __global__ void k_morph_arg(const void* __restrict__ in, int dt, int64_t n0, int
        p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = p % n2, y = (p / n2) % n1, z = p / (n1 * n2);
     int64_t best_q = -1;
-    float best = 0.0f;
+    uint32_t best = 0u;
     for (int dz = -rad; dz <= rad; ++dz) {
       const int64_t sz = reflect(z + sg * dz, n0);
       for (int dy = -rad; dy <= rad; ++dy) {
@@ -348,7 +359,7 @@ __global__ void k_morph_arg(const void* __restrict__ in, int dt, int64_t n0, int
           if (ball && dz * dz + dy * dy + dx * dx > rad * rad) continue;
           const int64_t sx = reflect(x + sg * dx, n2);
           const int64_t q = (sz * n1 + sy) * n2 + sx;
-          const float v = load_as_f32(in, dt, q);
+          const uint32_t v = load_key(in, dt, q);
           const bool better = best_q < 0 || (is_dilate ? v > best : v < best) ||
                               (v == best && q < best_q);
           if (better) {
@@ -385,10 +396,10 @@ __global__ void __launch_bounds__(kBlock)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // reflected input box, x pass (value, source x), y pass (value, source
   // y * n2 + x), reflected coordinates; sizes in cube_arg_smem<RAD>()
-  auto v0 = reinterpret_cast<float(*)[VY][VX]>(smem_raw);
-  auto v1 = reinterpret_cast<float(*)[VY][kCX]>(smem_raw + 4 * VZ * VY * VX);
+  auto v0 = reinterpret_cast<uint32_t(*)[VY][VX]>(smem_raw);
+  auto v1 = reinterpret_cast<uint32_t(*)[VY][kCX]>(smem_raw + 4 * VZ * VY * VX);
   auto i1 = reinterpret_cast<int32_t(*)[VY][kCX]>(smem_raw + 4 * VZ * VY * (VX + kCX));
-  auto v2 = reinterpret_cast<float(*)[kCY][kCX]>(smem_raw + 4 * VZ * VY * (VX + 2 * kCX));
+  auto v2 = reinterpret_cast<uint32_t(*)[kCY][kCX]>(smem_raw + 4 * VZ * VY * (VX + 2 * kCX));
   auto i2 = reinterpret_cast<int32_t(*)[kCY][kCX]>(smem_raw + 4 * VZ * (VY * (VX + 2 * kCX) + kCY * kCX));
   int32_t* sx = reinterpret_cast<int32_t*>(smem_raw + 4 * VZ * (VY * (VX + 2 * kCX) + 2 * kCY * kCX));
   int32_t* sy = sx + VX;
@@ -402,22 +413,22 @@ __global__ void __launch_bounds__(kBlock)
   __syncthreads();
   for (int e = tid; e < VZ * VY * VX; e += kBlock) {
     const int c = e % VX, b = (e / VX) % VY, a = e / (VX * VY);
-    v0[a][b][c] = load_as_f32(in, dt, ((int64_t)sz[a] * n1 + sy[b]) * n2 + sx[c]);
+    v0[a][b][c] = load_key(in, dt, ((int64_t)sz[a] * n1 + sy[b]) * n2 + sx[c]);
   }
   __syncthreads();
   // linear indices fit in int32 (the index array is int32)
-  auto better = [&](float v, int32_t q, float best, int32_t bq) {
+  auto better = [&](uint32_t v, int32_t q, uint32_t best, int32_t bq) {
     return (is_dilate ? v > best : v < best) || (v == best && q < bq);
   };
   // x pass over every staged row; window offset sg*dx from the output column
   for (int e = tid; e < VZ * VY * kCX; e += kBlock) {
     const int x = e % kCX, b = (e / kCX) % VY, a = e / (kCX * VY);
-    float best = 0.0f;
+    uint32_t best = 0u;
     int bq = -1;
 #pragma unroll
     for (int d = -RAD; d <= RAD; ++d) {
       const int c = x + RAD + sg * d;
-      const float v = v0[a][b][c];
+      const uint32_t v = v0[a][b][c];
       if (bq < 0 || better(v, sx[c], best, bq)) {
         best = v;
         bq = sx[c];
@@ -429,12 +440,12 @@ __global__ void __launch_bounds__(kBlock)
   __syncthreads();
   for (int e = tid; e < VZ * kCY * kCX; e += kBlock) {
     const int x = e % kCX, y = (e / kCX) % kCY, a = e / (kCX * kCY);
-    float best = 0.0f;
+    uint32_t best = 0u;
     int32_t bq = -1;
 #pragma unroll
     for (int d = -RAD; d <= RAD; ++d) {
       const int b = y + RAD + sg * d;
-      const float v = v1[a][b][x];
+      const uint32_t v = v1[a][b][x];
       const int32_t q = sy[b] * n2 + i1[a][b][x];
       if (bq < 0 || better(v, q, best, bq)) {
         best = v;
@@ -448,14 +459,14 @@ __global__ void __launch_bounds__(kBlock)
   for (int e = tid; e < kCZ * kCY * kCX; e += kBlock) {
     const int x = e % kCX, y = (e / kCX) % kCY, z = e / (kCX * kCY);
     if (z0 + z >= n0 || y0 + y >= n1 || x0 + x >= n2) continue;
-    float best = 0.0f;
+    uint32_t best = 0u;
     int32_t bq = -1;
     const int32_t plane = n1 * n2;
 #pragma unroll
     for (int d = -RAD; d <= RAD; ++d) {
       const int a = z + RAD + sg * d;
       const int32_t q = sz[a] * plane + i2[a][y][x];
-      const float v = v2[a][y][x];
+      const uint32_t v = v2[a][y][x];
       if (bq < 0 || better(v, q, best, bq)) {
         best = v;
         bq = q;
@@ -674,18 +685,19 @@ namespace {
 constexpr int64_t kNoAllocMaxVoxels = int64_t(1) << 24;  // 256^3 voxels, 64 MiB
 static __device__ __align__(256) int32_t g_noalloc_arg[kNoAllocMaxVoxels];
 int32_t* g_noalloc_ptr[64];  // device address per device, set on first use
+std::mutex g_noalloc_mu;     // guards g_noalloc_ptr
 }  // namespace
+
+// Drops the cached device addresses (hp_release_cache), so that after a
+// cudaDeviceReset the next call looks the array up in the new context.
+void noalloc_forget() {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  for (auto& p : g_noalloc_ptr) p = nullptr;
+}
 
 }  // namespace hp
 
 using namespace hp;
-
-struct hp_volume {
-  void* data;
-  int dtype;
-  int loc;
-  int64_t nx, ny, nz;
-};
 
 extern "C" int hp_morph3d_backward_noalloc(const hp_volume* in, const hp_volume* gout,
                                            int is_dilate, hp_se se, int radius, hp_volume* gin,
@@ -712,15 +724,19 @@ extern "C" int hp_morph3d_backward_noalloc(const hp_volume* in, const hp_volume*
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= 64) return set_error(HP_ERR_UNSUPPORTED, "device index above 63");
-  if (!g_noalloc_ptr[dev]) {
+  int32_t* arg = nullptr;
+  {
     // host code only sees a stand-in for the array; its device address is
     // looked up once per device, with that device current
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_arg);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc index array)");
-    g_noalloc_ptr[dev] = static_cast<int32_t*>(p);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_arg);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc index array)");
+      g_noalloc_ptr[dev] = static_cast<int32_t*>(p);
+    }
+    arg = g_noalloc_ptr[dev];
   }
-  int32_t* arg = g_noalloc_ptr[dev];
   cudaStream_t s = (cudaStream_t)stream;
   // every index the gather reads is written by the argmin pass first, so
   // nothing in the shared array needs clearing between calls

@@ -481,15 +481,28 @@ __global__ void __launch_bounds__(TX * TY / 4, 1)
 }
 
 // --------------------------------------------------------------------------
-// Generic single-axis pass: dst = conv_axis(src) over the global volume
-// (dense, whole volume in device memory), y[i] = sum_k g(k) x[R(i-k)].
-// src may be the job's input (any dtype, box) for the first pass.
-template <typename TIN>
-__global__ void k_axis_pass(const TIN* src, const int64_t* src_lo, const int64_t* src_dims,
-                            float* dst, int64_t n0, int64_t n1, int64_t n2, int axis,
-                            const float* __restrict__ w, int r, int64_t G0, int64_t G1,
-                            int64_t G2, int64_t off0, int64_t off1, int64_t off2) {
-  // dst covers region [off, off + n) of the global volume, densely.
+// Generic single-axis pass: dst = conv_axis(src), y[i] = sum_k g(k) x[R(i-k)],
+// over the region [off, off + n) of the global volume G (dense in dst).
+// src is a dense box (lo, dims) of the global volume: the job's input (any
+// dtype) for the first pass, a scratch volume after it. The last pass
+// stores straight into the job's output (FP32, or rounded once to f16).
+struct AxisBox {
+  int64_t lo[3], dims[3];
+};
+struct AxisTaps1 {
+  float w[kMaxTaps];
+};
+
+__device__ __forceinline__ void store_out(const DevOut& O, int64_t idx, float v) {
+  if (O.dtype == HP_F32) static_cast<float*>(O.ptr)[idx] = v;
+  else static_cast<__half*>(O.ptr)[idx] = __float2half_rn(v);
+}
+
+template <typename TIN, bool TO_OUT>
+__global__ void k_axis_pass(const TIN* __restrict__ src, const AxisBox S, float* __restrict__ dst,
+                            DevOut O, int64_t n0, int64_t n1, int64_t n2, int axis,
+                            const AxisTaps1 w, int r, int64_t G0, int64_t G1, int64_t G2,
+                            int64_t off0, int64_t off1, int64_t off2) {
   const int64_t total = n0 * n1 * n2;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
@@ -498,30 +511,18 @@ __global__ void k_axis_pass(const TIN* src, const int64_t* src_lo, const int64_t
     const int64_t Gs[3] = {G0, G1, G2};
     float acc = 0.0f;
     for (int j = 0; j <= 2 * r; ++j) {  // input coordinate increasing: k = r - j
-      int64_t s[3] = {c[0], c[1], c[2]};
-      s[axis] = reflect(c[axis] - (r - j), Gs[axis]);
-      const int64_t l0 = s[0] - src_lo[0], l1 = s[1] - src_lo[1], l2 = s[2] - src_lo[2];
+      int64_t sc[3] = {c[0], c[1], c[2]};
+      sc[axis] = reflect(c[axis] - (r - j), Gs[axis]);
+      const int64_t l0 = sc[0] - S.lo[0], l1 = sc[1] - S.lo[1], l2 = sc[2] - S.lo[2];
       float v = 0.0f;
-      if (l0 >= 0 && l0 < src_dims[0] && l1 >= 0 && l1 < src_dims[1] && l2 >= 0 && l2 < src_dims[2])
-        v = to_f32<TIN>(src[(l0 * src_dims[1] + l1) * src_dims[2] + l2]);
-      acc = fmaf(w[2 * r - j], v, acc);
+      if (l0 >= 0 && l0 < S.dims[0] && l1 >= 0 && l1 < S.dims[1] && l2 >= 0 && l2 < S.dims[2])
+        v = to_f32<TIN>(src[(l0 * S.dims[1] + l1) * S.dims[2] + l2]);
+      acc = fmaf(w.w[2 * r - j], v, acc);
     }
-    dst[q] = acc;
-  }
-}
-
-__global__ void k_copy_out(const float* src, int64_t n0, int64_t n1, int64_t n2, DevOut O,
-                           int64_t off0, int64_t off1, int64_t off2) {
-  const int64_t total = n0 * n1 * n2;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
-    const int64_t idx =
-        ((off0 + z - O.lo[0]) * O.dims[1] + (off1 + y - O.lo[1])) * O.dims[2] + (off2 + x - O.lo[2]);
-    if (O.dtype == HP_F32)
-      static_cast<float*>(O.ptr)[idx] = src[q];
+    if (TO_OUT)
+      store_out(O, ((c[0] - O.lo[0]) * O.dims[1] + (c[1] - O.lo[1])) * O.dims[2] + (c[2] - O.lo[2]), acc);
     else
-      static_cast<__half*>(O.ptr)[idx] = __float2half_rn(src[q]);
+      dst[q] = acc;
   }
 }
 
@@ -563,109 +564,114 @@ cudaError_t dispatch_zm(int r, const GaussParams& P, const CUtensorMap& map, dim
   }
 }
 
-cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
-  // Three passes x -> y -> z through two FP32 scratch volumes covering the
-  // regions each pass needs (core grown by r along the later axes, clipped
-  // to the source hull). Scratch is stream-ordered.
-  const int r = taps.r;
-  int64_t lo[3], hi[3];
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = job.core_lo[a];
-    hi[a] = job.core_hi[a];
-  }
-  // region after x pass: z and y grown to the hull of their reflected
-  // sources, x = core
-  int64_t rlo[3], rhi[3];
+// Regions of the generic three-pass path: after the x pass, z and y grown
+// to the hull of their reflected sources and x = core; after the y pass,
+// z grown and y, x = core.
+struct GenericRegions {
+  int64_t rlo[2];
+  int64_t n_x[3], n_y[3];
+};
+
+GenericRegions generic_regions(const Job& job, int r) {
+  GenericRegions g;
+  int64_t rhi[2];
   for (int a = 0; a < 2; ++a) {
-    const int64_t n = job.gdims[a];
+    const int64_t n = job.gdims[a], lo = job.core_lo[a], hi = job.core_hi[a];
     int64_t mn = n, mx = -1;
-    if (hi[a] - lo[a] + 2 * r >= 2 * n) {
+    if (hi - lo + 2 * r >= 2 * n) {
       mn = 0;
       mx = n - 1;
     } else {
-      for (int64_t c = lo[a] - r; c < hi[a] + r; ++c) {
+      for (int64_t c = lo - r; c < hi + r; ++c) {
         const int64_t sidx = reflect(c, n);
         mn = std::min(mn, sidx);
         mx = std::max(mx, sidx);
       }
     }
-    rlo[a] = mn;
+    g.rlo[a] = mn;
     rhi[a] = mx + 1;
   }
-  const int64_t n_x[3] = {rhi[0] - rlo[0], rhi[1] - rlo[1], hi[2] - lo[2]};
-  const int64_t n_y[3] = {rhi[0] - rlo[0], hi[1] - lo[1], hi[2] - lo[2]};
-  const int64_t n_z[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
-  size_t b1 = sizeof(float) * n_x[0] * n_x[1] * n_x[2];
-  size_t b2 = sizeof(float) * n_y[0] * n_y[1] * n_y[2];
-  size_t bz = sizeof(float) * n_z[0] * n_z[1] * n_z[2];
-  float *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;
-  float* dw = nullptr;
-  int64_t* dmeta = nullptr;
-  cudaError_t e;
-  if ((e = cudaMallocAsync(&t1, b1, s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync(&t2, b2, s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync(&t3, bz, s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync(&dw, sizeof(float) * 3 * kMaxTaps, s)) != cudaSuccess) return e;
-  if ((e = cudaMallocAsync(&dmeta, sizeof(int64_t) * 18, s)) != cudaSuccess) return e;
-  int64_t meta[18] = {job.in.lo[0], job.in.lo[1], job.in.lo[2], job.in.dims[0], job.in.dims[1],
-                      job.in.dims[2],
-                      rlo[0], rlo[1], lo[2], n_x[0], n_x[1], n_x[2],
-                      rlo[0], lo[1], lo[2], n_y[0], n_y[1], n_y[2]};
-  e = cudaMemcpyAsync(dmeta, meta, sizeof(meta), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dw, taps.w, sizeof(float) * 3 * kMaxTaps, cudaMemcpyHostToDevice, s);
-  // cudaMemcpyAsync from pageable memory is staged synchronously, so the
-  // host arrays above may go out of scope after return.
-  if (e == cudaSuccess) {
-    const int blk = 256;
-    auto grid_for = [&](const int64_t* n) {
-      int64_t t = n[0] * n[1] * n[2];
-      return (unsigned)std::min<int64_t>((t + blk - 1) / blk, 148 * 32);
-    };
-    const float* wz = dw;
-    const float* wy = dw + kMaxTaps;
-    const float* wx = dw + 2 * kMaxTaps;
-    switch (job.in.dtype) {
-#define HP_PASS1(T)                                                                            \
-  k_axis_pass<T><<<grid_for(n_x), blk, 0, s>>>(static_cast<const T*>(job.in.ptr), dmeta,     \
-                                               dmeta + 3, t1, n_x[0], n_x[1], n_x[2], 2, wx, r, \
-                                               job.gdims[0], job.gdims[1], job.gdims[2],        \
-                                               rlo[0], rlo[1], lo[2]);                         \
-  break;
-      case HP_U8: HP_PASS1(uint8_t)
-      case HP_U16: HP_PASS1(uint16_t)
-      case HP_F16: HP_PASS1(__half)
-      case HP_F32: HP_PASS1(float)
-#undef HP_PASS1
-    }
-    k_axis_pass<float><<<grid_for(n_y), blk, 0, s>>>(t1, dmeta + 6, dmeta + 9, t2, n_y[0], n_y[1],
-                                                     n_y[2], 1, wy, r, job.gdims[0], job.gdims[1],
-                                                     job.gdims[2], rlo[0], lo[1], lo[2]);
-    k_axis_pass<float><<<grid_for(n_z), blk, 0, s>>>(t2, dmeta + 12, dmeta + 15, t3, n_z[0],
-                                                     n_z[1], n_z[2], 0, wz, r, job.gdims[0],
-                                                     job.gdims[1], job.gdims[2], lo[0], lo[1],
-                                                     lo[2]);
-    k_copy_out<<<grid_for(n_z), blk, 0, s>>>(t3, n_z[0], n_z[1], n_z[2], job.out, lo[0], lo[1],
-                                            lo[2]);
-    e = cudaGetLastError();
+  const int64_t cx = job.core_hi[2] - job.core_lo[2], cy = job.core_hi[1] - job.core_lo[1];
+  g.n_x[0] = rhi[0] - g.rlo[0];
+  g.n_x[1] = rhi[1] - g.rlo[1];
+  g.n_x[2] = cx;
+  g.n_y[0] = g.n_x[0];
+  g.n_y[1] = cy;
+  g.n_y[2] = cx;
+  return g;
+}
+
+bool needs_generic(const Job& job, int r) {
+  return !(r >= 1 && r <= kMaxR && job.gdims[2] >= r && job.gdims[1] >= r);
+}
+
+cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
+  // Three passes x -> y -> z; the x and y passes go through two FP32
+  // scratch volumes that the caller provides in job.scratch (the z pass
+  // stores into the output). The kernels take taps and boxes by value.
+  const int r = taps.r;
+  const int64_t cz = job.core_hi[0] - job.core_lo[0], cy = job.core_hi[1] - job.core_lo[1],
+                cx = job.core_hi[2] - job.core_lo[2];
+  if (cz <= 0 || cy <= 0 || cx <= 0) return cudaSuccess;
+  const GenericRegions g = generic_regions(job, r);
+  const size_t b1 = sizeof(float) * (size_t)(g.n_x[0] * g.n_x[1] * g.n_x[2]);
+  const size_t b2 = sizeof(float) * (size_t)(g.n_y[0] * g.n_y[1] * g.n_y[2]);
+  if (!job.scratch || job.scratch_bytes < b1 + b2) return cudaErrorInvalidValue;
+  float* t1 = static_cast<float*>(job.scratch);
+  float* t2 = t1 + b1 / sizeof(float);
+  AxisTaps1 wz, wy, wx;
+  for (int k = 0; k < kMaxTaps; ++k) {
+    wz.w[k] = taps.w[0][k];
+    wy.w[k] = taps.w[1][k];
+    wx.w[k] = taps.w[2][k];
   }
-  cudaFreeAsync(t1, s);
-  cudaFreeAsync(t2, s);
-  cudaFreeAsync(t3, s);
-  cudaFreeAsync(dw, s);
-  cudaFreeAsync(dmeta, s);
-  return e;
+  const AxisBox sin{{job.in.lo[0], job.in.lo[1], job.in.lo[2]},
+                    {job.in.dims[0], job.in.dims[1], job.in.dims[2]}};
+  const AxisBox s1{{g.rlo[0], g.rlo[1], job.core_lo[2]}, {g.n_x[0], g.n_x[1], g.n_x[2]}};
+  const AxisBox s2{{g.rlo[0], job.core_lo[1], job.core_lo[2]}, {g.n_y[0], g.n_y[1], g.n_y[2]}};
+  const int blk = 256;
+  auto grid_for = [&](const int64_t* n) {
+    const int64_t t = n[0] * n[1] * n[2];
+    return (unsigned)std::min<int64_t>((t + blk - 1) / blk, (int64_t)num_sms() * 32);
+  };
+  const int64_t n_z[3] = {cz, cy, cx};
+  const int64_t G0 = job.gdims[0], G1 = job.gdims[1], G2 = job.gdims[2];
+  switch (job.in.dtype) {
+#define HP_PASS1(T)                                                                             \
+  k_axis_pass<T, false><<<grid_for(g.n_x), blk, 0, s>>>(                                       \
+      static_cast<const T*>(job.in.ptr), sin, t1, job.out, g.n_x[0], g.n_x[1], g.n_x[2], 2, wx, \
+      r, G0, G1, G2, g.rlo[0], g.rlo[1], job.core_lo[2]);                                       \
+  break;
+    case HP_U8: HP_PASS1(uint8_t)
+    case HP_U16: HP_PASS1(uint16_t)
+    case HP_F16: HP_PASS1(__half)
+    case HP_F32: HP_PASS1(float)
+#undef HP_PASS1
+    default: return cudaErrorInvalidValue;
+  }
+  k_axis_pass<float, false><<<grid_for(g.n_y), blk, 0, s>>>(
+      t1, s1, t2, job.out, g.n_y[0], g.n_y[1], g.n_y[2], 1, wy, r, G0, G1, G2, g.rlo[0],
+      job.core_lo[1], job.core_lo[2]);
+  k_axis_pass<float, true><<<grid_for(n_z), blk, 0, s>>>(
+      t2, s2, nullptr, job.out, n_z[0], n_z[1], n_z[2], 0, wz, r, G0, G1, G2, job.core_lo[0],
+      job.core_lo[1], job.core_lo[2]);
+  return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t gauss_scratch_bytes(const Job& job, int r) {
+  if (!needs_generic(job, r)) return 0;
+  const GenericRegions g = generic_regions(job, r);
+  return sizeof(float) * (size_t)(g.n_x[0] * g.n_x[1] * g.n_x[2] + g.n_y[0] * g.n_y[1] * g.n_y[2]);
+}
 
 cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s) {
   const int r = taps.r;
   // register z-march (k_gauss_zr.cu) wherever its layout rules hold
   const cudaError_t ezr = launch_gauss_zr(job, taps, s);
   if (ezr != cudaErrorNotSupported) return ezr;
-  bool tiled = r >= 1 && r <= kMaxR && job.gdims[2] >= r && job.gdims[1] >= r;
-  if (!tiled) return launch_generic(job, taps, s);
+  if (needs_generic(job, r)) return launch_generic(job, taps, s);
 
   GaussParams P;
   P.job = job;

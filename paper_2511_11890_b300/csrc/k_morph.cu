@@ -22,10 +22,12 @@
 // Min is associative and exact, so the result does not depend on tiling.
 #include <cuda_fp16.h>
 
+#include <float.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include <type_traits>
 
@@ -746,19 +748,42 @@ __global__ void k_threshold(const Job J, float t) {
 }
 }  // namespace
 
-// out = in > t, compared in the input's own precision: integers and f32
-// compare exactly against the FP32 threshold; f16 inputs against t rounded
-// to f16.
+// The largest value of the input's type that is <= t (t not NaN), returned
+// as a float, which holds it exactly for every input type. For every value
+// f of that type, f > t_below(t) exactly when f > t, so the kernel's FP32
+// comparison decides f > t without rounding t.
+float threshold_below(double t, int dtype) {
+  if (dtype == HP_U8 || dtype == HP_U16) {
+    const double top = dtype == HP_U8 ? 255.0 : 65535.0;
+    return (float)std::min(std::max(std::floor(t), -1.0), top);
+  }
+  float tf;
+  if (t >= (double)FLT_MAX) tf = std::isinf(t) ? INFINITY : FLT_MAX;
+  else if (t < -(double)FLT_MAX) tf = -INFINITY;
+  else {
+    tf = (float)t;  // nearest; step down when it rounded up
+    if ((double)tf > t) tf = std::nextafter(tf, -INFINITY);
+  }
+  if (dtype == HP_F32) return tf;
+  // float16: the largest half <= tf (hence <= t)
+  if (tf >= 65504.0f) return std::isinf(tf) ? INFINITY : 65504.0f;
+  if (tf < -65504.0f) return -INFINITY;
+  return __half2float(__float2half_rd(tf));
+}
+
+// out = in > t, decided exactly: the kernel compares the input (converted
+// to FP32 without rounding) against threshold_below(t).
 cudaError_t launch_threshold(const Job& job, double t, cudaStream_t s) {
   const int64_t n = (job.core_hi[0] - job.core_lo[0]) * (job.core_hi[1] - job.core_lo[1]) *
                     (job.core_hi[2] - job.core_lo[2]);
   if (n <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 32);
+  const float tb = threshold_below(t, job.in.dtype);
   switch (job.in.dtype) {
-    case HP_U8: k_threshold<uint8_t><<<grid, 256, 0, s>>>(job, (float)t); break;
-    case HP_U16: k_threshold<uint16_t><<<grid, 256, 0, s>>>(job, (float)t); break;
-    case HP_F16: k_threshold<__half><<<grid, 256, 0, s>>>(job, __half2float(__float2half_rn((float)t))); break;
-    case HP_F32: k_threshold<float><<<grid, 256, 0, s>>>(job, (float)t); break;
+    case HP_U8: k_threshold<uint8_t><<<grid, 256, 0, s>>>(job, tb); break;
+    case HP_U16: k_threshold<uint16_t><<<grid, 256, 0, s>>>(job, tb); break;
+    case HP_F16: k_threshold<__half><<<grid, 256, 0, s>>>(job, tb); break;
+    case HP_F32: k_threshold<float><<<grid, 256, 0, s>>>(job, tb); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

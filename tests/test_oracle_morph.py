@@ -207,3 +207,118 @@ def test_open_close_invariants(se, rad):
     assert np.array_equal(t.astype(np.int64), f.astype(np.int64) - o.astype(np.int64))
     k = np.full((6, 7, 8), 1234, np.uint16)
     assert not oracle.tophat3d(k, se, rad).any()
+
+
+# ------------------------------------------- totalOrder: signed zeros, NaN
+
+def _f32(bits):
+    return np.array(bits, np.uint32).view(np.float32).reshape(1, 1, -1)
+
+
+def _bits(a):
+    return a.view(np.uint32 if a.dtype == np.float32 else np.uint16).ravel().tolist()
+
+
+P0, N0 = 0x00000000, 0x80000000  # float32 +0, -0
+PNAN, NNAN = 0x7FC00000, 0xFFC00000
+PINF, NINF, ONE = 0x7F800000, 0xFF800000, 0x3F800000
+
+
+def test_signed_zero_order_hand_built():
+    """-0 < +0 in min and max: values worked out by hand on a 1 x 1 x 4
+    line (cube r = 1, reflect: x = 0 reads x = 0, 0, 1; x = 3 reads 2, 3, 3)."""
+    f = _f32([P0, N0, P0, P0])
+    assert _bits(oracle.erode3d(f, oracle.SE_CUBE, 1)) == [N0, N0, N0, P0]
+    assert _bits(oracle.dilate3d(f, oracle.SE_CUBE, 1)) == [P0, P0, P0, P0]
+    w = np.array([1.0, 2.0, 4.0, 8.0]).reshape(1, 1, 4)
+    # erosion: x = 0, 1, 2 route to the only -0 (x = 1); x = 3 sees +0 at
+    # x = 2, 3 (tie) and takes x = 2
+    g = oracle.morph3d_vjp(f, oracle.SE_CUBE, 1, False, w)
+    assert g.ravel().tolist() == [0.0, 7.0, 8.0, 0.0]
+    # dilation: x = 0 -> 0, x = 1 -> 0 (+0 at 0 and 2), x = 2 -> 2, x = 3 -> 2
+    g = oracle.morph3d_vjp(f, oracle.SE_CUBE, 1, True, w)
+    assert g.ravel().tolist() == [3.0, 0.0, 12.0, 0.0]
+    # float16 and float64 follow the same order
+    h = np.array([0x0000, 0x8000, 0x0000, 0x0000], np.uint16).view(np.float16).reshape(1, 1, 4)
+    assert _bits(oracle.erode3d(h, oracle.SE_BALL, 1)) == [0x8000, 0x8000, 0x8000, 0x0000]
+    d = np.array([0.0, -0.0, 0.0, 0.0]).reshape(1, 1, 4)
+    assert np.signbit(oracle.erode3d(d, oracle.SE_CUBE, 1)).ravel().tolist() == [True, True, True, False]
+
+
+def test_nan_and_inf_order_hand_built():
+    """NaN with the sign bit clear is above +inf, with it set below -inf;
+    line [1, +NaN, -inf, -NaN, +inf], cube r = 1, worked out by hand."""
+    f = _f32([ONE, PNAN, NINF, NNAN, PINF])
+    assert _bits(oracle.erode3d(f, oracle.SE_CUBE, 1)) == [ONE, NINF, NNAN, NNAN, NNAN]
+    assert _bits(oracle.dilate3d(f, oracle.SE_CUBE, 1)) == [PNAN, PNAN, PNAN, PINF, PINF]
+    # NaNs of one sign by significand field: ascending for +, descending for -
+    f = _f32([PNAN | 1, PNAN, PNAN | 1])
+    assert _bits(oracle.erode3d(f, oracle.SE_CUBE, 1)) == [PNAN, PNAN, PNAN]
+    assert _bits(oracle.dilate3d(f, oracle.SE_CUBE, 1)) == [PNAN | 1] * 3
+    f = _f32([NNAN | 1, NNAN, NNAN | 1])
+    assert _bits(oracle.erode3d(f, oracle.SE_CUBE, 1)) == [NNAN | 1] * 3
+    assert _bits(oracle.dilate3d(f, oracle.SE_CUBE, 1)) == [NNAN, NNAN, NNAN]
+    h = np.array([0x3C00, 0x7E00, 0xFC00, 0xFE00, 0x7C00], np.uint16).view(np.float16).reshape(1, 1, 5)
+    assert _bits(oracle.erode3d(h, oracle.SE_CUBE, 1)) == [0x3C00, 0xFC00, 0xFE00, 0xFE00, 0xFE00]
+    assert _bits(oracle.dilate3d(h, oracle.SE_CUBE, 1)) == [0x7E00, 0x7E00, 0x7E00, 0x7C00, 0x7C00]
+    # the subgradient routes to the source the forward copied
+    w = np.ones((1, 1, 5))
+    _, arg = oracle.morph3d_vjp(f.reshape(1, 1, 3), oracle.SE_CUBE, 1, False, w[..., :3], return_arg=True)
+    assert arg.ravel().tolist() == [0, 0, 2]
+
+
+def _f16_table():
+    """Every finite float16 value (as exact Fractions) sorted, with its bits."""
+    from fractions import Fraction
+    bits = np.arange(65536, dtype=np.uint16)
+    vals = bits.view(np.float16)
+    ok = np.isfinite(vals) & ~((bits == 0x8000))
+    return sorted((Fraction(float(v)), int(b)) for v, b in zip(vals[ok], bits[ok]))
+
+
+def _rne_f16(x, table):
+    """Round the exact rational x to float16 by brute force: nearest entry
+    of the table, ties to the even significand (bit pattern LSB 0)."""
+    import bisect
+    keys = [t[0] for t in table]
+    i = bisect.bisect_left(keys, x)
+    cands = [table[j] for j in (i - 1, i) if 0 <= j < len(table)]
+    best = min(cands, key=lambda t: (abs(t[0] - x), t[1] & 1))
+    return best[1]
+
+
+@pytest.mark.parametrize("se,rad", [(oracle.SE_CUBE, 1), (oracle.SE_BALL, 2)])
+def test_tophat_f16_is_one_rounding_of_the_exact_difference(se, rad):
+    """float16 top-hat: every voxel is the exact rational f - opening(f)
+    rounded once to float16 by a brute-force nearest-value search."""
+    from fractions import Fraction
+    table = _f16_table()
+    rng = np.random.default_rng(11)
+    # wide exponent spread, so differences lose bits when rounded
+    f = (rng.standard_normal((5, 6, 7)) * 2.0 ** rng.integers(-12, 12, (5, 6, 7))).astype(np.float16)
+    o = oracle.open3d(f, se, rad)
+    t = oracle.tophat3d(f, se, rad)
+    got = t.view(np.uint16).ravel().tolist()
+    for k, (a, b) in enumerate(zip(f.ravel(), o.ravel())):
+        want = _rne_f16(Fraction(float(a)) - Fraction(float(b)), table)
+        assert got[k] == want or (want == 0 and got[k] in (0, 0x8000)), (k, a, b)
+
+
+def test_f16_difference_rounded_through_f32_is_rounded_once():
+    """FP32 has 24 >= 2 x 11 + 2 significand bits, so rounding a float16
+    difference to FP32 and then to float16 equals rounding it once: checked
+    against the brute-force rounding on pairs across the exponent range."""
+    from fractions import Fraction
+    table = _f16_table()
+    rng = np.random.default_rng(12)
+    a = (rng.standard_normal(3000) * 2.0 ** rng.integers(-14, 15, 3000)).astype(np.float16)
+    b = (rng.standard_normal(3000) * 2.0 ** rng.integers(-14, 15, 3000)).astype(np.float16)
+    ok = np.isfinite(a.astype(np.float32) - b.astype(np.float32))
+    via32 = (a.astype(np.float32) - b.astype(np.float32)).astype(np.float16)
+    for x, y, v in zip(a[ok], b[ok], via32[ok]):
+        ex = Fraction(float(x)) - Fraction(float(y))
+        if abs(ex) > 65504:
+            continue
+        want = _rne_f16(ex, table)
+        got = int(np.array(v).view(np.uint16))
+        assert got == want or (want == 0 and got in (0, 0x8000))

@@ -24,7 +24,9 @@
  *     normalised in FP64 and rounded once to FP32.
  *   - Erosion takes the min over the structuring element B of f(p + o),
  *     dilation the max of f(p - o); B is a cube of half-width radius or the
- *     digital ball dz^2 + dy^2 + dx^2 <= radius^2. Morphology is exact.
+ *     digital ball dz^2 + dy^2 + dx^2 <= radius^2. Morphology is exact and
+ *     orders floating-point values by IEEE 754 totalOrder (-0 < +0; a NaN
+ *     with the sign bit clear above +inf, with it set below -inf).
  *
  * Execution mode follows where the volumes live:
  *   - HP_DEVICE in and out: the data stays in device memory. The call
@@ -126,7 +128,10 @@ int hp_get_memory_budget(size_t* bytes);
  * smoothing and derivative features). order = {oz, oy, ox}, each in
  * {0, 1, 2}; NULL means {0, 0, 0}. truncate <= 0 selects 3.0. Input dtype
  * u8/u16/f16/f32; output dtype f32 or f16 (rounded to nearest even once).
- * Radius up to 32. */
+ * Radius up to 32. Radii above 12 (and volumes thinner than the radius in x
+ * or y) take a three-pass path with two FP32 scratch volumes (at most 8
+ * bytes per voxel of the input, or of each brick's input box out of core),
+ * counted against the memory budget. */
 int hp_gaussian3d(const hp_volume* in, hp_volume* out, double sigma, double truncate,
                   const int order[3], void* stream);
 

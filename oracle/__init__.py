@@ -69,6 +69,8 @@ def _load():
         lib.orc_gaussian3d_adjoint.argtypes = [vp, p3, d, d, vp, vp]
         lib.orc_filterbank3d_vjp.argtypes = [vp, i, p3, vp, vp, i, d, vp, vp]
         lib.orc_morph3d_vjp.argtypes = [vp, i, p3, i, i, i, vp, vp, vp]
+        lib.orc_box_sums.argtypes = [vp, i, p3, i, vp, vp]
+        lib.orc_threshold_box.argtypes = [vp, i, p3, i, i, d, d, vp, vp]
         _lib = lib
     return _lib
 
@@ -205,6 +207,57 @@ def threshold_local(f: np.ndarray, sigma: float, offset: float = 0.0):
     within the Gaussian's error bar of T) from those it may not."""
     t = gaussian3d(f, sigma) - offset
     return (f.astype(np.float64) > t).astype(np.uint8), t
+
+
+LOCAL_MEAN, LOCAL_NIBLACK, LOCAL_SAUVOLA = 0, 1, 2
+
+
+def box_sums(f: np.ndarray, w: int):
+    """FP64 window sums of f and f^2 over the (2w+1)^3 cube, reflect
+    boundary, accumulated x then y then z in increasing source coordinate."""
+    f, dt = _in(f)
+    s1 = np.empty(f.shape, np.float64)
+    s2 = np.empty(f.shape, np.float64)
+    _check(_load().orc_box_sums(f.ctypes.data, dt, _v3(f.shape), int(w), s1.ctypes.data,
+                                s2.ctypes.data))
+    return s1, s2
+
+
+def threshold_box(f: np.ndarray, method: int, w: int, k: float = 0.0, c: float = 0.0,
+                  return_threshold: bool = False):
+    """Local threshold over a (2w+1)^3 box window (Sec. III-C threshold
+    algorithms: mean, Niblack, Sauvola), decided in FP64: u8 = f > T with
+    T = m - c (mean), m + k s (Niblack) or m (1 + k (s / c - 1)) (Sauvola,
+    c = R), m and s the window mean and standard deviation."""
+    f, dt = _in(f)
+    out = np.empty(f.shape, np.uint8)
+    thr = np.empty(f.shape, np.float64) if return_threshold else None
+    _check(_load().orc_threshold_box(f.ctypes.data, dt, _v3(f.shape), int(method), int(w),
+                                     float(k), float(c), out.ctypes.data,
+                                     thr.ctypes.data if return_threshold else None))
+    return (out, thr) if return_threshold else out
+
+
+HESSIAN_ORDERS = ((2, 0, 0), (0, 2, 0), (0, 0, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1))
+
+
+def hessian3d(f: np.ndarray, sigma: float):
+    """The six distinct entries of the Hessian of the Gaussian-smoothed
+    volume (Sec. III-C "Hessian" texture features), FP64, in the order
+    Dzz, Dyy, Dxx, Dzy, Dzx, Dyx: each the Gaussian derivative filter of
+    orders (oz, oy, ox) summing to 2."""
+    return [gaussian3d(f, sigma, o) for o in HESSIAN_ORDERS]
+
+
+def hessian_eigenvalues(f: np.ndarray, sigma: float):
+    """Eigenvalues of the symmetric 3x3 Hessian per voxel, ascending
+    (l1 <= l2 <= l3), in FP64: the matrix assembled from hessian3d and
+    numpy.linalg.eigvalsh (LAPACK's symmetric eigensolver) as the step."""
+    zz, yy, xx, zy, zx, yx = hessian3d(f, sigma)
+    h = np.stack([np.stack([zz, zy, zx], -1), np.stack([zy, yy, yx], -1),
+                  np.stack([zx, yx, xx], -1)], -2)
+    ev = np.linalg.eigvalsh(h)
+    return [np.ascontiguousarray(ev[..., i]) for i in range(3)]
 
 
 def threshold(f: np.ndarray, t: float = 0.5) -> np.ndarray:

@@ -504,3 +504,97 @@ int orc_morph3d_vjp(const void* in, int dtype, const int64_t dims[3], int se, in
       }
   return ORC_OK;
 }
+
+/* ------------------------------------------------ box statistics, thresholds */
+
+/* Local sums over the cube window of half-width w with reflect boundary
+ * (Sec. III-C local thresholds): s1[p] = sum f(R(p + o)), s2[p] = sum
+ * f(R(p + o))^2 over |o|_inf <= w, whole volume. Accumulated separably in
+ * FP64, x then y then z, each 1D window in increasing source coordinate
+ * (exact for u8 / u16 input, whose sums stay below 2^53). */
+int orc_box_sums(const void* in, int dtype, const int64_t d[3], int w, double* s1, double* s2) {
+  if (dtype_size(dtype) == 0 || w < 0) return ORC_ERR_ARG;
+  int64_t nv = d[0] * d[1] * d[2];
+  double* a1 = (double*)malloc(sizeof(double) * (size_t)nv);
+  double* a2 = (double*)malloc(sizeof(double) * (size_t)nv);
+  double* b1 = (double*)malloc(sizeof(double) * (size_t)nv);
+  double* b2 = (double*)malloc(sizeof(double) * (size_t)nv);
+  int rc = ORC_OK;
+  if (!a1 || !a2 || !b1 || !b2) { rc = ORC_ERR_NOMEM; goto done; }
+  /* x */
+  for (int64_t z = 0; z < d[0]; ++z)
+    for (int64_t y = 0; y < d[1]; ++y)
+      for (int64_t x = 0; x < d[2]; ++x) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = -w; k <= w; ++k) {
+          double v = load_elem(in, dtype, (z * d[1] + y) * d[2] + orc_reflect(x + k, d[2]));
+          t1 += v;
+          t2 += v * v;
+        }
+        a1[(z * d[1] + y) * d[2] + x] = t1;
+        a2[(z * d[1] + y) * d[2] + x] = t2;
+      }
+  /* y */
+  for (int64_t z = 0; z < d[0]; ++z)
+    for (int64_t y = 0; y < d[1]; ++y)
+      for (int64_t x = 0; x < d[2]; ++x) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = -w; k <= w; ++k) {
+          int64_t q = (z * d[1] + orc_reflect(y + k, d[1])) * d[2] + x;
+          t1 += a1[q];
+          t2 += a2[q];
+        }
+        b1[(z * d[1] + y) * d[2] + x] = t1;
+        b2[(z * d[1] + y) * d[2] + x] = t2;
+      }
+  /* z */
+  for (int64_t z = 0; z < d[0]; ++z)
+    for (int64_t y = 0; y < d[1]; ++y)
+      for (int64_t x = 0; x < d[2]; ++x) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = -w; k <= w; ++k) {
+          int64_t q = (orc_reflect(z + k, d[0]) * d[1] + y) * d[2] + x;
+          t1 += b1[q];
+          t2 += b2[q];
+        }
+        s1[(z * d[1] + y) * d[2] + x] = t1;
+        s2[(z * d[1] + y) * d[2] + x] = t2;
+      }
+done:
+  free(a1); free(a2); free(b1); free(b2);
+  return rc;
+}
+
+enum { ORC_LOCAL_MEAN = 0, ORC_LOCAL_NIBLACK = 1, ORC_LOCAL_SAUVOLA = 2 };
+
+/* Local threshold from the window statistics, all in FP64 in this order
+ * (Sec. III-C threshold algorithms):
+ *   m = s1 / N,  v = max(s2 / N - m * m, 0),  s = sqrt(v),  N = (2w + 1)^3;
+ *   mean:    T = m - c
+ *   Niblack: T = m + k * s
+ *   Sauvola: T = m * (1 + k * (s / c - 1))     (c = the dynamic range R)
+ * and out = f > T (u8). Also writes T when `thr` is not NULL. */
+int orc_threshold_box(const void* in, int dtype, const int64_t d[3], int method, int w, double k,
+                      double c, uint8_t* out, double* thr) {
+  if (method < ORC_LOCAL_MEAN || method > ORC_LOCAL_SAUVOLA) return ORC_ERR_ARG;
+  int64_t nv = d[0] * d[1] * d[2];
+  double* s1 = (double*)malloc(sizeof(double) * (size_t)nv);
+  double* s2 = (double*)malloc(sizeof(double) * (size_t)nv);
+  if (!s1 || !s2) { free(s1); free(s2); return ORC_ERR_NOMEM; }
+  int rc = orc_box_sums(in, dtype, d, w, s1, s2);
+  double n = (double)(2 * w + 1) * (double)(2 * w + 1) * (double)(2 * w + 1);
+  for (int64_t q = 0; rc == ORC_OK && q < nv; ++q) {
+    double m = s1[q] / n;
+    double v = s2[q] / n - m * m;
+    if (v < 0.0) v = 0.0;
+    double s = sqrt(v);
+    double t;
+    if (method == ORC_LOCAL_MEAN) t = m - c;
+    else if (method == ORC_LOCAL_NIBLACK) t = m + k * s;
+    else t = m * (1.0 + k * (s / c - 1.0));
+    out[q] = load_elem(in, dtype, q) > t ? 1 : 0;
+    if (thr) thr[q] = t;
+  }
+  free(s1); free(s2);
+  return rc;
+}

@@ -77,6 +77,8 @@ typedef enum { HP_U8 = 0, HP_U16 = 1, HP_F16 = 2, HP_F32 = 3 } hp_dtype;
 typedef enum { HP_HOST = 0, HP_DEVICE = 1 } hp_loc;
 typedef enum { HP_SE_CUBE = 0, HP_SE_BALL = 1 } hp_se;
 typedef enum { HP_FILTER_G = 0, HP_FILTER_GM = 1, HP_FILTER_LOG = 2 } hp_filter_kind;
+typedef enum { HP_LOCAL_MEAN = 0, HP_LOCAL_NIBLACK = 1, HP_LOCAL_SAUVOLA = 2 } hp_local_method;
+typedef enum { HP_HESSIAN_COMPONENTS = 0, HP_HESSIAN_EIGENVALUES = 1 } hp_hessian_output;
 
 /* Opaque, non-owning view of a dense C-order volume. */
 typedef struct hp_volume hp_volume;
@@ -136,10 +138,18 @@ int hp_gaussian3d(const hp_volume* in, hp_volume* out, double sigma, double trun
                   const int order[3], void* stream);
 
 /* Multi-sigma filter bank: n outputs, outs[i] holds filter f[i]. All outputs
- * have the input's extents and dtype f16 or f32. Device mode runs one
- * persistent, CUDA-graph-captured launch over a work list of
- * (brick, tile, sigma) items; the launch plan (graph + work list) is cached
- * per shape, filter set, brick set and buffer addresses. truncate is 3.0. */
+ * have the input's extents, its location, and one dtype, f16 or f32.
+ * truncate is 3.0; radii 1..12; at most 8 distinct sigmas; each
+ * (kind, sigma) at most once.
+ *   - Device mode runs one persistent, CUDA-graph-captured launch over a
+ *     work list of (brick, tile, sigma) items; the launch plan (graph + work
+ *     list) is cached per shape, filter set, brick set and buffer addresses.
+ *   - Host mode (Sec. III-D) streams Z slabs (halo = the largest radius)
+ *     through the device under the memory budget: each slab's input crosses
+ *     the host link once for all n outputs, and the bank kernels run on it
+ *     with a per-slab work list (no graph, nothing cached). Results equal
+ *     device mode bit for bit. HP_ERR_BUDGET when one plane with its halo
+ *     and outputs does not fit. */
 int hp_filterbank3d(const hp_volume* in, hp_volume* const* outs, const hp_filter* f, int n,
                     void* stream);
 /* As hp_filterbank3d, with the work list built over the given bricks
@@ -183,6 +193,36 @@ int hp_unsharp3d(const hp_volume* in, hp_volume* out, double sigma, double amoun
  * HP_ERR_UNSUPPORTED for host volumes. */
 int hp_threshold_local3d(const hp_volume* in, hp_volume* out, double sigma, double offset,
                          void* stream);
+
+/* Box-window local threshold (Sec. III-C, threshold algorithms: mean,
+ * Niblack, Sauvola): out (u8) = in > T, with m and s the mean and standard
+ * deviation of the input over the (2 radius + 1)^3 cube around each voxel
+ * (reflect boundary) and
+ *   HP_LOCAL_MEAN:    T = m - c
+ *   HP_LOCAL_NIBLACK: T = m + k s
+ *   HP_LOCAL_SAUVOLA: T = m (1 + k (s / c - 1))   (c = the dynamic range R)
+ * Window sums run separably (x, then y, then z, each in increasing source
+ * coordinate): exactly in integers for u8 / u16 input, in FP64 for f16 / f32;
+ * m = S1/N, s = sqrt(max(S2/N - m^2, 0)), T and the comparison are FP64, one
+ * rounded operation at a time, so the decision is reproducible bit for bit.
+ * radius in [0, 15]; c > 0 for Sauvola. Host volumes run out of core (halo
+ * = radius); device volumes use library scratch of 24 (integer input) or 32
+ * (floating-point input) bytes per voxel. */
+int hp_threshold_box3d(const hp_volume* in, hp_volume* out, int method, int radius, double k,
+                       double c, void* stream);
+
+/* Hessian texture features (Sec. III-C, "Hessian"): the second derivatives
+ * of the Gaussian-smoothed volume, each the hp_gaussian3d derivative filter
+ * whose orders sum to 2 (truncate 3, reflect, FP32).
+ *   HP_HESSIAN_COMPONENTS: n = 6 outputs Dzz, Dyy, Dxx, Dzy, Dzx, Dyx;
+ *   HP_HESSIAN_EIGENVALUES: n = 3 outputs, the eigenvalues of the symmetric
+ *     3x3 Hessian per voxel in ascending order, solved in FP32 in closed form
+ *     (trigonometric solution of the characteristic cubic); the components
+ *     live in library scratch (24 bytes per voxel).
+ * Outputs f32 or f16 (one dtype), the input's extents and location; host
+ * volumes run out of core. */
+int hp_hessian3d(const hp_volume* in, hp_volume* const* outs, int what, double sigma,
+                 void* stream);
 
 /* Global threshold (Sec. III-C, threshold algorithms): out (u8) = in > t,
  * decided exactly for every input dtype: the kernels compare against the
@@ -232,6 +272,29 @@ int hp_morph3d_backward(const hp_volume* in, const hp_volume* gout, int is_dilat
 int hp_morph3d_backward_noalloc(const hp_volume* in, const hp_volume* gout, int is_dilate,
                                 hp_se se, int radius, hp_volume* gin, int accumulate,
                                 void* stream);
+
+/* Devices that host-mode (out-of-core) calls spread their bricks over
+ * (Sec. III-D step 3 and Sec. V: round-robin chunk scheduling without
+ * inter-GPU communication): brick k of a call runs on devices[k mod n], each
+ * device with its own streams and stage buffers, no peer access and no
+ * collective. The budget (hp_set_memory_budget, or 0.8 x that device's free
+ * memory) applies per device; entries naming the same device share it.
+ * n = 0 (the default) means the current device only. Device-mode calls are
+ * not affected. Process-wide; HP_ERR_INVALID_ARG for an index that is not a
+ * device. hp_get_devices writes up to max_n entries and the count. */
+int hp_set_devices(const int* devices, int n);
+int hp_get_devices(int* devices, int max_n, int* n);
+
+/* Brick shard of this process for host-mode calls: of the planned bricks
+ * (in the planner's order) only those with index i mod world == rank run,
+ * and only their core boxes of the output are written; the rest of the
+ * output is left as it was. Processes that run the same call with
+ * rank = 0..world-1 together write every output voxel exactly once, with
+ * no communication between them. The planned brick list depends on the
+ * budget, so a shard with world > 1 requires an explicit
+ * hp_set_memory_budget (else HP_ERR_INVALID_ARG); rank 0 of world 1 (the
+ * default) runs every brick. Process-wide. */
+int hp_set_brick_shard(int rank, int world);
 
 /* Chunk planner (Sec. III-D step 2), host only, no device work. Splits an
  * (nz, ny, nx) volume into bricks whose core boxes tile it exactly; box i's

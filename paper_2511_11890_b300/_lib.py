@@ -20,14 +20,18 @@ HP_U8, HP_U16, HP_F16, HP_F32 = 0, 1, 2, 3
 HP_HOST, HP_DEVICE = 0, 1
 HP_SE_CUBE, HP_SE_BALL = 0, 1
 HP_FILTER_G, HP_FILTER_GM, HP_FILTER_LOG = 0, 1, 2
+HP_LOCAL_MEAN, HP_LOCAL_NIBLACK, HP_LOCAL_SAUVOLA = 0, 1, 2
+HP_HESSIAN_COMPONENTS, HP_HESSIAN_EIGENVALUES = 0, 1
 
 # Every entry point declared in include/hp.h.
 EXPORTS = [
     "hp_volume_create", "hp_volume_destroy", "hp_set_memory_budget", "hp_get_memory_budget",
     "hp_gaussian3d", "hp_filterbank3d", "hp_filterbank3d_bricks", "hp_erode3d", "hp_dilate3d",
     "hp_open3d", "hp_close3d", "hp_tophat3d", "hp_unsharp3d", "hp_threshold_local3d",
-    "hp_threshold3d", "hp_filterbank3d_adjoint", "hp_morph3d_backward",
-    "hp_morph3d_backward_noalloc", "hp_plan_bricks",
+    "hp_threshold3d", "hp_threshold_box3d", "hp_hessian3d", "hp_filterbank3d_adjoint",
+    "hp_morph3d_backward",
+    "hp_morph3d_backward_noalloc", "hp_set_devices", "hp_get_devices", "hp_set_brick_shard",
+    "hp_plan_bricks",
     "hp_stream_status", "hp_selftest_wait_timeout", "hp_release_cache", "hp_get_stats", "hp_last_error", "hp_version",
 ]
 
@@ -77,9 +81,14 @@ def _load() -> ctypes.CDLL:
         "hp_unsharp3d": [vp, vp, d, d, vp],
         "hp_threshold_local3d": [vp, vp, d, d, vp],
         "hp_threshold3d": [vp, vp, d, vp],
+        "hp_threshold_box3d": [vp, vp, i, i, d, d, vp],
+        "hp_hessian3d": [vp, pvp, i, d, vp],
         "hp_filterbank3d_adjoint": [vp, pvp, ctypes.POINTER(hp_filter), i, vp, vp],
         "hp_morph3d_backward": [vp, vp, i, i, i, vp, i, vp],
         "hp_morph3d_backward_noalloc": [vp, vp, i, i, i, vp, i, vp],
+        "hp_set_devices": [ctypes.POINTER(i), i],
+        "hp_get_devices": [ctypes.POINTER(i), i, ctypes.POINTER(i)],
+        "hp_set_brick_shard": [i, i],
         "hp_plan_bricks": [i64, i64, i64, i, sz, sz, sz, i, i, ctypes.POINTER(hp_box),
                            ctypes.POINTER(hp_box), i, ctypes.POINTER(i)],
         "hp_stream_status": [vp],

@@ -162,6 +162,42 @@ def threshold3d(x, t: float = 0.5, out=None, stream=None):
     return out
 
 
+LOCAL = {"mean": _lib.HP_LOCAL_MEAN, "niblack": _lib.HP_LOCAL_NIBLACK,
+         "sauvola": _lib.HP_LOCAL_SAUVOLA}
+
+
+def threshold_box3d(x, method="niblack", radius: int = 7, k: float = 0.2, c: float = 0.0,
+                    out=None, stream=None):
+    """Box-window local threshold: u8 = x > T, T from the window mean m and
+    standard deviation s: 'mean' m - c, 'niblack' m + k s, 'sauvola'
+    m (1 + k (s / c - 1)) (c = R)."""
+    if out is None:
+        out = _empty_like(x, HP_U8)
+    with _ctx(x), _View(x) as vi, _View(out) as vo:
+        check(lib.hp_threshold_box3d(vi, vo, int(LOCAL.get(method, method)), int(radius), float(k),
+                                     float(c), _stream(x, stream)))
+    return out
+
+
+def hessian3d(x, sigma: float, eigenvalues: bool = False, outs=None, out_dtype: int = HP_F32,
+              stream=None):
+    """Hessian features: the six components (Dzz, Dyy, Dxx, Dzy, Dzx, Dyx),
+    or with eigenvalues=True the three ascending eigenvalues per voxel."""
+    n = 3 if eigenvalues else 6
+    if outs is None:
+        outs = [_empty_like(x, out_dtype) for _ in range(n)]
+    views = [_View(o) for o in outs]
+    try:
+        handles = (ctypes.c_void_p * len(outs))(*[v.h.value for v in views])
+        what = _lib.HP_HESSIAN_EIGENVALUES if eigenvalues else _lib.HP_HESSIAN_COMPONENTS
+        with _ctx(x), _View(x) as vi:
+            check(lib.hp_hessian3d(vi, handles, what, float(sigma), _stream(x, stream)))
+    finally:
+        for v in views:
+            v.__exit__()
+    return outs
+
+
 def _filters(filters):
     arr = (hp_filter * len(filters))()
     for i, (k, s) in enumerate(filters):
@@ -252,6 +288,28 @@ def shard_bricks(n: int, rank: int, world: int):
     if world < 1 or not 0 <= rank < world:
         raise ValueError("rank must be in [0, world)")
     return list(range(rank, int(n), world))
+
+
+def set_devices(devices):
+    """Devices host-mode (out-of-core) calls deal their bricks over, round
+    robin (brick k on devices[k mod n]); [] = the current device only."""
+    devs = [int(d) for d in devices]
+    arr = (ctypes.c_int * max(1, len(devs)))(*devs)
+    check(lib.hp_set_devices(arr, len(devs)))
+
+
+def get_devices() -> list:
+    n = ctypes.c_int(0)
+    check(lib.hp_get_devices(None, 0, ctypes.byref(n)))
+    arr = (ctypes.c_int * max(1, n.value))()
+    check(lib.hp_get_devices(arr, n.value, ctypes.byref(n)))
+    return list(arr[:n.value])
+
+
+def set_brick_shard(rank: int, world: int):
+    """Host-mode calls of this process run only bricks i with i mod world ==
+    rank (and write only their cores); (0, 1) runs every brick."""
+    check(lib.hp_set_brick_shard(int(rank), int(world)))
 
 
 def set_memory_budget(nbytes: int):

@@ -337,7 +337,7 @@ static size_t stage_bytes(const int64_t ext[3], const int64_t n[3], int halo, si
 
 // Plan bricks; returns HP_OK or HP_ERR_BUDGET / HP_ERR_INVALID_ARG.
 static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t scr_b,
-                size_t budget, int stages, int min_bricks, std::vector<Brick>* out) {
+                size_t budget, int stages, int min_bricks, bool z_only, std::vector<Brick>* out) {
   if (n[0] < 1 || n[1] < 1 || n[2] < 1 || halo < 0 || stages < 1)
     return set_error(HP_ERR_INVALID_ARG, "plan: bad extents, halo or stages");
   const size_t per = budget / (size_t)stages;
@@ -345,7 +345,7 @@ static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t 
   // Prefer Z slabs (contiguous planes); split y, then x, only when one
   // plane plus halos does not fit.
   int axis_split = -1;
-  for (int a = 0; a < 3 && axis_split < 0; ++a) {
+  for (int a = 0; a < (z_only ? 1 : 3) && axis_split < 0; ++a) {
     for (int b = 0; b < a; ++b) ext[b] = 1;
     for (int b = a; b < 3; ++b) ext[b] = n[b];
     ext[a] = 1;
@@ -396,13 +396,29 @@ static int plan(const int64_t n[3], int halo, size_t in_b, size_t out_b, size_t 
 struct Op {
   int halo;
   int out_dtype;
+  int nout = 1;         // outputs per voxel (filter bank: one per filter)
+  bool z_only = false;  // plan Z slabs only (whole x/y planes per brick)
   // planning bound of the kernel scratch, bytes per voxel of the input box
   size_t scratch_per_in_voxel = 0;
   // exact scratch bytes of one job (null: none)
   std::function<size_t(const Job&)> scratch_bytes;
-  // enqueue the op for one job (job.scratch set when scratch_bytes > 0)
-  std::function<cudaError_t(const Job&, cudaStream_t)> launch;
+  // host-mode bricks also get a page-locked host buffer of the same size
+  bool host_scratch = false;
+  // enqueue the op for one job: job.out is output 0, outs[k] output k (each
+  // a dense box like job.out); job.scratch is set when scratch_bytes > 0.
+  // Returns an hp_status.
+  std::function<int(const Job&, void* const* outs, cudaStream_t)> launch;
 };
+
+// Wraps a cudaError_t launcher as an Op launch.
+static int launched(cudaError_t e) { return e == cudaSuccess ? HP_OK : cuda_fail(e, "kernel launch"); }
+
+// Out-of-core placement (Sec. III-D step 3 and Sec. V: round-robin chunk
+// scheduling without inter-GPU communication): the devices host-mode calls
+// spread their bricks over, and the shard of the brick list this process
+// executes.
+static std::vector<int> g_devices;  // empty: the current device
+static int g_shard_rank = 0, g_shard_world = 1;
 
 static bool is_pinned(const void* p) {
   cudaPointerAttributes at;
@@ -492,19 +508,64 @@ struct Faults {
   bool fail_copy() { return memcpy_at >= 0 && copies++ == memcpy_at; }
 };
 
-static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
+// Host-mode execution: plan halo-padded bricks for the budget, keep the
+// bricks of this process's shard (i mod world == rank), deal them
+// round-robin over the device list (brick k of the shard to device
+// k mod ndev), and stream each through one of S stages of its device: H2D
+// of the halo box, the kernels, D2H of the core box(es). Each device has its
+// own streams and buffers; no device talks to another. Slots that name the
+// same device share its budget.
+static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
   auto t0 = std::chrono::steady_clock::now();
   Faults faults;
   const int64_t n[3] = {in->nz, in->ny, in->nx};
   const size_t ies = dtype_size(in->dtype), oes = dtype_size(op.out_dtype);
-  size_t budget = 0;
-  int st = effective_budget(&budget);
-  if (st != HP_OK) return st;
+  const int nout = op.nout;
+  int caller_dev = 0;
+  cudaError_t ce = cudaGetDevice(&caller_dev);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+  std::vector<int> devs;
+  int rank = 0, world = 1;
+  size_t user_budget = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    devs = g_devices;
+    rank = g_shard_rank;
+    world = g_shard_world;
+  }
+  user_budget = budget_setting();
+  if (devs.empty()) devs.push_back(caller_dev);
+  const int ndev = (int)devs.size();
+  // per-slot budget: each device's budget split over the slots naming it
+  size_t budget = SIZE_MAX;
+  for (int k = 0; k < ndev; ++k) {
+    int same = 0;
+    for (int d : devs) same += d == devs[k];
+    size_t b = user_budget;
+    if (b == 0) {
+      size_t fr = 0, tot = 0;
+      if ((ce = cudaSetDevice(devs[k])) != cudaSuccess || (ce = cudaMemGetInfo(&fr, &tot)) != cudaSuccess) {
+        cudaSetDevice(caller_dev);
+        return cuda_fail(ce, "cudaMemGetInfo");
+      }
+      b = (size_t)(0.8 * (double)fr);
+    }
+    budget = std::min(budget, b / (size_t)same);
+  }
+  cudaSetDevice(caller_dev);
   if (faults.budget) budget = 1;
+  if (world > 1 && user_budget == 0)
+    return set_error(HP_ERR_INVALID_ARG,
+                     "a brick shard needs an explicit memory budget (hp_set_memory_budget), so "
+                     "that every process plans the same bricks");
   const int S = 3;
-  std::vector<Brick> bricks;
-  st = plan(n, op.halo, ies, oes, op.scratch_per_in_voxel, budget, S, 8, &bricks);
+  std::vector<Brick> all;
+  int st = plan(n, op.halo, ies, oes * nout, op.scratch_per_in_voxel, budget, S, 8 * ndev * world,
+                op.z_only, &all);
   if (st != HP_OK) return st;
+  std::vector<Brick> bricks;  // this process's shard
+  for (size_t i = 0; i < all.size(); ++i)
+    if ((int)(i % (size_t)world) == rank) bricks.push_back(all[i]);
 
   const int64_t vol_lo[3] = {0, 0, 0};
   // the job of brick b with stage buffers din / dout
@@ -533,60 +594,70 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     max_out = std::max(max_out, vo);
     if (op.scratch_bytes) max_scr = std::max(max_scr, op.scratch_bytes(brick_job(b, nullptr, nullptr)));
   }
-  const int nst = (int)std::min<size_t>(S, bricks.size());
-  const bool in_pinned = is_pinned(in->data), out_pinned = is_pinned(out->data);
+  const bool in_pinned = is_pinned(in->data);
+  bool out_pinned = true;
+  for (int k = 0; k < nout; ++k) out_pinned = out_pinned && is_pinned(outs[k]->data);
 
   struct Stage {
+    int dev = 0;
     void* din = nullptr;
-    void* dout = nullptr;
+    void* dout = nullptr;  // nout core boxes of max_out bytes
     void* dscr = nullptr;
+    void* hscr = nullptr;
     void* hin = nullptr;
     void* hout = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
     int brick = -1;
   };
-  std::vector<Stage> sg(nst);
+  // slot k (device devs[k]) owns stages [k * nst, (k + 1) * nst)
+  const int per_slot = (int)((bricks.size() + ndev - 1) / ndev);
+  const int nst = std::max(1, std::min(S, per_slot));
+  const int nslot = bricks.empty() ? 0 : std::min<int>(ndev, (int)bricks.size());
+  std::vector<Stage> sg((size_t)nslot * nst);
   uint64_t h2d = 0, d2h = 0;
   size_t pinned = 0;
   int rc = HP_OK;
-  int64_t dev_bytes = 0;
   auto fail = [&](int code, const std::string& m) {
     if (rc == HP_OK) rc = set_error(code, m);
   };
   auto cfail = [&](cudaError_t e, const char* what) {
     if (rc == HP_OK) rc = cuda_fail(e, what);
   };
-  for (auto& x : sg) {
+  for (size_t i = 0; i < sg.size(); ++i) {
+    Stage& x = sg[i];
+    x.dev = devs[i / nst];
     if (rc != HP_OK) break;
     cudaError_t e;
+    if ((e = cudaSetDevice(x.dev)) != cudaSuccess) { cfail(e, "cudaSetDevice"); break; }
     if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
-    if ((e = cudaMalloc(&x.din, max_in)) != cudaSuccess) { cfail(e, "cudaMalloc(in stage)"); break; }
-    dev_bytes += (int64_t)max_in;
+    if ((e = cudaMalloc(&x.din, max_in)) != cudaSuccess) { cfail(e, "cudaMalloc(in stage)"); x.din = nullptr; break; }
     track_alloc((int64_t)max_in);
     if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
-    if ((e = cudaMalloc(&x.dout, max_out)) != cudaSuccess) { cfail(e, "cudaMalloc(out stage)"); break; }
-    dev_bytes += (int64_t)max_out;
-    track_alloc((int64_t)max_out);
+    if ((e = cudaMalloc(&x.dout, max_out * nout)) != cudaSuccess) { cfail(e, "cudaMalloc(out stage)"); x.dout = nullptr; break; }
+    track_alloc((int64_t)(max_out * nout));
     if (max_scr > 0) {
       if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
-      if ((e = cudaMalloc(&x.dscr, max_scr)) != cudaSuccess) { cfail(e, "cudaMalloc(scratch stage)"); break; }
-      dev_bytes += (int64_t)max_scr;
+      if ((e = cudaMalloc(&x.dscr, max_scr)) != cudaSuccess) { cfail(e, "cudaMalloc(scratch stage)"); x.dscr = nullptr; break; }
       track_alloc((int64_t)max_scr);
+      if (op.host_scratch) {
+        if ((e = cudaHostAlloc(&x.hscr, max_scr, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); x.hscr = nullptr; break; }
+        pinned += max_scr;
+      }
     }
     if (!in_pinned) {
-      if ((e = cudaHostAlloc(&x.hin, max_in, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); break; }
+      if ((e = cudaHostAlloc(&x.hin, max_in, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); x.hin = nullptr; break; }
       pinned += max_in;
     }
     if (!out_pinned) {
-      if ((e = cudaHostAlloc(&x.hout, max_out, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); break; }
-      pinned += max_out;
+      if ((e = cudaHostAlloc(&x.hout, max_out * nout, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); x.hout = nullptr; break; }
+      pinned += max_out * nout;
     }
-    if ((e = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking)) != cudaSuccess) { cfail(e, "cudaStreamCreate"); break; }
-    if ((e = cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming)) != cudaSuccess) { cfail(e, "cudaEventCreate"); break; }
+    if ((e = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking)) != cudaSuccess) { cfail(e, "cudaStreamCreate"); x.s = nullptr; break; }
+    if ((e = cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming)) != cudaSuccess) { cfail(e, "cudaEventCreate"); x.ev = nullptr; break; }
   }
 
-  // completes brick b of stage x: copy its staged output to the user array
+  // completes the brick of stage x: copy its staged outputs to the user arrays
   auto retire = [&](Stage& x) {
     if (x.brick < 0) return;
     cudaError_t e = cudaEventSynchronize(x.ev);
@@ -595,20 +666,26 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
       const Brick& b = bricks[x.brick];
       const int64_t cd[3] = {b.core.hi[0] - b.core.lo[0], b.core.hi[1] - b.core.lo[1],
                              b.core.hi[2] - b.core.lo[2]};
-      host_copy_box(out->data, x.hout, oes, cd, b.core.lo, n, vol_lo, b.core.lo, b.core.hi);
+      for (int k = 0; k < nout; ++k)
+        host_copy_box(outs[k]->data, (const char*)x.hout + k * max_out, oes, cd, b.core.lo, n,
+                      vol_lo, b.core.lo, b.core.hi);
     }
     x.brick = -1;
   };
 
+  std::vector<int> next_stage(nslot, 0);
   for (size_t i = 0; i < bricks.size() && rc == HP_OK; ++i) {
-    Stage& x = sg[i % nst];
+    const int slot = (int)(i % (size_t)nslot);
+    Stage& x = sg[(size_t)slot * nst + (next_stage[slot]++ % nst)];
     retire(x);
     if (rc != HP_OK) break;
+    cudaError_t e;
+    if ((e = cudaSetDevice(x.dev)) != cudaSuccess) { cfail(e, "cudaSetDevice"); break; }
     const Brick& b = bricks[i];
     const int64_t idims[3] = {b.in.hi[0] - b.in.lo[0], b.in.hi[1] - b.in.lo[1], b.in.hi[2] - b.in.lo[2]};
     const int64_t cdims[3] = {b.core.hi[0] - b.core.lo[0], b.core.hi[1] - b.core.lo[1],
                               b.core.hi[2] - b.core.lo[2]};
-    cudaError_t e;
+    const size_t cbytes = oes * (size_t)(cdims[0] * cdims[1] * cdims[2]);
     if (faults.fail_copy()) { fail(HP_ERR_CUDA, "injected memcpy failure"); break; }
     if (in_pinned) {
       e = copy_box_async(x.din, idims, b.in.lo, in->data, n, vol_lo, b.in.lo, b.in.hi, ies,
@@ -623,17 +700,20 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     Job job = brick_job(b, x.din, x.dout);
     job.scratch = x.dscr;
     job.scratch_bytes = max_scr;
-    if ((e = op.launch(job, x.s)) != cudaSuccess) { cfail(e, "kernel launch"); break; }
+    job.host_scratch = x.hscr;
+    std::vector<void*> souts(nout);
+    for (int k = 0; k < nout; ++k) souts[k] = (char*)x.dout + k * max_out;
+    if ((st = op.launch(job, souts.data(), x.s)) != HP_OK) { if (rc == HP_OK) rc = st; break; }
     if (faults.fail_copy()) { fail(HP_ERR_CUDA, "injected memcpy failure"); break; }
-    if (out_pinned) {
-      e = copy_box_async(out->data, n, vol_lo, x.dout, cdims, b.core.lo, b.core.lo, b.core.hi, oes,
-                         cudaMemcpyDeviceToHost, x.s);
-    } else {
-      e = cudaMemcpyAsync(x.hout, x.dout, oes * cdims[0] * cdims[1] * cdims[2],
-                          cudaMemcpyDeviceToHost, x.s);
+    for (int k = 0; k < nout && e == cudaSuccess; ++k) {
+      if (out_pinned)
+        e = copy_box_async(outs[k]->data, n, vol_lo, souts[k], cdims, b.core.lo, b.core.lo,
+                           b.core.hi, oes, cudaMemcpyDeviceToHost, x.s);
+      else
+        e = cudaMemcpyAsync((char*)x.hout + k * max_out, souts[k], cbytes, cudaMemcpyDeviceToHost, x.s);
     }
     if (e != cudaSuccess) { cfail(e, "D2H copy"); break; }
-    d2h += oes * (uint64_t)(cdims[0] * cdims[1] * cdims[2]);
+    d2h += cbytes * nout;
     if ((e = cudaEventRecord(x.ev, x.s)) != cudaSuccess) { cfail(e, "cudaEventRecord"); break; }
     x.brick = (int)i;
   }
@@ -641,8 +721,9 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     if (rc == HP_OK) retire(x);
     else if (x.s) cudaStreamSynchronize(x.s);
   }
-  // kernels whose bounded waits gave up leave a mark in the error word
-  if (rc == HP_OK) {
+  // kernels whose bounded waits gave up leave a mark in their device's error word
+  for (int k = 0; k < nslot && rc == HP_OK; ++k) {
+    if (cudaSetDevice(devs[k]) != cudaSuccess) continue;
     int* ew = device_error_word();
     int hv = 0;
     if (ew && cudaMemcpy(&hv, ew, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && hv) {
@@ -651,14 +732,17 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     }
   }
   for (auto& x : sg) {
+    cudaSetDevice(x.dev);
     if (x.ev) cudaEventDestroy(x.ev);
     if (x.s) cudaStreamDestroy(x.s);
     if (x.din) { cudaFree(x.din); track_free((int64_t)max_in); }
-    if (x.dout) { cudaFree(x.dout); track_free((int64_t)max_out); }
+    if (x.dout) { cudaFree(x.dout); track_free((int64_t)(max_out * nout)); }
     if (x.dscr) { cudaFree(x.dscr); track_free((int64_t)max_scr); }
+    if (x.hscr) cudaFreeHost(x.hscr);
     if (x.hin) cudaFreeHost(x.hin);
     if (x.hout) cudaFreeHost(x.hout);
   }
+  cudaSetDevice(caller_dev);
   cudaError_t le = cudaGetLastError();
   if (rc == HP_OK && le != cudaSuccess) rc = cuda_fail(le, "executor");
   {
@@ -671,7 +755,6 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* out) {
     g_stats.wall_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
-  (void)dev_bytes;
   return rc;
 }
 
@@ -711,9 +794,32 @@ static void begin_call() {
   g_stats.wall_ms = 0;
 }
 
+static int run_multi(const Op& op, const hp_volume* in, hp_volume* const* outs, void* stream) {
+  begin_call();
+  if (in->loc == HP_HOST) return run_host(op, in, outs);
+  Job j = whole_job(in, outs[0], op.out_dtype);
+  const cudaStream_t s = (cudaStream_t)stream;
+  Scratch sc(s);
+  const size_t need = op.scratch_bytes ? op.scratch_bytes(j) : 0;
+  if (need > 0) {
+    const int st = check_scratch_budget(need);
+    if (st != HP_OK) return st;
+    cudaError_t e = sc.alloc(&j.scratch, need);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel scratch");
+    j.scratch_bytes = need;
+  }
+  std::vector<void*> ptrs(op.nout);
+  for (int k = 0; k < op.nout; ++k) ptrs[k] = outs[k]->data;
+  const int st = op.launch(j, ptrs.data(), s);
+  if (st != HP_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_stats.bricks = 1;
+  return HP_OK;
+}
+
 static int run(const Op& op, const hp_volume* in, hp_volume* out, void* stream) {
   begin_call();
-  if (in->loc == HP_HOST) return run_host(op, in, out);
+  if (in->loc == HP_HOST) return run_host(op, in, &out);
   Job j = whole_job(in, out, op.out_dtype);
   const cudaStream_t s = (cudaStream_t)stream;
   Scratch sc(s);
@@ -725,11 +831,48 @@ static int run(const Op& op, const hp_volume* in, hp_volume* out, void* stream) 
     if (e != cudaSuccess) return cuda_fail(e, "kernel scratch");
     j.scratch_bytes = need;
   }
-  cudaError_t e = op.launch(j, s);
-  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  const int st = op.launch(j, &out->data, s);
+  if (st != HP_OK) return st;
   std::lock_guard<std::mutex> lk(g_mu);
   g_stats.bricks = 1;
   return HP_OK;
+}
+
+// Out-of-core filter bank (Sec. III-D applied to the bank): Z slabs whose
+// input (halo = the largest radius) crosses the host link once for all the
+// bank's outputs; each slab runs the bank kernels on its core planes.
+int run_bank_host(const hp_volume* in, hp_volume* const* outs, const BankRequest& proto) {
+  begin_call();
+  int rmax = 0;
+  for (auto& f : proto.filters) rmax = std::max(rmax, radius_of(f.second, 3.0));
+  Op op;
+  op.halo = rmax;
+  op.out_dtype = proto.out_dtype;
+  op.nout = (int)proto.filters.size();
+  op.z_only = true;
+  op.scratch_per_in_voxel = 1;  // bound of the work list (32 B per >= 256-voxel tile item)
+  op.host_scratch = true;
+  auto request = [proto](const Job& j) {
+    BankRequest q = proto;
+    q.in = j.in.ptr;
+    q.in_z0 = j.in.lo[0];
+    q.in_nz = j.in.dims[0];
+    q.out_z0 = j.core_lo[0];
+    hp_box core;
+    for (int a = 0; a < 3; ++a) {
+      core.lo[a] = j.core_lo[a];
+      core.hi[a] = j.core_hi[a];
+    }
+    q.bricks.assign(1, core);
+    return q;
+  };
+  op.scratch_bytes = [request](const Job& j) { return bank_worklist_bytes(request(j)); };
+  op.launch = [request](const Job& j, void* const* souts, cudaStream_t s) {
+    BankRequest q = request(j);
+    for (size_t k = 0; k < q.outs.size(); ++k) q.outs[k] = souts[k];
+    return run_filterbank_brick(q, j.scratch, j.host_scratch, j.scratch_bytes, s);
+  };
+  return run_host(op, in, outs);
 }
 
 }  // namespace hp
@@ -803,7 +946,7 @@ int hp_gaussian3d(const hp_volume* in, hp_volume* out, double sigma, double trun
       op.scratch_bytes = [r](const Job& j) { return gauss_scratch_bytes(j, r); };
     }
   }
-  op.launch = [taps](const Job& j, cudaStream_t s) { return launch_gauss(j, *taps, s); };
+  op.launch = [taps](const Job& j, void* const*, cudaStream_t s) { return launched(launch_gauss(j, *taps, s)); };
   return run(op, in, out, stream);
 }
 
@@ -817,8 +960,8 @@ static int morph(const hp_volume* in, hp_volume* out, hp_se se, int radius, void
   Op op;
   op.halo = radius;
   op.out_dtype = out->dtype;
-  op.launch = [se, radius, dil](const Job& j, cudaStream_t s) {
-    return launch_morph(j, (int)se, radius, dil, s);
+  op.launch = [se, radius, dil](const Job& j, void* const*, cudaStream_t s) {
+    return launched(launch_morph(j, (int)se, radius, dil, s));
   };
   return run(op, in, out, stream);
 }
@@ -839,8 +982,121 @@ int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream) 
   Op op;
   op.halo = 0;
   op.out_dtype = HP_U8;
-  op.launch = [t](const Job& j, cudaStream_t s) { return launch_threshold(j, t, s); };
+  op.launch = [t](const Job& j, void* const*, cudaStream_t s) { return launched(launch_threshold(j, t, s)); };
   return run(op, in, out, stream);
+}
+
+int hp_threshold_box3d(const hp_volume* in, hp_volume* out, int method, int radius, double k,
+                       double c, void* stream) {
+  int st = check_pair(in, out);
+  if (st != HP_OK) return st;
+  if (out->dtype != HP_U8) return set_error(HP_ERR_UNSUPPORTED, "local threshold output dtype must be u8");
+  if (method < HP_LOCAL_MEAN || method > HP_LOCAL_SAUVOLA)
+    return set_error(HP_ERR_INVALID_ARG, "unknown local threshold method");
+  if (radius < 0 || radius > 15) return set_error(HP_ERR_INVALID_ARG, "radius must be in [0, 15]");
+  if (!std::isfinite(k) || !std::isfinite(c)) return set_error(HP_ERR_INVALID_ARG, "k and c must be finite");
+  if (method == HP_LOCAL_SAUVOLA && !(c > 0)) return set_error(HP_ERR_INVALID_ARG, "Sauvola needs c = R > 0");
+  Op op;
+  op.halo = radius;
+  op.out_dtype = HP_U8;
+  const bool fp = in->dtype == HP_F16 || in->dtype == HP_F32;
+  op.scratch_per_in_voxel = fp ? 32 : 24;
+  op.scratch_bytes = [radius](const Job& j) { return box_scratch_bytes(j, radius); };
+  op.launch = [method, radius, k, c](const Job& j, void* const*, cudaStream_t s) {
+    return launched(launch_threshold_box(j, method, radius, k, c, s));
+  };
+  return run(op, in, out, stream);
+}
+
+int hp_hessian3d(const hp_volume* in, hp_volume* const* outs, int what, double sigma,
+                 void* stream) {
+  if (what != HP_HESSIAN_COMPONENTS && what != HP_HESSIAN_EIGENVALUES)
+    return set_error(HP_ERR_INVALID_ARG, "what must be HP_HESSIAN_COMPONENTS or HP_HESSIAN_EIGENVALUES");
+  const int nout = what == HP_HESSIAN_COMPONENTS ? 6 : 3;
+  if (!outs) return set_error(HP_ERR_INVALID_ARG, "null outputs");
+  for (int k = 0; k < nout; ++k) {
+    int st = check_pair(in, outs[k]);
+    if (st != HP_OK) return st;
+    if (outs[k]->dtype != HP_F32 && outs[k]->dtype != HP_F16)
+      return set_error(HP_ERR_UNSUPPORTED, "Hessian outputs must be f32 or f16");
+    if (outs[k]->dtype != outs[0]->dtype)
+      return set_error(HP_ERR_UNSUPPORTED, "Hessian outputs must share one dtype");
+  }
+  if (!(sigma > 0) || !std::isfinite(sigma)) return set_error(HP_ERR_INVALID_ARG, "sigma must be > 0");
+  const int r = radius_of(sigma, 3.0);
+  if (r > kMaxRGeneric) return set_error(HP_ERR_UNSUPPORTED, "radius exceeds 32");
+  static const int kOrders[6][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+  auto taps = std::make_shared<std::vector<Taps>>(6);
+  for (int k = 0; k < 6; ++k) make_taps(sigma, 3.0, kOrders[k], &(*taps)[k]);
+  const bool eig = what == HP_HESSIAN_EIGENVALUES;
+  Op op;
+  op.halo = r;
+  op.out_dtype = outs[0]->dtype;
+  op.nout = nout;
+  Job probe = whole_job(in, outs[0], outs[0]->dtype);
+  const bool gen = gauss_scratch_bytes(probe, r) > 0;
+  op.scratch_per_in_voxel = (eig ? 24 : 0) + (gen ? 8 : 0);
+  auto core_voxels = [](const Job& j) {
+    return (j.core_hi[0] - j.core_lo[0]) * (j.core_hi[1] - j.core_lo[1]) * (j.core_hi[2] - j.core_lo[2]);
+  };
+  if (op.scratch_per_in_voxel > 0)
+    op.scratch_bytes = [eig, r, core_voxels](const Job& j) {
+      return (eig ? hessian_eig_scratch(core_voxels(j)) : 0) + gauss_scratch_bytes(j, r);
+    };
+  op.launch = [taps, eig, core_voxels](const Job& j, void* const* o, cudaStream_t s) -> int {
+    const int64_t nv = core_voxels(j);
+    const size_t comp_bytes = eig ? hessian_eig_scratch(nv) : 0;
+    float* comps = static_cast<float*>(j.scratch);
+    for (int k = 0; k < 6; ++k) {
+      Job jk = j;
+      if (eig) {
+        jk.out.ptr = comps + (size_t)k * nv;
+        jk.out.dtype = HP_F32;
+      } else {
+        jk.out.ptr = o[k];
+      }
+      // generic-path scratch after the components
+      jk.scratch = j.scratch ? static_cast<char*>(j.scratch) + comp_bytes : nullptr;
+      jk.scratch_bytes = j.scratch_bytes - comp_bytes;
+      const cudaError_t e = launch_gauss(jk, (*taps)[k], s);
+      if (e != cudaSuccess) return cuda_fail(e, "Hessian component launch");
+    }
+    if (eig) return launched(launch_hessian_eig(comps, nv, o, j.out.dtype, s));
+    return HP_OK;
+  };
+  (void)r;
+  return run_multi(op, in, outs, stream);
+}
+
+int hp_set_devices(const int* devices, int n) {
+  if (n < 0 || (n > 0 && !devices)) return set_error(HP_ERR_INVALID_ARG, "bad device list");
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  for (int i = 0; i < n; ++i)
+    if (devices[i] < 0 || devices[i] >= count)
+      return set_error(HP_ERR_INVALID_ARG, "device " + std::to_string(devices[i]) + " does not exist");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_devices.assign(devices, devices + n);
+  return HP_OK;
+}
+
+int hp_get_devices(int* devices, int max_n, int* n) {
+  if (!n) return set_error(HP_ERR_INVALID_ARG, "null count");
+  std::lock_guard<std::mutex> lk(g_mu);
+  *n = (int)g_devices.size();
+  for (int i = 0; i < *n && i < max_n; ++i)
+    if (devices) devices[i] = g_devices[i];
+  return HP_OK;
+}
+
+int hp_set_brick_shard(int rank, int world) {
+  if (world < 1 || rank < 0 || rank >= world)
+    return set_error(HP_ERR_INVALID_ARG, "shard needs 0 <= rank < world");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_shard_rank = rank;
+  g_shard_world = world;
+  return HP_OK;
 }
 
 int hp_plan_bricks(int64_t nx, int64_t ny, int64_t nz, int halo, size_t in_bytes,
@@ -849,7 +1105,7 @@ int hp_plan_bricks(int64_t nx, int64_t ny, int64_t nz, int halo, size_t in_bytes
   if (!nbricks) return set_error(HP_ERR_INVALID_ARG, "null nbricks");
   const int64_t n[3] = {nz, ny, nx};
   std::vector<Brick> b;
-  int st = plan(n, halo, in_bytes, out_bytes, 0, budget, stages, min_bricks, &b);
+  int st = plan(n, halo, in_bytes, out_bytes, 0, budget, stages, min_bricks, false, &b);
   if (st != HP_OK) return st;
   *nbricks = (int)b.size();
   for (int i = 0; i < (int)b.size() && i < max_bricks; ++i) {

@@ -13,15 +13,6 @@
 
 namespace hp {
 
-struct BankRequest {
-  const void* in;
-  int dtype, out_dtype;
-  int64_t G[3];
-  std::vector<std::pair<int, double>> filters;
-  std::vector<void*> outs;
-  std::vector<hp_box> bricks;
-};
-int run_filterbank(const BankRequest& q, cudaStream_t s);
 void bank_release_cache();
 cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3],
                                const Taps& taps, float* t1, float* t2, int accumulate,
@@ -73,8 +64,10 @@ static int bank_common(const hp_volume* in, hp_volume* const* outs, const hp_fil
                        const hp_box* bricks, int nbricks, void* stream) {
   if (!in || !in->data || !outs || !f || n < 1)
     return set_error(HP_ERR_INVALID_ARG, "filter bank: null argument or n < 1");
-  if (in->loc != HP_DEVICE)
-    return set_error(HP_ERR_UNSUPPORTED, "filter bank runs on device volumes only");
+  if (in->loc != HP_HOST && in->loc != HP_DEVICE)
+    return set_error(HP_ERR_INVALID_ARG, "filter bank: unknown location");
+  if (in->loc == HP_HOST && bricks)
+    return set_error(HP_ERR_UNSUPPORTED, "filter bank: brick lists are for device volumes (host volumes are planned by the library)");
   BankRequest q;
   q.in = in->data;
   q.dtype = in->dtype;
@@ -86,7 +79,7 @@ static int bank_common(const hp_volume* in, hp_volume* const* outs, const hp_fil
   for (int i = 0; i < n; ++i) {
     const hp_volume* o = outs[i];
     if (!o || !o->data) return set_error(HP_ERR_INVALID_ARG, "filter bank: null output");
-    if (o->loc != HP_DEVICE) return set_error(HP_ERR_UNSUPPORTED, "filter bank: outputs must be device volumes");
+    if (o->loc != in->loc) return set_error(HP_ERR_UNSUPPORTED, "filter bank: mixed host/device locations");
     if (o->nx != in->nx || o->ny != in->ny || o->nz != in->nz)
       return set_error(HP_ERR_INVALID_ARG, "filter bank: output extents differ from the input");
     if (o->dtype != HP_F16 && o->dtype != HP_F32)
@@ -103,6 +96,16 @@ static int bank_common(const hp_volume* in, hp_volume* const* outs, const hp_fil
     if (!(f[i].sigma > 0)) return set_error(HP_ERR_INVALID_ARG, "filter bank: sigma must be > 0");
     q.filters.push_back({f[i].kind, f[i].sigma});
     q.outs.push_back(o->data);
+  }
+  if (in->loc == HP_HOST) {
+    for (auto& f : q.filters)
+      if (radius_of(f.second, 3.0) < 1 || radius_of(f.second, 3.0) > kMaxR)
+        return set_error(HP_ERR_UNSUPPORTED, "filter bank: radius must be in [1, 12] (sigma in ~[0.17, 4.16])");
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j)
+        if (f[i].kind == f[j].kind && f[i].sigma == f[j].sigma)
+          return set_error(HP_ERR_INVALID_ARG, "filter bank: duplicate (kind, sigma)");
+    return run_bank_host(in, outs, q);
   }
   if (bricks && nbricks > 0) {
     q.bricks.assign(bricks, bricks + nbricks);

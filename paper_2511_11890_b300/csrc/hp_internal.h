@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hp.h"
@@ -76,6 +77,7 @@ struct Job {
   int64_t core_hi[3];
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* host_scratch = nullptr;  // page-locked, scratch_bytes long (host-mode bricks only)
 };
 
 // FP32 taps per axis (z, y, x), index k + r for k in [-r, r].
@@ -91,6 +93,28 @@ void taps1d_f64(double sigma, int r, int order, double* w);
 
 // Device-side error word (per device), set by bounded waits that give up.
 int* device_error_word();
+
+// Hessian eigenvalue epilogue: comps = six dense FP32 volumes of n voxels
+// (Dzz, Dyy, Dxx, Dzy, Dzx, Dyx) one after another; outs[0..2] = ascending
+// eigenvalues in out_dtype.
+size_t hessian_eig_scratch(int64_t core_voxels);
+cudaError_t launch_hessian_eig(const float* comps, int64_t n, void* const* outs, int out_dtype,
+                               cudaStream_t s);
+// Box-window local threshold (mean / Niblack / Sauvola) of a job: window
+// sums through job.scratch (box_scratch_bytes), decision into job.out (u8).
+size_t box_scratch_bytes(const Job& job, int w);
+cudaError_t launch_threshold_box(const Job& job, int method, int w, double k, double c,
+                                 cudaStream_t s);
+
+// Regions of a separable three-pass job of radius r (Gaussian generic path,
+// box sums): after the x pass, z and y cover the hull of the reflected
+// sources of the core grown by r (from rlo) and x the core; after the y
+// pass, z as before and y, x the core.
+struct SepRegions {
+  int64_t rlo[2];
+  int64_t n_x[3], n_y[3];
+};
+SepRegions sep_regions(const Job& job, int r);
 
 // Launchers (enqueue only). Return a cudaError_t.
 // Scratch bytes launch_gauss needs in job.scratch for radius r (nonzero only
@@ -138,6 +162,27 @@ int max_smem_per_sm();
 // planes plus `halo`; returns the multiple of `align` that minimises
 // waves x (chunk + halo).
 int64_t pick_zchunk(int64_t cz, int64_t tiles, int64_t slots, int halo, int align);
+
+// A filter-bank request: the input and each output are whole x/y planes of
+// the volume G, starting at planes in_z0 / out_z0 (0: the whole volume);
+// the work list covers `bricks` (core boxes in global coordinates).
+struct BankRequest {
+  const void* in;
+  int dtype, out_dtype;
+  int64_t G[3];
+  std::vector<std::pair<int, double>> filters;  // (kind, sigma)
+  std::vector<void*> outs;
+  std::vector<hp_box> bricks;
+  int64_t in_z0 = 0, in_nz = 0, out_z0 = 0;  // in_nz = 0: the whole volume
+};
+// Device-mode bank: autotuned, cached, CUDA-graph launch.
+int run_filterbank(const BankRequest& q, cudaStream_t s);
+// Out-of-core brick: work list in caller device memory wl, staged through
+// the caller's page-locked hwl, both bank_worklist_bytes(q) long; no graph.
+size_t bank_worklist_bytes(const BankRequest& q);
+int run_filterbank_brick(const BankRequest& q, void* wl, void* hwl, size_t wl_bytes, cudaStream_t s);
+// Host-mode (out-of-core) bank over Z slabs; outs are host volumes.
+int run_bank_host(const hp_volume* in, hp_volume* const* outs, const BankRequest& proto);
 
 // HP_LOG >= 1 prints the kernel path chosen for each launch to stderr.
 int log_level();

@@ -136,7 +136,7 @@ __device__ void run_item(const BankParams& P, const CUtensorMap* tmap, const Ban
   const int base = phase_base;
   auto issue = [&](int n) {
     const int b = (base + n) % kNS;
-    const int zl = (int)reflect(cz0 - R + n, Gz);
+    const int zl = (int)(reflect(cz0 - R + n, Gz) - P.in_z0);
     uint64_t* bar = &bars[b];
     mbar_arrive_expect_tx(bar, bw * Gm::BH * es);
     tma_load_3d(stages + b * sbytes, tmap, (int)(cx0 - ra), (int)(cy0 - R), zl, bar);
@@ -202,7 +202,7 @@ __device__ void run_item(const BankParams& P, const CUtensorMap* tmap, const Ban
               const int sc = scol[k];
               float v = 0.0f;
               if (sr >= 0 && sc >= 0) {
-                const int64_t e = (sz * Gy + sr) * Gx + sc;
+                const int64_t e = ((sz - P.in_z0) * Gy + sr) * Gx + sc;
                 switch (dt) {
                   case HP_U8: v = to_f32<uint8_t>(static_cast<const uint8_t*>(P.in)[e]); break;
                   case HP_U16: v = to_f32<uint16_t>(static_cast<const uint16_t*>(P.in)[e]); break;
@@ -318,7 +318,7 @@ __device__ void run_item(const BankParams& P, const CUtensorMap* tmap, const Ban
         const int64_t gy = cy0 + py, gx = cx0 + px;
         if (gy < it.y1 && gx < it.x1) {
           const int64_t pstride = Gy * Gx;
-          int64_t idx = ((cz0 + zb) * Gy + gy) * Gx + gx;
+          int64_t idx = ((cz0 + zb - P.out_z0) * Gy + gy) * Gx + gx;
 #pragma unroll
           for (int j = 0; j < kBZ; ++j, idx += pstride) {
             if (zb + j >= nout) break;
@@ -417,15 +417,6 @@ int cfg_smem(int cfg, int r, int es) {
 
 // ----------------------------------------------------------------- host side
 
-struct BankRequest {
-  const void* in;
-  int dtype, out_dtype;
-  int64_t G[3];
-  std::vector<std::pair<int, double>> filters;  // (kind, sigma)
-  std::vector<void*> outs;
-  std::vector<hp_box> bricks;
-};
-
 // Tuning knobs picked by the autotuner: tile configuration for small radii
 // and z-chunk length.
 struct BankTune {
@@ -441,6 +432,7 @@ struct BankPlan {
   BankParams P;
   BankItem* d_items = nullptr;
   int* d_counter = nullptr;  // [2]: one per launch
+  bool owns = true;          // false: work list in caller memory, no graph
   BankMaps maps;
   int smem = 0;
   int grid = 0;
@@ -457,8 +449,8 @@ struct BankPlan {
   ~BankPlan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    if (d_items) cudaFree(d_items);
-    if (d_counter) cudaFree(d_counter);
+    if (owns && d_items) cudaFree(d_items);
+    if (owns && d_counter) cudaFree(d_counter);
   }
 };
 
@@ -509,15 +501,25 @@ static std::string key_of(const BankRequest& q, const BankTune* t, bool with_ptr
   return k;
 }
 
-// Build a plan (work list, TMA maps, graph) for one tuning choice.
-static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<BankPlan>* out) {
+// Build a plan (work list, TMA maps, graph) for one tuning choice. With
+// `wl` set, the counters and the work list go into that caller device
+// memory (wl_bytes), copied on stream s from the caller's page-locked
+// buffer hwl (wl_bytes, not reused until the copy has run), and no graph
+// is made: the plan is launched directly (launch_direct) and owns no
+// device memory.
+static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<BankPlan>* out,
+                      void* wl = nullptr, size_t wl_bytes = 0, cudaStream_t s = nullptr,
+                      void* hwl = nullptr) {
   auto plan = std::make_unique<BankPlan>();
+  plan->owns = wl == nullptr;
   BankParams& P = plan->P;
   memset(&P, 0, sizeof(P));
   P.in = q.in;
   P.dtype = q.dtype;
   P.out_dtype = q.out_dtype;
   for (int a = 0; a < 3; ++a) P.G[a] = q.G[a];
+  P.in_z0 = q.in_z0;
+  P.out_z0 = q.out_z0;
   // sigma groups, heaviest first
   std::vector<double> sigmas;
   for (auto& f : q.filters)
@@ -616,21 +618,36 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   P.nitems = (int)items.size();
   cudaError_t e;
   const size_t nall = items.size() + items2.size();
-  if ((e = cudaMalloc(&plan->d_items, sizeof(BankItem) * std::max<size_t>(1, nall))) != cudaSuccess)
-    return cuda_fail(e, "cudaMalloc(work list)");
-  if ((e = cudaMalloc(&plan->d_counter, 2 * sizeof(int))) != cudaSuccess)
-    return cuda_fail(e, "cudaMalloc(counter)");
-  plan->bytes = sizeof(BankItem) * nall + 2 * sizeof(int);
   items.insert(items.end(), items2.begin(), items2.end());
-  if (nall && (e = cudaMemcpy(plan->d_items, items.data(), sizeof(BankItem) * nall,
-                              cudaMemcpyHostToDevice)) != cudaSuccess)
-    return cuda_fail(e, "copy work list");
+  if (wl) {
+    // counters in the first 256 bytes, the work list after them
+    if (256 + sizeof(BankItem) * nall > wl_bytes)
+      return set_error(HP_ERR_INTERNAL, "filter bank: work list exceeds its buffer");
+    if (!hwl) return set_error(HP_ERR_INTERNAL, "filter bank: no staging buffer for the work list");
+    plan->d_counter = static_cast<int*>(wl);
+    plan->d_items = reinterpret_cast<BankItem*>(static_cast<char*>(wl) + 256);
+    if (nall) {
+      memcpy(static_cast<char*>(hwl) + 256, items.data(), sizeof(BankItem) * nall);
+      if ((e = cudaMemcpyAsync(plan->d_items, static_cast<char*>(hwl) + 256, sizeof(BankItem) * nall,
+                               cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "copy work list");
+    }
+  } else {
+    if ((e = cudaMalloc(&plan->d_items, sizeof(BankItem) * std::max<size_t>(1, nall))) != cudaSuccess)
+      return cuda_fail(e, "cudaMalloc(work list)");
+    if ((e = cudaMalloc(&plan->d_counter, 2 * sizeof(int))) != cudaSuccess)
+      return cuda_fail(e, "cudaMalloc(counter)");
+    plan->bytes = sizeof(BankItem) * nall + 2 * sizeof(int);
+    if (nall && (e = cudaMemcpy(plan->d_items, items.data(), sizeof(BankItem) * nall,
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "copy work list");
+  }
   P.items = plan->d_items;
   P.counter = plan->d_counter;
   P.err = device_error_word();
   // TMA maps, per sigma group.
   memset(&plan->maps, 0, sizeof(plan->maps));
-  const int64_t dims[3] = {q.G[2], q.G[1], q.G[0]};
+  const int64_t dims[3] = {q.G[2], q.G[1], q.in_nz > 0 ? q.in_nz : q.G[0]};
   for (int g = 0; g < P.ngroups && tma; ++g) {
     const int r = P.grp[g].r;
     const int tx = cfg_of(r) == 1 ? 32 : 16;
@@ -665,6 +682,10 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, nt1, smem);
   plan->grid = std::max(1, std::min(P.nitems, sms * std::max(1, per_sm)));
+  if (wl) {
+    *out = std::move(plan);
+    return HP_OK;
+  }
   // graph: reset the counters, then the persistent launch(es); two launches
   // are sibling nodes, so the second fills SMs as the first drains
   if ((e = cudaGraphCreate(&plan->graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
@@ -705,6 +726,25 @@ static int build_plan(const BankRequest& q, const BankTune& t, std::unique_ptr<B
   if ((e = cudaGraphInstantiate(&plan->exec, plan->graph, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphInstantiate");
   *out = std::move(plan);
+  return HP_OK;
+}
+
+// Launch of a plan without a graph: counters reset, then the launch(es) in
+// stream order (the second follows the first).
+static int launch_direct(BankPlan& pl, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(pl.d_counter, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(bank counters)");
+  if (pl.P.nitems > 0 || !pl.kernel2) {
+    void* args[2] = {&pl.P, &pl.maps};
+    e = cudaLaunchKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "filter bank launch");
+  }
+  if (pl.kernel2) {
+    void* args[2] = {&pl.P2, &pl.maps};
+    e = cudaLaunchKernel(pl.kernel2, dim3(pl.grid2), dim3(b2::kThreads2), args, pl.smem2, s);
+    if (e != cudaSuccess) return cuda_fail(e, "filter bank launch");
+  }
+  g_last_kernels.store((pl.P.nitems > 0 || !pl.kernel2 ? 1 : 0) + (pl.kernel2 ? 1 : 0));
   return HP_OK;
 }
 
@@ -800,6 +840,38 @@ int run_filterbank(const BankRequest& q, cudaStream_t s) {
     g_plans[k] = std::move(np);
   }
   return launch_plan(*pl, s);
+}
+
+// Out-of-core tuning choice: 16 x 16 tiles, radii <= 6 in a second launch
+// at two CTAs per SM where they fit, z chunks of 128 planes.
+static const BankTune kHostTune = {2, 128};
+
+size_t bank_worklist_bytes(const BankRequest& q) {
+  // items of 16 x 16 tiles and 128-plane chunks per distinct sigma and
+  // brick (32 x 16 tiles need fewer), after 256 bytes of counters
+  int ng = 0;
+  std::vector<double> seen;
+  for (auto& f : q.filters)
+    if (std::find(seen.begin(), seen.end(), f.second) == seen.end()) {
+      seen.push_back(f.second);
+      ++ng;
+    }
+  size_t items = 0;
+  for (auto& b : q.bricks)
+    items += (size_t)((b.hi[1] - b.lo[1] + 15) / 16) * (size_t)((b.hi[2] - b.lo[2] + 15) / 16) *
+             (size_t)((b.hi[0] - b.lo[0] + kHostTune.zchunk - 1) / kHostTune.zchunk);
+  return 256 + sizeof(BankItem) * items * (size_t)ng;
+}
+
+// One out-of-core brick: the bank over q.bricks (the brick's core) with the
+// input and outputs as plane ranges of the volume (in_z0, out_z0), the work
+// list in caller device memory wl staged through the caller's page-locked
+// hwl (both bank_worklist_bytes), launched without a graph.
+int run_filterbank_brick(const BankRequest& q, void* wl, void* hwl, size_t wl_bytes, cudaStream_t s) {
+  std::unique_ptr<BankPlan> pl;
+  int rc = build_plan(q, kHostTune, &pl, wl, wl_bytes, s, hwl);
+  if (rc != HP_OK) return rc;
+  return launch_direct(*pl, s);
 }
 
 const void* bank2_kernel_u16(int minb);

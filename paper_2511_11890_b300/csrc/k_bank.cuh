@@ -48,10 +48,12 @@ struct BankGroup {
 };
 
 struct BankParams {
-  const void* in;
+  const void* in;  // planes [in_z0, in_z0 + nz) of the volume (whole x/y planes)
   int dtype;
   int out_dtype;
-  int64_t G[3];  // (z, y, x)
+  int64_t G[3];    // global volume (z, y, x)
+  int64_t in_z0;   // global z of the input's first plane
+  int64_t out_z0;  // global z of the outputs' first plane
   int ngroups;
   BankGroup grp[kBankMaxGroups];
   const BankItem* items;
@@ -281,12 +283,13 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
     const int z0 = cz0 - R + n0;
     if (n0 + kKP <= total && z0 >= 0 && z0 + kKP <= Gz) {
       mbar_arrive_expect_tx(&bars[b], g.GB);
-      tma_load_3d(dst, md, cx0 - g.RA, cy0 - R, z0, &bars[b]);
+      tma_load_3d(dst, md, cx0 - g.RA, cy0 - R, (int)(z0 - P.in_z0), &bars[b]);
     } else {
       const int cnt = min(kKP, total - n0);
       mbar_arrive_expect_tx(&bars[b], cnt * g.PB);
       for (int p = 0; p < cnt; ++p)
-        tma_load_3d(dst + p * g.PB, m1, cx0 - g.RA, cy0 - R, (int)reflect(z0 + p, Gz), &bars[b]);
+        tma_load_3d(dst + p * g.PB, m1, cx0 - g.RA, cy0 - R, (int)(reflect(z0 + p, Gz) - P.in_z0),
+                    &bars[b]);
     }
   };
   __syncthreads();  // tables ready; the previous item's stage reads are done
@@ -347,7 +350,7 @@ __device__ void run_item2(const BankParams& P, const BankMaps& maps, const BankI
         const int64_t gy = cy0 + py, gx = cx0 + px;
         if (gy < it.y1 && gx < it.x1) {
           const int64_t pstride = Gy * Gx;
-          int64_t idx = ((int64_t)(cz0 + zb) * Gy + gy) * Gx + gx;
+          int64_t idx = ((int64_t)(cz0 + zb - P.out_z0) * Gy + gy) * Gx + gx;
 #pragma unroll
           for (int j = 0; j < kKP; ++j, idx += pstride) {
             if (zb + j >= nout) break;

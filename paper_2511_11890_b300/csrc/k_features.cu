@@ -1,0 +1,295 @@
+// Texture features and local thresholds (Harpia Sec. III-C): the per-voxel
+// eigenvalues of the Gaussian Hessian, and box-window local statistics for
+// the mean, Niblack and Sauvola threshold algorithms.
+//
+// Hessian eigenvalues: the six distinct second derivatives come from the
+// Gaussian derivative kernels (launch_gauss with orders summing to 2); the
+// epilogue here solves the symmetric 3x3 eigenproblem per voxel in FP32 in
+// closed form (the trigonometric solution of the characteristic cubic):
+// with q = tr(H)/3, p = sqrt(tr((H - qI)^2) / 6) and r = det(H - qI)/(2p^3),
+// the eigenvalues are q + 2p cos(acos(r)/3 + 2 pi j / 3), j = 0, 1, 2.
+//
+// Box statistics: the window sums S1 = sum f and S2 = sum f^2 over the
+// (2w+1)^3 cube with reflect boundaries are formed separably, x then y then
+// z, each 1D window summed in increasing source coordinate. Integer inputs
+// (u8, u16) sum in 32/64-bit integers (exact); floating-point inputs in FP64
+// with explicitly rounded operations. The decision epilogue evaluates
+//   m = S1/N, v = max(S2/N - m*m, 0), s = sqrt(v),
+//   T = m - c (mean) | m + k s (Niblack) | m (1 + k (s/c - 1)) (Sauvola)
+// in FP64, one IEEE-rounded operation at a time (no contraction), and
+// writes f > T.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "hp_device.cuh"
+#include "hp_internal.h"
+
+namespace hp {
+
+namespace {
+
+constexpr int kBlk = 256;
+
+__device__ __forceinline__ void store_f(void* base, int dt, int64_t i, float v) {
+  if (dt == HP_F32) static_cast<float*>(base)[i] = v;
+  else static_cast<__half*>(base)[i] = __float2half_rn(v);
+}
+
+// Eigenvalues of [[a, d, e], [d, b, f], [e, f, c]], ascending.
+__device__ __forceinline__ void sym3_eig(float a, float b, float c, float d, float e, float f,
+                                         float& l1, float& l2, float& l3) {
+  const float p1 = fmaf(d, d, fmaf(e, e, f * f));
+  const float q = (a + b + c) * (1.0f / 3.0f);
+  if (p1 == 0.0f) {
+    l1 = fminf(a, fminf(b, c));
+    l3 = fmaxf(a, fmaxf(b, c));
+    l2 = (a + b + c) - l1 - l3;
+    return;
+  }
+  const float aa = a - q, bb = b - q, cc = c - q;
+  const float p2 = fmaf(aa, aa, fmaf(bb, bb, fmaf(cc, cc, 2.0f * p1)));
+  const float p = sqrtf(p2 * (1.0f / 6.0f));
+  if (!(p > 0.0f)) {
+    l1 = l2 = l3 = q;
+    return;
+  }
+  const float ip = 1.0f / p;
+  const float ba = aa * ip, bbb = bb * ip, bc = cc * ip, bd = d * ip, be = e * ip, bf = f * ip;
+  // det(B) / 2 for B = (H - qI) / p
+  const float det = ba * (bbb * bc - bf * bf) - bd * (bd * bc - bf * be) + be * (bd * bf - bbb * be);
+  const float r = fminf(1.0f, fmaxf(-1.0f, 0.5f * det));
+  const float phi = acosf(r) * (1.0f / 3.0f);
+  l3 = q + 2.0f * p * cosf(phi);
+  l1 = q + 2.0f * p * cosf(phi + 2.0943951023931957f);
+  l2 = 3.0f * q - l1 - l3;
+  // order l1 <= l2 <= l3 against rounding near repeated eigenvalues
+  if (l2 < l1) { const float t = l1; l1 = l2; l2 = t; }
+  if (l3 < l2) { const float t = l2; l2 = l3; l3 = t; }
+  if (l2 < l1) { const float t = l1; l1 = l2; l2 = t; }
+}
+
+// comps: six dense FP32 volumes of n voxels (Dzz, Dyy, Dxx, Dzy, Dzx, Dyx),
+// one after another; outs: three volumes of out_dtype.
+__global__ void k_hessian_eig(const float* __restrict__ comps, int64_t n, void* o1, void* o2,
+                              void* o3, int dt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float l1, l2, l3;
+    sym3_eig(comps[i], comps[n + i], comps[2 * n + i], comps[3 * n + i], comps[4 * n + i],
+             comps[5 * n + i], l1, l2, l3);
+    store_f(o1, dt, i, l1);
+    store_f(o2, dt, i, l2);
+    store_f(o3, dt, i, l3);
+  }
+}
+
+// ----------------------------------------------------------- box statistics
+
+template <typename T>
+__device__ __forceinline__ T load_t(const void* p, int64_t i) {
+  return static_cast<const T*>(p)[i];
+}
+
+// Integer sums: S1 in int32, S2 in int64 (exact: u16 values, windows of at
+// most 31^3 voxels).
+struct ISum {
+  int32_t* s1;
+  int64_t* s2;
+};
+// Floating-point sums: FP64.
+struct FSum {
+  double* s1;
+  double* s2;
+};
+
+// x pass over the region [off, off + n) of the global volume: window sums
+// along x of the input (a dense box at in_lo with in_dims).
+template <typename TIN>
+__global__ void k_box_x_int(const TIN* __restrict__ in, DevBox B, ISum dst, int64_t n0, int64_t n1,
+                            int64_t n2, int64_t off0, int64_t off1, int64_t off2, int64_t Gx, int w) {
+  const int64_t total = n0 * n1 * n2;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
+    const int64_t row = ((off0 + z - B.lo[0]) * B.dims[1] + (off1 + y - B.lo[1])) * B.dims[2];
+    int32_t t1 = 0;
+    int64_t t2 = 0;
+    for (int k = -w; k <= w; ++k) {
+      const int32_t v = (int32_t)in[row + reflect(off2 + x + k, Gx) - B.lo[2]];
+      t1 += v;
+      t2 += (int64_t)(v * (uint32_t)v);
+    }
+    dst.s1[q] = t1;
+    dst.s2[q] = t2;
+  }
+}
+
+template <typename TIN>
+__global__ void k_box_x_fp(const TIN* __restrict__ in, DevBox B, FSum dst, int64_t n0, int64_t n1,
+                           int64_t n2, int64_t off0, int64_t off1, int64_t off2, int64_t Gx, int w) {
+  const int64_t total = n0 * n1 * n2;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
+    const int64_t row = ((off0 + z - B.lo[0]) * B.dims[1] + (off1 + y - B.lo[1])) * B.dims[2];
+    double t1 = 0.0, t2 = 0.0;
+    for (int k = -w; k <= w; ++k) {
+      const double v = (double)to_f32<TIN>(in[row + reflect(off2 + x + k, Gx) - B.lo[2]]);
+      t1 = __dadd_rn(t1, v);
+      t2 = __dadd_rn(t2, __dmul_rn(v, v));
+    }
+    dst.s1[q] = t1;
+    dst.s2[q] = t2;
+  }
+}
+
+// y (axis 1) or z (axis 0) pass from a dense source region (lo, dims) to
+// the region [off, off + n): window sums along the axis.
+struct Reg {
+  int64_t lo[3], dims[3];
+};
+
+__device__ __forceinline__ int64_t reg_index(const Reg& R, int64_t z, int64_t y, int64_t x) {
+  return ((z - R.lo[0]) * R.dims[1] + (y - R.lo[1])) * R.dims[2] + (x - R.lo[2]);
+}
+
+template <typename S1, typename S2, bool FP>
+__device__ __forceinline__ void axis_sum(const S1* s1, const S2* s2, const Reg& R, int axis,
+                                         int64_t c0, int64_t c1, int64_t c2, int64_t Gn, int w,
+                                         S1& t1, S2& t2) {
+  t1 = 0;
+  t2 = 0;
+  for (int k = -w; k <= w; ++k) {
+    int64_t c[3] = {c0, c1, c2};
+    c[axis] = reflect(c[axis] + k, Gn);
+    const int64_t i = reg_index(R, c[0], c[1], c[2]);
+    if constexpr (FP) {
+      t1 = (S1)__dadd_rn((double)t1, (double)s1[i]);
+      t2 = (S2)__dadd_rn((double)t2, (double)s2[i]);
+    } else {
+      t1 += s1[i];
+      t2 += s2[i];
+    }
+  }
+}
+
+template <typename S1, typename S2, bool FP>
+__global__ void k_box_y(const S1* __restrict__ a1, const S2* __restrict__ a2, Reg src, S1* b1, S2* b2,
+                        int64_t n0, int64_t n1, int64_t n2, int64_t off0, int64_t off1, int64_t off2,
+                        int64_t Gy, int w) {
+  const int64_t total = n0 * n1 * n2;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
+    S1 t1;
+    S2 t2;
+    axis_sum<S1, S2, FP>(a1, a2, src, 1, off0 + z, off1 + y, off2 + x, Gy, w, t1, t2);
+    b1[q] = t1;
+    b2[q] = t2;
+  }
+}
+
+// z pass and decision: out (u8, the job's output box) = f > T.
+template <typename TIN, typename S1, typename S2, bool FP>
+__global__ void k_box_z_decide(const S1* __restrict__ b1, const S2* __restrict__ b2, Reg src,
+                               const TIN* __restrict__ in, DevBox B, DevOut O, int64_t n0, int64_t n1,
+                               int64_t n2, int64_t off0, int64_t off1, int64_t off2, int64_t Gz,
+                               int w, int method, double k, double c) {
+  const int64_t total = n0 * n1 * n2;
+  const double nw = (double)(2 * w + 1) * (double)(2 * w + 1) * (double)(2 * w + 1);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = off2 + q % n2, y = off1 + (q / n2) % n1, z = off0 + q / (n1 * n2);
+    S1 t1;
+    S2 t2;
+    axis_sum<S1, S2, FP>(b1, b2, src, 0, z, y, x, Gz, w, t1, t2);
+    const double s1 = (double)t1, s2 = (double)t2;
+    const double m = __ddiv_rn(s1, nw);
+    double v = __dsub_rn(__ddiv_rn(s2, nw), __dmul_rn(m, m));
+    if (v < 0.0) v = 0.0;
+    const double sd = __dsqrt_rn(v);
+    double t;
+    if (method == HP_LOCAL_MEAN) t = __dsub_rn(m, c);
+    else if (method == HP_LOCAL_NIBLACK) t = __dadd_rn(m, __dmul_rn(k, sd));
+    else t = __dmul_rn(m, __dadd_rn(1.0, __dmul_rn(k, __dsub_rn(__ddiv_rn(sd, c), 1.0))));
+    const double f = (double)to_f32<TIN>(
+        in[((z - B.lo[0]) * B.dims[1] + (y - B.lo[1])) * B.dims[2] + (x - B.lo[2])]);
+    static_cast<uint8_t*>(O.ptr)[((z - O.lo[0]) * O.dims[1] + (y - O.lo[1])) * O.dims[2] +
+                                 (x - O.lo[2])] = f > t ? 1 : 0;
+  }
+}
+
+unsigned grid_for(int64_t t) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((t + kBlk - 1) / kBlk, (int64_t)num_sms() * 32));
+}
+
+template <typename TIN, typename S1, typename S2, bool FP>
+cudaError_t box_launch(const Job& job, int method, int w, double k, double c, cudaStream_t s) {
+  const SepRegions g = sep_regions(job, w);
+  const int64_t cz = job.core_hi[0] - job.core_lo[0], cy = job.core_hi[1] - job.core_lo[1],
+                cx = job.core_hi[2] - job.core_lo[2];
+  const int64_t vx = g.n_x[0] * g.n_x[1] * g.n_x[2], vy = g.n_y[0] * g.n_y[1] * g.n_y[2];
+  const size_t need = (sizeof(S1) + sizeof(S2)) * (size_t)(vx + vy) + 64;
+  if (!job.scratch || job.scratch_bytes < need) return cudaErrorInvalidValue;
+  // scratch: x-pass S2 | y-pass S2 | x-pass S1 | y-pass S1 (8-byte items first)
+  char* p = static_cast<char*>(job.scratch);
+  S2* a2 = reinterpret_cast<S2*>(p);
+  S2* b2 = a2 + vx;
+  S1* a1 = reinterpret_cast<S1*>(b2 + vy);
+  S1* b1 = a1 + vx;
+  const TIN* in = static_cast<const TIN*>(job.in.ptr);
+  const Reg rx{{g.rlo[0], g.rlo[1], job.core_lo[2]}, {g.n_x[0], g.n_x[1], g.n_x[2]}};
+  const Reg ry{{g.rlo[0], job.core_lo[1], job.core_lo[2]}, {g.n_y[0], g.n_y[1], g.n_y[2]}};
+  if constexpr (FP)
+    k_box_x_fp<TIN><<<grid_for(vx), kBlk, 0, s>>>(in, job.in, FSum{a1, a2}, g.n_x[0], g.n_x[1],
+                                                  g.n_x[2], g.rlo[0], g.rlo[1], job.core_lo[2],
+                                                  job.gdims[2], w);
+  else
+    k_box_x_int<TIN><<<grid_for(vx), kBlk, 0, s>>>(in, job.in, ISum{a1, a2}, g.n_x[0], g.n_x[1],
+                                                   g.n_x[2], g.rlo[0], g.rlo[1], job.core_lo[2],
+                                                   job.gdims[2], w);
+  k_box_y<S1, S2, FP><<<grid_for(vy), kBlk, 0, s>>>(a1, a2, rx, b1, b2, g.n_y[0], g.n_y[1], g.n_y[2],
+                                                    g.rlo[0], job.core_lo[1], job.core_lo[2],
+                                                    job.gdims[1], w);
+  k_box_z_decide<TIN, S1, S2, FP><<<grid_for(cz * cy * cx), kBlk, 0, s>>>(
+      b1, b2, ry, in, job.in, job.out, cz, cy, cx, job.core_lo[0], job.core_lo[1], job.core_lo[2],
+      job.gdims[0], w, method, k, c);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t hessian_eig_scratch(int64_t core_voxels) { return 6 * sizeof(float) * (size_t)core_voxels; }
+
+cudaError_t launch_hessian_eig(const float* comps, int64_t n, void* const* outs, int out_dtype,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_hessian_eig<<<grid_for(n), kBlk, 0, s>>>(comps, n, outs[0], outs[1], outs[2], out_dtype);
+  return cudaGetLastError();
+}
+
+size_t box_scratch_bytes(const Job& job, int w) {
+  const SepRegions g = sep_regions(job, w);
+  const int64_t vx = g.n_x[0] * g.n_x[1] * g.n_x[2], vy = g.n_y[0] * g.n_y[1] * g.n_y[2];
+  const bool fp = job.in.dtype == HP_F16 || job.in.dtype == HP_F32;
+  const size_t per = fp ? 16 : 12;
+  return per * (size_t)(vx + vy) + 64;
+}
+
+cudaError_t launch_threshold_box(const Job& job, int method, int w, double k, double c,
+                                 cudaStream_t s) {
+  if (job.core_hi[0] <= job.core_lo[0] || job.core_hi[1] <= job.core_lo[1] ||
+      job.core_hi[2] <= job.core_lo[2])
+    return cudaSuccess;
+  switch (job.in.dtype) {
+    case HP_U8: return box_launch<uint8_t, int32_t, int64_t, false>(job, method, w, k, c, s);
+    case HP_U16: return box_launch<uint16_t, int32_t, int64_t, false>(job, method, w, k, c, s);
+    case HP_F16: return box_launch<__half, double, double, true>(job, method, w, k, c, s);
+    case HP_F32: return box_launch<float, double, double, true>(job, method, w, k, c, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace hp

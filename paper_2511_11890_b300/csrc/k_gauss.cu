@@ -564,43 +564,6 @@ cudaError_t dispatch_zm(int r, const GaussParams& P, const CUtensorMap& map, dim
   }
 }
 
-// Regions of the generic three-pass path: after the x pass, z and y grown
-// to the hull of their reflected sources and x = core; after the y pass,
-// z grown and y, x = core.
-struct GenericRegions {
-  int64_t rlo[2];
-  int64_t n_x[3], n_y[3];
-};
-
-GenericRegions generic_regions(const Job& job, int r) {
-  GenericRegions g;
-  int64_t rhi[2];
-  for (int a = 0; a < 2; ++a) {
-    const int64_t n = job.gdims[a], lo = job.core_lo[a], hi = job.core_hi[a];
-    int64_t mn = n, mx = -1;
-    if (hi - lo + 2 * r >= 2 * n) {
-      mn = 0;
-      mx = n - 1;
-    } else {
-      for (int64_t c = lo - r; c < hi + r; ++c) {
-        const int64_t sidx = reflect(c, n);
-        mn = std::min(mn, sidx);
-        mx = std::max(mx, sidx);
-      }
-    }
-    g.rlo[a] = mn;
-    rhi[a] = mx + 1;
-  }
-  const int64_t cx = job.core_hi[2] - job.core_lo[2], cy = job.core_hi[1] - job.core_lo[1];
-  g.n_x[0] = rhi[0] - g.rlo[0];
-  g.n_x[1] = rhi[1] - g.rlo[1];
-  g.n_x[2] = cx;
-  g.n_y[0] = g.n_x[0];
-  g.n_y[1] = cy;
-  g.n_y[2] = cx;
-  return g;
-}
-
 bool needs_generic(const Job& job, int r) {
   return !(r >= 1 && r <= kMaxR && job.gdims[2] >= r && job.gdims[1] >= r);
 }
@@ -613,7 +576,7 @@ cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
   const int64_t cz = job.core_hi[0] - job.core_lo[0], cy = job.core_hi[1] - job.core_lo[1],
                 cx = job.core_hi[2] - job.core_lo[2];
   if (cz <= 0 || cy <= 0 || cx <= 0) return cudaSuccess;
-  const GenericRegions g = generic_regions(job, r);
+  const SepRegions g = sep_regions(job, r);
   const size_t b1 = sizeof(float) * (size_t)(g.n_x[0] * g.n_x[1] * g.n_x[2]);
   const size_t b2 = sizeof(float) * (size_t)(g.n_y[0] * g.n_y[1] * g.n_y[2]);
   if (!job.scratch || job.scratch_bytes < b1 + b2) return cudaErrorInvalidValue;
@@ -660,9 +623,41 @@ cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
 
 }  // namespace
 
+// Regions of a separable three-pass job of radius r: after the x pass, z
+// and y grown to the hull of their reflected sources and x = core; after
+// the y pass, z grown and y, x = core.
+SepRegions sep_regions(const Job& job, int r) {
+  SepRegions g;
+  int64_t rhi[2];
+  for (int a = 0; a < 2; ++a) {
+    const int64_t n = job.gdims[a], lo = job.core_lo[a], hi = job.core_hi[a];
+    int64_t mn = n, mx = -1;
+    if (hi - lo + 2 * r >= 2 * n) {
+      mn = 0;
+      mx = n - 1;
+    } else {
+      for (int64_t c = lo - r; c < hi + r; ++c) {
+        const int64_t sidx = reflect(c, n);
+        mn = std::min(mn, sidx);
+        mx = std::max(mx, sidx);
+      }
+    }
+    g.rlo[a] = mn;
+    rhi[a] = mx + 1;
+  }
+  const int64_t cx = job.core_hi[2] - job.core_lo[2], cy = job.core_hi[1] - job.core_lo[1];
+  g.n_x[0] = rhi[0] - g.rlo[0];
+  g.n_x[1] = rhi[1] - g.rlo[1];
+  g.n_x[2] = cx;
+  g.n_y[0] = g.n_x[0];
+  g.n_y[1] = cy;
+  g.n_y[2] = cx;
+  return g;
+}
+
 size_t gauss_scratch_bytes(const Job& job, int r) {
   if (!needs_generic(job, r)) return 0;
-  const GenericRegions g = generic_regions(job, r);
+  const SepRegions g = sep_regions(job, r);
   return sizeof(float) * (size_t)(g.n_x[0] * g.n_x[1] * g.n_x[2] + g.n_y[0] * g.n_y[1] * g.n_y[2]);
 }
 

@@ -1,9 +1,14 @@
-"""Multi-rank host logic on CPU (gloo, world size 2): the round-robin brick
-shard of the paper's multi-GPU chunk scheduling (Sec. III-D) reproduces the
-whole volume when each rank filters only its bricks, and the benchmark's
-whole-job reduction takes the slowest rank. The per-brick filtering here is
-the oracle's box mode (CPU); the GPU path runs the same bricks through the
-C ABI."""
+"""Multi-rank logic over gloo, world size 2: the round-robin brick shard of
+the paper's multi-GPU chunk scheduling (Sec. III-D) reproduces the whole
+volume when each rank filters only its bricks, and the benchmark's
+whole-job reduction takes the slowest rank.
+
+On CPU the per-brick filtering of each rank is the oracle's box mode over
+the planner's bricks. Where a CUDA device is present (the gpu-marked test),
+each rank runs its shard through libhp itself (hp_set_brick_shard on a host
+volume, out of core on cuda:0); the ranks' kernels never wait on each
+other, and the only exchange is the gather of the finished parts that the
+test makes."""
 import os
 import socket
 import sys
@@ -67,6 +72,36 @@ def _bricks_worker(rank, world, port, out_dir):
         dist.destroy_process_group()
 
 
+def _libhp_shard_worker(rank, world, port, out_dir):
+    _init(rank, world, port)
+    try:
+        import paper_2511_11890_b300 as hp
+        import synth
+        f = synth.porous((48, 64, 80), 7)[0]
+        hp.set_memory_budget(6_000_000)
+        hp.set_brick_shard(rank, world)
+        part = np.full(f.shape, np.nan, np.float32)
+        hp.gaussian3d(f, 1.5, out=part)               # host volume: this rank's bricks only
+        nb = hp.stats()["bricks"]
+        parts = [torch.empty(f.size, dtype=torch.float32) for _ in range(world)]
+        dist.all_gather(parts, torch.from_numpy(part.ravel()))
+        counts = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(counts, torch.tensor([nb], dtype=torch.int64))
+        if rank == 0:
+            whole = np.full(f.size, np.nan, np.float32)
+            covered = np.zeros(f.size, np.int32)
+            for p in parts:
+                p = p.numpy()
+                m = ~np.isnan(p)
+                whole[m] = p[m]
+                covered += m
+            np.save(os.path.join(out_dir, "whole.npy"), whole.reshape(f.shape))
+            np.save(os.path.join(out_dir, "covered.npy"), covered.reshape(f.shape))
+            np.save(os.path.join(out_dir, "counts.npy"), np.array([int(c) for c in counts]))
+    finally:
+        dist.destroy_process_group()
+
+
 def _reduce_worker(rank, world, port, out_dir):
     _init(rank, world, port)
     try:
@@ -89,6 +124,24 @@ def test_round_robin_bricks_reproduce_whole_volume(tmp_path):
     assert (covered == 1).all(), "every voxel belongs to exactly one rank's bricks"
     f = synth.porous((24, 40, 56), 7)[0]
     ref = oracle.gaussian3d(f, 1.5).astype(np.float32)
+    assert np.array_equal(whole.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.gpu
+def test_libhp_shards_over_gloo_ranks_reproduce_whole_volume(tmp_path):
+    """Two processes, each running its half of the bricks through libhp on
+    cuda:0; the union equals one process running every brick, bit for bit."""
+    hp = pytest.importorskip("paper_2511_11890_b300")
+    import synth
+    mp.start_processes(_libhp_shard_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2,
+                       start_method="spawn")
+    whole = np.load(tmp_path / "whole.npy")
+    covered = np.load(tmp_path / "covered.npy")
+    counts = np.load(tmp_path / "counts.npy")
+    assert (covered == 1).all(), "every voxel belongs to exactly one rank's bricks"
+    assert counts.min() >= 2 and abs(int(counts[0]) - int(counts[1])) <= 1
+    f = synth.porous((48, 64, 80), 7)[0]
+    ref = hp.gaussian3d(torch.from_numpy(f).cuda(), 1.5).cpu().numpy()
     assert np.array_equal(whole.view(np.uint32), ref.view(np.uint32))
 
 

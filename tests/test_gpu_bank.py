@@ -57,7 +57,13 @@ def test_bank_subset_and_errors():
     with pytest.raises(hp.HPError):
         hp.filterbank3d(x, [(hp.G, 1.0), (hp.G, 1.0)])        # duplicate
     with pytest.raises(hp.HPError):
-        hp.filterbank3d(f, [(hp.G, 1.0)])                      # host volume
+        hp.filterbank3d(f, [(hp.G, 1.0), (hp.G, 1.0)])        # duplicate, host volume
+    with pytest.raises(hp.HPError, match="HP_ERR_UNSUPPORTED"):
+        hp.filterbank3d(f, [(hp.G, 5.0)])                      # radius 15 > 12
+    # a host volume runs out of core with the same result
+    host = hp.filterbank3d(f, filt, out_dtype=hp.HP_F32)
+    for h, o in zip(host, outs):
+        assert np.array_equal(h.view(np.uint32), to_np(o).view(np.uint32))
 
 
 def test_bank_512_37_bricks_sampled():

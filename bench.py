@@ -13,6 +13,15 @@ inside the timed region).
 `--impl reference` times the CPU oracle (the test oracle, single-threaded
 FP64 C) on bounded sub-boxes of the same workload.
 
+The default line also carries, besides the step: the FP32 FMA roofline of
+the dominant kernel against the derived peak (this device's SM count x 128
+lanes x 2 x max clock) and libhp's measured FMA probe; `bank` (the 512^3
+float16 12-filter bank over 37 bricks, one graph launch); `ooc` (2048^3
+uint16 out of core under an 8e9-byte budget, with a host-link probe at each
+op's brick size and byte mix and the fraction of the link bound reached;
+`--no-ooc` skips it); and the oracle timed single-threaded (`cpu_baseline`)
+and as its OpenMP build on every host core (`cpu_baseline_mt`).
+
 Other measured configurations, one JSON line each (not the benchmark step):
 `--workload ooc2048` (2048^3 uint16 out-of-core under an 8e9-byte budget,
 host-link efficiency), `spheres128` (128^3 float32 Gaussian -> threshold ->
@@ -129,6 +138,47 @@ def _traffic(kernel: str, nvox: int):
         return (rec["dram_read_bytes"] + rec["dram_write_bytes"]) * nvox / rec["captured_voxels"]
     except Exception:
         return None
+
+
+def fma_peaks(hp, torch, sm_max_mhz: float):
+    """FP32 FMA ceilings in TFLOP/s: derived (SM count of this device x 128
+    FP32 lanes x 2 flop x max SM clock) and measured (libhp's FMA probe:
+    packed FMA chains on every SM, CUDA events)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    derived = sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+    measured = hp.probe_fp32_fma(5) / 1e12
+    return derived, measured, sms
+
+
+def bank_measure(hp, torch, synth, steps: int, warmup: int, peak_derived: float,
+                 peak_measured: float, hbm_gbs: float):
+    """The 512^3 float16 12-filter bank (G, GM, LoG at sigma 0.7, 1, 2, 4)
+    over 37 seeded k-d bricks, one graph launch per bank: ms per bank and
+    its FMA and HBM rooflines."""
+    n = 512
+    f = synth.porous_f16(n, synth.SEED_BASE + 3)
+    x = torch.from_numpy(f).cuda()
+    bank = [(k, s) for s in BANK_SIGMAS for k in (hp.G, hp.GM, hp.LOG)]
+    bricks = synth.kd_bricks(n, 37, synth.SEED_BASE + 3)
+    outs = [torch.empty((n, n, n), dtype=torch.float16, device="cuda") for _ in bank]
+    stream = torch.cuda.current_stream()
+    ms, clk = _timed(lambda: hp.filterbank3d(x, bank, outs=outs, bricks=bricks), steps,
+                     max(3, warmup), stream)
+    hp.stream_status(stream)
+    kernels = int(hp.stats()["bank_kernels"])
+    nvox = n ** 3
+    # per sigma, each pass 2r+1 taps: x pass 3 orders; y pass y0(X0), y0(X1),
+    # y1(X0), and y2(X0) + y0(X2) summed (5 passes); z pass G, D_z, D_zz,
+    # D_x, D_y and D_xx + D_yy (6): 14 passes
+    fma = sum(14 * (2 * int(np.floor(3 * s + 0.5)) + 1) for s in BANK_SIGMAS)
+    tflops = nvox * fma * 2 / (ms / 1e3) / 1e12
+    gbs = nvox * (2 + 2 * len(bank)) / (ms / 1e3) / 1e9
+    del outs, x
+    return {"ms": ms, "voxels_per_s": nvox / (ms / 1e3), "kernels_per_launch": kernels,
+            "fma_per_voxel": fma, "TFLOP/s": tflops, "alu_frac": tflops / peak_derived,
+            "alu_frac_of_measured": tflops / peak_measured, "GB/s": gbs,
+            "hbm_frac": gbs / hbm_gbs, "clocks": clk,
+            "workload": "porous 512^3 f16 -> 12 x f16 (G, GM, LoG at sigma 0.7/1/2/4), 37 k-d bricks"}
 
 
 def reduce_over_ranks(local_ms: float, ws: int, units_per_rank: float, device=None):
@@ -282,14 +332,15 @@ def run_hp(args):
     # per-kernel rooflines: algorithmic bytes (u16 in + out) and FP32 FMAs
     nvox = N ** 3
     kern = {}
-    fma_peak_tflops = 148 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+    fma_peak_tflops, fma_measured_tflops, sms = fma_peaks(hp, torch, sm_max_mhz)
     for s, nm in zip(SIGMAS, names):
         r = int(np.floor(3 * s + 0.5))
         byts = nvox * (2 + 4)
         flops = nvox * 3 * (2 * r + 1) * 2
         ms = per[nm]
         kern[nm] = {"ms": ms, "GB/s": byts / ms / 1e6, "hbm_frac": byts / ms / 1e6 / hbm_gbs,
-                    "TFLOP/s": flops / ms / 1e9, "alu_frac": flops / ms / 1e9 / fma_peak_tflops}
+                    "TFLOP/s": flops / ms / 1e9, "alu_frac": flops / ms / 1e9 / fma_peak_tflops,
+                    "alu_frac_of_measured": flops / ms / 1e9 / fma_measured_tflops}
     for nm in names[3:]:
         byts = nvox * 4
         ms = per[nm]
@@ -299,7 +350,11 @@ def run_hp(args):
     if "alu_frac" in dk and dk["alu_frac"] > dk["hbm_frac"]:
         roof = {"bound": "alu", "achieved": dk["TFLOP/s"], "peak": fma_peak_tflops,
                 "unit": "TFLOP/s", "frac": dk["alu_frac"], "traffic": None,
-                "kernel": dom, "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock"}
+                "kernel": dom,
+                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock",
+                "measured_peak": fma_measured_tflops,
+                "frac_of_measured": dk["alu_frac_of_measured"],
+                "measured_peak_kind": "libhp FMA probe (packed fma.rn.f32x2 chains, CUDA events)"}
     else:
         roof = {"bound": "hbm", "achieved": dk["GB/s"], "peak": hbm_gbs, "unit": "GB/s",
                 "frac": dk["hbm_frac"], "traffic": None, "kernel": dom, "peak_kind": peak_kind}
@@ -307,11 +362,18 @@ def run_hp(args):
     step_bytes = nvox * (3 * 6 + 2 * 4)
     hbm_step_frac = step_bytes / (total_ms / args.steps) / 1e6 / hbm_gbs
 
+    del outs_g, out_e, out_d
+    torch.cuda.empty_cache()
+    # configuration 4: the filter bank (one graph launch per bank)
+    bank = None
+    if rank == 0 and not args.no_bank:
+        bank = bank_measure(hp, torch, synth, args.steps, args.warmup, fma_peak_tflops,
+                            fma_measured_tflops, hbm_gbs)
+        torch.cuda.empty_cache()
+
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        del outs_g, out_e, out_d
-        torch.cuda.empty_cache()
         xh = torch.from_numpy(f).pin_memory()
         oh = [torch.empty((N, N, N), dtype=torch.float32).pin_memory() for _ in SIGMAS]
         eh = torch.empty((N, N, N), dtype=torch.uint16).pin_memory()
@@ -340,11 +402,30 @@ def run_hp(args):
         e2e = {"value": ws * ke * nvox / dt, "unit": "voxels/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke,
                "link_GB/s": (h2d + d2h) / (dt / ke) / 1e9}
+        del xh, oh, eh, dh
 
-    cpu = None
+    # configuration 3: out of core at 2048^3 under an 8e9-byte budget
+    ooc = None
+    if rank == 0 and not args.no_ooc:
+        del x
+        torch.cuda.empty_cache()
+        ooc = ooc_measure(hp, torch, steps=2)
+
+    cpu = cpu_mt = None
     if rank == 0 and ws == 1 and not args.no_cpu:
+        nproc = os.cpu_count() or 1
         v, sample = cpu_oracle_sample(args.cpu_seconds)
-        cpu = {"value": v, "unit": "voxels/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "voxels/s", "cores": 1, "kind": "oracle", "sample": sample,
+               "nproc": nproc}
+        import oracle
+        oracle.use_threads(True)
+        try:
+            v, sample = cpu_oracle_sample(max(4.0, args.cpu_seconds / 2))
+        finally:
+            oracle.use_threads(False)
+        cpu_mt = {"value": v, "unit": "voxels/s", "cores": nproc,
+                  "kind": "oracle, the same source built with OpenMP over z", "sample": sample,
+                  "nproc": nproc}
 
     if rank == 0:
         line = {
@@ -356,8 +437,9 @@ def run_hp(args):
                        "volume": [N, N, N], "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs (2 GiB) and outputs (16 GiB) larger than L2",
                        "hbm_frac_of_step": hbm_step_frac},
-            "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 5 * args.steps, "clocks": clk.summary(),
+            "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "cpu_baseline_mt": cpu_mt,
+            "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk.summary(),
+            "bank": bank, "ooc": ooc,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -365,39 +447,98 @@ def run_hp(args):
     return 0
 
 
-def link_probe(nbytes: int, reps: int = 3):
-    """Pinned host <-> device copy bandwidth (GB/s) at one chunk size: H2D
-    alone, D2H alone, and both at once on two streams."""
+def link_probe(chunk: int, d2h_per_h2d: float, seconds: float = 1.0):
+    """Pinned host <-> device copy rates (GB/s) with chunks of the brick
+    size, each leg for at least `seconds`: H2D alone, D2H alone, and both
+    directions at once with D2H bytes = d2h_per_h2d x H2D bytes (the mix of
+    the operation being measured), two streams per direction. The link
+    bound of an operation moving (h, d) bytes is then
+    max(h / h2d, d / d2h, (h + d) / both) seconds."""
     import torch
-    h1 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
-    h2 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
-    d1 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    d2 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    dchunk = max(1 << 20, int(chunk * d2h_per_h2d) // 4096 * 4096)
+    hs = [torch.empty(chunk, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    ds = [torch.empty(chunk, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    hd = [torch.empty(dchunk, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    dd = [torch.empty(dchunk, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    st = [torch.cuda.Stream() for _ in range(4)]
 
-    def timed(fn):
-        best = 1e30
-        for _ in range(reps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
+    def run(h2d: bool, d2h: bool):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nb_h = nb_d = 0
+        i = 0
+        while True:
+            if h2d:
+                with torch.cuda.stream(st[i % 2]):
+                    ds[i % 2].copy_(hs[i % 2], non_blocking=True)
+                nb_h += chunk
+            if d2h:
+                with torch.cuda.stream(st[2 + i % 2]):
+                    hd[i % 2].copy_(dd[i % 2], non_blocking=True)
+                nb_d += dchunk
+            i += 1
+            if i % 4 == 0:
+                torch.cuda.synchronize()
+                if time.perf_counter() - t0 >= seconds:
+                    break
+        dt = time.perf_counter() - t0
+        return nb_h / dt / 1e9, nb_d / dt / 1e9
+
+    run(True, True)  # warm-up
+    h2d, _ = run(True, False)
+    _, d2h = run(False, True)
+    bh, bd = run(True, True)
+    return {"chunk_bytes": chunk, "h2d": h2d, "d2h": d2h, "both_h2d": bh, "both_d2h": bd,
+            "both_total": bh + bd, "d2h_per_h2d": dchunk / chunk}
+
+
+def link_bound_s(h2d_bytes: int, d2h_bytes: int, probe: dict) -> float:
+    """Seconds the host link needs for these bytes at the probe's rates."""
+    return max(h2d_bytes / 1e9 / probe["h2d"], d2h_bytes / 1e9 / probe["d2h"],
+               (h2d_bytes + d2h_bytes) / 1e9 / probe["both_total"])
+
+
+def ooc_measure(hp, torch, f=None, steps: int = 2):
+    """Out-of-core 2048^3 uint16 (pinned host buffers, budget 8e9 B):
+    Gaussian sigma 3 (f32) and ball-5 dilation (u16); per op the best of
+    `steps` timed calls after one warm-up, the bytes moved, the link probe
+    at the op's brick size and byte mix, and the fraction of the link bound
+    reached."""
+    import synth
+    n, budget = 2048, 8_000_000_000
+    if f is None:
+        f, _ = synth.porous(n, 2511118900 + 2)
+    xh = torch.from_numpy(f).pin_memory()
+    del f
+    og = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+    od = torch.empty((n, n, n), dtype=torch.uint16).pin_memory()
+    old = hp.get_memory_budget()
+    hp.set_memory_budget(budget)
+    res = {}
+    try:
+        for name, fn in (("gauss_s3", lambda: hp.gaussian3d(xh, 3.0, out=og)),
+                         ("dilate_ball5", lambda: hp.dilate3d(xh, "ball", 5, out=od))):
             fn()
-            torch.cuda.synchronize()
-            best = min(best, time.perf_counter() - t0)
-        return best
-
-    def h2d():
-        with torch.cuda.stream(s1):
-            d1.copy_(h1, non_blocking=True)
-
-    def d2h():
-        with torch.cuda.stream(s2):
-            h2.copy_(d2, non_blocking=True)
-
-    t_h2d, t_d2h = timed(h2d), timed(d2h)
-    t_both = timed(lambda: (h2d(), d2h()))
-    gb = nbytes / 1e9
-    return {"h2d": gb / t_h2d, "d2h": gb / t_d2h, "concurrent_h2d": gb / t_both,
-            "concurrent_d2h": gb / t_both}
+            times = []
+            for _ in range(max(1, steps)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                times.append(time.perf_counter() - t0)
+            st = hp.stats()
+            dt = min(times)
+            chunk = int(min(1 << 30, max(1 << 26, st["h2d_bytes"] // max(1, st["bricks"]))))
+            probe = link_probe(chunk // 4096 * 4096, st["d2h_bytes"] / max(1, st["h2d_bytes"]))
+            bound = link_bound_s(st["h2d_bytes"], st["d2h_bytes"], probe)
+            res[name] = {"s": dt, "voxels_per_s": n ** 3 / dt, "bricks": st["bricks"],
+                         "h2d_bytes": st["h2d_bytes"], "d2h_bytes": st["d2h_bytes"],
+                         "peak_device_bytes": st["peak_device_bytes"], "budget_bytes": budget,
+                         "link_GBps": (st["h2d_bytes"] + st["d2h_bytes"]) / dt / 1e9,
+                         "probe_GBps": probe, "link_bound_s": bound, "link_frac": bound / dt}
+    finally:
+        hp.set_memory_budget(old)
+        del xh, og, od
+    return res
 
 
 def run_outofcore(args):
@@ -407,34 +548,8 @@ def run_outofcore(args):
     import torch
 
     import paper_2511_11890_b300 as hp
-    import synth
-    n, budget = 2048, 8_000_000_000
-    f, _ = synth.porous(n, 2511118900 + 2)
-    xh = torch.from_numpy(f).pin_memory()
-    del f
-    og = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
-    od = torch.empty((n, n, n), dtype=torch.uint16).pin_memory()
-    hp.set_memory_budget(budget)
-    res = {}
-    for name, fn in (("gauss_s3", lambda: hp.gaussian3d(xh, 3.0, out=og)),
-                     ("dilate_ball5", lambda: hp.dilate3d(xh, "ball", 5, out=od))):
-        fn()  # warm-up (pins nothing new; output buffers are already pinned)
-        times = []
-        for _ in range(max(1, args.steps)):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            fn()
-            times.append(time.perf_counter() - t0)
-        st = hp.stats()
-        dt = min(times)
-        probe = link_probe(min(1 << 30, max(1 << 26, st["h2d_bytes"] // max(1, st["bricks"]))))
-        ideal = max(st["h2d_bytes"] / 1e9 / probe["concurrent_h2d"],
-                    st["d2h_bytes"] / 1e9 / probe["concurrent_d2h"])
-        res[name] = {"s": dt, "voxels_per_s": n ** 3 / dt, "bricks": st["bricks"],
-                     "h2d_bytes": st["h2d_bytes"], "d2h_bytes": st["d2h_bytes"],
-                     "peak_device_bytes": st["peak_device_bytes"],
-                     "link_GBps": (st["h2d_bytes"] + st["d2h_bytes"]) / dt / 1e9,
-                     "probe_GBps": probe, "link_efficiency": ideal / dt}
+    n = 2048
+    res = ooc_measure(hp, torch, steps=args.steps)
     total = sum(v["s"] for v in res.values())
     line = {"metric": "voxels/s, out-of-core 2048^3 uint16 under an 8e9-byte budget "
                       "(gaussian s=3 + ball-5 dilation); % of host link",
@@ -600,41 +715,20 @@ def run_bank512(args):
 
     import paper_2511_11890_b300 as hp
     import synth
-    n = 512
-    f = synth.porous_f16(n, synth.SEED_BASE + 3)
-    x = torch.from_numpy(f).cuda()
-    bank = [(k, s) for s in BANK_SIGMAS for k in (hp.G, hp.GM, hp.LOG)]
-    bricks = synth.kd_bricks(n, 37, synth.SEED_BASE + 3)
-    outs = [torch.empty((n, n, n), dtype=torch.float16, device="cuda") for _ in bank]
-    stream = torch.cuda.current_stream()
-
-    def step():
-        hp.filterbank3d(x, bank, outs=outs, bricks=bricks)
-
-    ms, clk = _timed(step, args.steps, max(3, args.warmup), stream)
-    hp.stream_status(stream)
-    kernels = int(hp.stats()["bank_kernels"])  # persistent kernels per bank launch
-    nvox = n ** 3
-    # per sigma, each pass 2r+1 taps: x pass 3 orders; y pass y0(X0), y0(X1),
-    # y1(X0), and y2(X0) + y0(X2) summed (5 passes); z pass G, D_z, D_zz,
-    # D_x, D_y and D_xx + D_yy (6): 14 passes
-    fma = sum(14 * (2 * int(np.floor(3 * s + 0.5)) + 1) for s in BANK_SIGMAS)
-    _, sm_max_mhz, _ = _peaks()
-    peak = 148 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
-    hbm_gbs, _, peak_kind = _peaks()
-    tflops = nvox * fma * 2 / (ms / 1e3) / 1e12
-    gbs = nvox * (2 + 2 * len(bank)) / (ms / 1e3) / 1e9
+    hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+    derived, measured, sms = fma_peaks(hp, torch, sm_max_mhz)
+    b = bank_measure(hp, torch, synth, args.steps, args.warmup, derived, measured, hbm_gbs)
     line = {"metric": "voxels/s, 512^3 float16 12-filter bank (G, GM, LoG at sigma 0.7/1/2/4), 37 bricks",
-            "value": nvox / (ms / 1e3), "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
-            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32 (f16 storage)",
+            "value": b["voxels_per_s"], "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
+            "ms_per_step": b["ms"], "higher_is_better": True, "dtype": "f32 (f16 storage)",
             "data": "synthetic porous tomogram (seeded), 37 seeded k-d bricks",
-            "config": {"workload": "porous 512^3 f16 -> 12 x f16, one graph launch per bank "
-                                   f"({kernels} persistent kernel{'s' if kernels > 1 else ''})"},
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                         "frac": tflops / peak, "fma_per_voxel": fma,
-                         "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock",
-                         "hbm": {"GB/s": gbs, "frac": gbs / hbm_gbs, "peak_kind": peak_kind}},
-            "gpu_launches": kernels * args.steps, "clocks": clk}
+            "config": {"workload": b["workload"] + f", {b['kernels_per_launch']} persistent kernel(s) per launch"},
+            "roofline": {"bound": "alu", "achieved": b["TFLOP/s"], "peak": derived, "unit": "TFLOP/s",
+                         "frac": b["alu_frac"], "fma_per_voxel": b["fma_per_voxel"],
+                         "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 x max SM clock",
+                         "measured_peak": measured, "frac_of_measured": b["alu_frac_of_measured"],
+                         "hbm": {"GB/s": b["GB/s"], "frac": b["hbm_frac"], "peak_kind": peak_kind}},
+            "gpu_launches": b["kernels_per_launch"] * args.steps, "clocks": b["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -683,6 +777,8 @@ def main():
     ap.add_argument("--impl", default="hp", choices=["hp", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-bank", action="store_true", help="skip the 512^3 filter-bank leg")
+    ap.add_argument("--no-ooc", action="store_true", help="skip the 2048^3 out-of-core leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="porous1024",
                     choices=["porous1024", "ooc2048", "spheres128", "bank512", "autograd256",

@@ -322,6 +322,14 @@ int hp_stream_status(void* stream);
  * or unbounded spin is involved. Returns HP_OK or HP_ERR_CUDA (launch). */
 int hp_selftest_wait_timeout(void* stream);
 
+/* Diagnostic (the paper has no counterpart): measures the FP32 FMA
+ * throughput of the current device, the ceiling the FMA-bound filters
+ * (large-radius Gaussians, the filter bank) are compared against. Runs
+ * independent packed fma.rn.f32x2 chains on every SM, `repeats` timed
+ * launches on `stream` (after one warm-up), and writes the best rate in
+ * FLOP/s (2 per FMA). Synchronises `stream`. */
+int hp_probe_fp32_fma(void* stream, int repeats, double* flops_per_s);
+
 /* Free cached filter-bank launch plans (graphs and work lists) and forget
  * cached per-device addresses of library device variables (call it after a
  * cudaDeviceReset). */

@@ -27,7 +27,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_MT = os.path.join(_HERE, "liboracle_mt.so")
 _lib = None
+_libs = {}
 
 U8, U16, F16, F32, F64 = 0, 1, 2, 3, 4
 SE_CUBE, SE_BALL = 0, 1
@@ -41,20 +43,36 @@ class OracleError(RuntimeError):
     pass
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc if it is missing or stale."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, threads: bool = False) -> str:
+    """Compile liboracle.so (single-threaded) or, with threads=True,
+    liboracle_mt.so (the same source with -fopenmp) if missing or stale."""
+    out = _LIB_MT if threads else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared",
-                               "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               "-fPIC", *(["-fopenmp"] if threads else []), "-o", tmp, _SRC,
+                               "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def use_threads(on: bool):
+    """Route the functions below to the OpenMP build (on) or the
+    single-threaded build (off, the default); results are identical."""
+    global _lib
+    _lib = _open(bool(on))
 
 
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        _lib = _open(False)
+    return _lib
+
+
+def _open(threads: bool):
+    if threads not in _libs:
+        lib = ctypes.CDLL(build(threads=threads))
         vp, i64, d, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
         p3 = ctypes.POINTER(ctypes.c_int64)
         lib.orc_reflect.argtypes = [i64, i64]
@@ -71,8 +89,8 @@ def _load():
         lib.orc_morph3d_vjp.argtypes = [vp, i, p3, i, i, i, vp, vp, vp]
         lib.orc_box_sums.argtypes = [vp, i, p3, i, vp, vp]
         lib.orc_threshold_box.argtypes = [vp, i, p3, i, i, d, d, vp, vp]
-        _lib = lib
-    return _lib
+        _libs[threads] = lib
+    return _libs[threads]
 
 
 def _check(rc: int):

@@ -32,7 +32,7 @@ EXPORTS = [
     "hp_morph3d_backward",
     "hp_morph3d_backward_noalloc", "hp_set_devices", "hp_get_devices", "hp_set_brick_shard",
     "hp_plan_bricks",
-    "hp_stream_status", "hp_selftest_wait_timeout", "hp_release_cache", "hp_get_stats", "hp_last_error", "hp_version",
+    "hp_stream_status", "hp_selftest_wait_timeout", "hp_probe_fp32_fma", "hp_release_cache", "hp_get_stats", "hp_last_error", "hp_version",
 ]
 
 
@@ -93,6 +93,7 @@ def _load() -> ctypes.CDLL:
                            ctypes.POINTER(hp_box), i, ctypes.POINTER(i)],
         "hp_stream_status": [vp],
         "hp_selftest_wait_timeout": [vp],
+        "hp_probe_fp32_fma": [vp, i, ctypes.POINTER(d)],
         "hp_release_cache": [],
         "hp_get_stats": [ctypes.POINTER(hp_stats)],
     }

@@ -334,6 +334,14 @@ def selftest_wait_timeout(stream=None):
     check(lib.hp_selftest_wait_timeout(ctypes.c_void_p(s.cuda_stream)))
 
 
+def probe_fp32_fma(repeats: int = 5, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device (FLOP/s)."""
+    s = stream if stream is not None else torch.cuda.current_stream()
+    v = ctypes.c_double(0.0)
+    check(lib.hp_probe_fp32_fma(ctypes.c_void_p(s.cuda_stream), int(repeats), ctypes.byref(v)))
+    return v.value
+
+
 def stats() -> dict:
     s = hp_stats()
     check(lib.hp_get_stats(ctypes.byref(s)))

@@ -33,3 +33,15 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     got = to_np(hp.gaussian3d(to_dev(f), 1.0))
     assert_filter_close(got, oracle.gaussian3d(f, 1.0), "after timeout")
     hp.stream_status()
+
+
+def test_fp32_fma_probe_is_plausible():
+    """The measured FP32 FMA rate lies between a quarter of and just above
+    the derived peak (SMs x 128 lanes x 2 flop x max clock)."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    rate = hp.probe_fp32_fma(3)
+    derived = props.multi_processor_count * 128 * 2 * 2.2e9   # a clock above every B300 boost
+    assert 0.25 * derived * (1.9 / 2.2) < rate < 1.05 * derived, rate
+    with pytest.raises(hp.HPError):
+        hp.probe_fp32_fma(0)

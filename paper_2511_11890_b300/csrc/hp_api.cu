@@ -960,6 +960,10 @@ static int morph(const hp_volume* in, hp_volume* out, hp_se se, int radius, void
   Op op;
   op.halo = radius;
   op.out_dtype = out->dtype;
+  if (morph_scratch_bytes(whole_job(in, out, out->dtype), (int)se, radius) > 0) {
+    op.scratch_per_in_voxel = 8;
+    op.scratch_bytes = [se, radius](const Job& j) { return morph_scratch_bytes(j, (int)se, radius); };
+  }
   op.launch = [se, radius, dil](const Job& j, void* const*, cudaStream_t s) {
     return launched(launch_morph(j, (int)se, radius, dil, s));
   };

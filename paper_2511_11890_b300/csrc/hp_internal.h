@@ -124,6 +124,11 @@ size_t gauss_scratch_bytes(const Job& job, int r);
 cudaError_t launch_gauss(const Job& job, const Taps& taps, cudaStream_t s);
 cudaError_t launch_gauss_zr(const Job& job, const Taps& taps, cudaStream_t s);
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
+// Scratch bytes launch_morph needs in job.scratch: the van Herk / Gil-Werman
+// cube passes (radii above the tiled kernels' limit, or volumes thinner than
+// the radius) keep two key regions (sep_regions), 8 bytes per input voxel at
+// most; 0 on the other paths.
+size_t morph_scratch_bytes(const Job& job, int se, int rad);
 cudaError_t launch_morph16(const Job& job, int se, int rad, int is_dilate, cudaStream_t s);
 cudaError_t launch_threshold(const Job& job, double t, cudaStream_t s);
 

@@ -674,6 +674,185 @@ cudaError_t launch_local_threshold(const void* f, int dtype, const float* m, flo
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- van Herk / Gil-Werman
+// Cube erosion / dilation as three line passes (x, y, z), each a running
+// min of keys over windows of 2L + 1 reflected samples by the van Herk /
+// Gil-Werman scheme: the extended line is cut into blocks of 2L + 1, and
+// per block the prefix minima G and suffix minima H are formed; the window
+// starting at j is then min(H[j], G[j + 2L]) (it spans at most two adjacent
+// blocks). Three comparisons per sample and axis, whatever L.
+//
+// A CTA takes kVL lines x kVS outputs of one axis: it stages the kVS + 2L
+// reflected samples of each line in shared memory (keys), scans the blocks
+// (one thread per block) and writes the outputs. The x and y passes write
+// keys to scratch regions (sep_regions); the z pass writes the output dtype.
+namespace {
+constexpr int kVL = 32;   // lines per CTA
+constexpr int kVS = 128;  // outputs per line per CTA
+constexpr int kVT = 256;  // threads per CTA
+
+struct VBox {
+  int64_t lo[3], dims[3];  // dense box of the global volume
+};
+
+// Source of a pass: the job's input (element type TIN, keys formed and
+// flipped on load) or a key scratch region (TIN = uint32_t, keys as stored).
+template <typename TIN, bool RAW, int AXIS>
+__global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, VBox S,
+                                                   void* __restrict__ dst, VBox D, int dst_dtype,
+                                                   int L, int64_t Gn, uint32_t flip,
+                                                   int64_t nlines, int64_t nseg) {
+  constexpr int axis = AXIS;
+  extern __shared__ uint32_t vsm[];
+  const int W = kVS + 2 * L;  // staged samples per line
+  uint32_t* E = vsm;
+  uint32_t* G = E + kVL * W;
+  uint32_t* H = G + kVL * W;
+  const int64_t line0 = (int64_t)blockIdx.x * kVL;
+  const int64_t seg0 = (int64_t)blockIdx.y * kVS;  // first output along the axis (region index)
+  const int tid = threadIdx.x;
+  // region of this pass = D's box; lines enumerate the other two axes of D
+  // (x fastest), so consecutive lines are consecutive x for the y and z passes
+  constexpr int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;  // the other axes, slow then fast
+  auto line_coords = [&](int64_t l, int64_t c[3]) {
+    c[a2] = D.lo[a2] + l % D.dims[a2];
+    c[a1] = D.lo[a1] + l / D.dims[a2];
+  };
+  // stage: along x, consecutive threads walk a line; along y and z they walk
+  // the lines (adjacent x)
+  for (int i = tid; i < kVL * W; i += kVT) {
+    int ln, pos;
+    if (axis == 2) {
+      ln = i / W;
+      pos = i % W;
+    } else {
+      ln = i % kVL;
+      pos = i / kVL;
+    }
+    const int64_t l = line0 + ln;
+    uint32_t key = 0xFFFFFFFFu;  // identity of min: samples no output reads
+    if (l < nlines && seg0 + pos < nseg + 2 * L) {
+      int64_t c[3];
+      line_coords(l, c);
+      c[axis] = reflect(D.lo[axis] + seg0 - L + pos, Gn);
+      const int64_t q = ((c[0] - S.lo[0]) * S.dims[1] + (c[1] - S.lo[1])) * S.dims[2] + (c[2] - S.lo[2]);
+      if constexpr (RAW) key = to_key<TIN>(src[q]) ^ flip;
+      else key = (uint32_t)src[q];
+    }
+    E[ln * W + pos] = key;
+  }
+  __syncthreads();
+  // prefix / suffix minima per block of k = 2L + 1 samples
+  const int k = 2 * L + 1;
+  const int nb = (W + k - 1) / k;
+  for (int t = tid; t < kVL * nb; t += kVT) {
+    const int ln = t / nb, b0 = (t % nb) * k, b1 = min(b0 + k, W);
+    const uint32_t* e = E + ln * W;
+    uint32_t* g = G + ln * W;
+    uint32_t* h = H + ln * W;
+    uint32_t m = 0xFFFFFFFFu;
+    for (int j = b0; j < b1; ++j) {
+      m = min(m, e[j]);
+      g[j] = m;
+    }
+    m = 0xFFFFFFFFu;
+    for (int j = b1 - 1; j >= b0; --j) {
+      m = min(m, e[j]);
+      h[j] = m;
+    }
+  }
+  __syncthreads();
+  // outputs: window [o, o + 2L] of the staged line
+  for (int i = tid; i < kVL * kVS; i += kVT) {
+    int ln, o;
+    if (axis == 2) {
+      ln = i / kVS;
+      o = i % kVS;
+    } else {
+      ln = i % kVL;
+      o = i / kVL;
+    }
+    const int64_t l = line0 + ln;
+    if (l >= nlines || seg0 + o >= nseg) continue;
+    const uint32_t m = min(H[ln * W + o], G[ln * W + o + 2 * L]);
+    int64_t c[3];
+    line_coords(l, c);
+    c[axis] = D.lo[axis] + seg0 + o;
+    const int64_t q = ((c[0] - D.lo[0]) * D.dims[1] + (c[1] - D.lo[1])) * D.dims[2] + (c[2] - D.lo[2]);
+    switch (dst_dtype) {
+      case -1: static_cast<uint32_t*>(dst)[q] = m; break;  // keys (scratch)
+      case HP_U8: static_cast<uint8_t*>(dst)[q] = from_key<uint8_t>(m ^ flip); break;
+      case HP_U16: static_cast<uint16_t*>(dst)[q] = from_key<uint16_t>(m ^ flip); break;
+      case HP_F16: static_cast<__half*>(dst)[q] = from_key<__half>(m ^ flip); break;
+      default: static_cast<float*>(dst)[q] = from_key<float>(m ^ flip); break;
+    }
+  }
+}
+
+size_t vhgw_smem(int L) { return (size_t)3 * kVL * (kVS + 2 * L) * sizeof(uint32_t); }
+
+template <typename TIN, bool RAW, int AXIS>
+cudaError_t vhgw_launch(const TIN* src, const VBox& S, void* dst, const VBox& D, int dst_dtype,
+                        int L, int64_t Gn, uint32_t flip, cudaStream_t s) {
+  constexpr int a1 = AXIS == 0 ? 1 : 0, a2 = AXIS == 2 ? 1 : 2;
+  const int64_t nlines = D.dims[a1] * D.dims[a2], nseg = D.dims[AXIS];
+  if (nlines <= 0 || nseg <= 0) return cudaSuccess;
+  const size_t smem = vhgw_smem(L);
+  static bool attr = false;  // per instantiation
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_vhgw_pass<TIN, RAW, AXIS>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)vhgw_smem(kMaxMorphR));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid((unsigned)((nlines + kVL - 1) / kVL), (unsigned)((nseg + kVS - 1) / kVS));
+  k_vhgw_pass<TIN, RAW, AXIS><<<grid, kVT, smem, s>>>(src, S, dst, D, dst_dtype, L, Gn, flip,
+                                                      nlines, nseg);
+  return cudaGetLastError();
+}
+
+template <typename TIN>
+cudaError_t vhgw_cube(const Job& job, int rad, int is_dilate, cudaStream_t s) {
+  const SepRegions g = sep_regions(job, rad);
+  const int64_t vx = g.n_x[0] * g.n_x[1] * g.n_x[2], vy = g.n_y[0] * g.n_y[1] * g.n_y[2];
+  if (!job.scratch || job.scratch_bytes < 4 * (size_t)(vx + vy)) return cudaErrorInvalidValue;
+  uint32_t* k1 = static_cast<uint32_t*>(job.scratch);
+  uint32_t* k2 = k1 + vx;
+  const uint32_t flip = is_dilate ? KeyMask<TIN>::value : 0u;
+  const VBox in{{job.in.lo[0], job.in.lo[1], job.in.lo[2]}, {job.in.dims[0], job.in.dims[1], job.in.dims[2]}};
+  const VBox rx{{g.rlo[0], g.rlo[1], job.core_lo[2]}, {g.n_x[0], g.n_x[1], g.n_x[2]}};
+  const VBox ry{{g.rlo[0], job.core_lo[1], job.core_lo[2]}, {g.n_y[0], g.n_y[1], g.n_y[2]}};
+  const VBox out{{job.out.lo[0], job.out.lo[1], job.out.lo[2]},
+                 {job.out.dims[0], job.out.dims[1], job.out.dims[2]}};
+  const VBox core{{job.core_lo[0], job.core_lo[1], job.core_lo[2]},
+                  {job.core_hi[0] - job.core_lo[0], job.core_hi[1] - job.core_lo[1],
+                   job.core_hi[2] - job.core_lo[2]}};
+  cudaError_t e = vhgw_launch<TIN, true, 2>(static_cast<const TIN*>(job.in.ptr), in, k1, rx, -1,
+                                            rad, job.gdims[2], flip, s);
+  if (e == cudaSuccess)
+    e = vhgw_launch<uint32_t, false, 1>(k1, rx, k2, ry, -1, rad, job.gdims[1], 0u, s);
+  if (e != cudaSuccess) return e;
+  // z pass: region = core, written into the output box (which contains it)
+  if (core.lo[0] == out.lo[0] && core.lo[1] == out.lo[1] && core.lo[2] == out.lo[2] &&
+      core.dims[0] == out.dims[0] && core.dims[1] == out.dims[1] && core.dims[2] == out.dims[2])
+    return vhgw_launch<uint32_t, false, 0>(k2, ry, job.out.ptr, out, job.out.dtype, rad,
+                                           job.gdims[0], flip, s);
+  return cudaErrorInvalidValue;  // output boxes equal the core on every path that gets here
+}
+}  // namespace
+
+bool morph_uses_vhgw(const Job& job, int se, int rad) {
+  return se == HP_SE_CUBE && rad >= 1 &&
+         !(rad <= kMaxTiledR && job.gdims[2] >= rad && job.gdims[1] >= rad);
+}
+
+size_t morph_scratch_bytes(const Job& job, int se, int rad) {
+  if (!morph_uses_vhgw(job, se, rad)) return 0;
+  const SepRegions g = sep_regions(job, rad);
+  return 4 * (size_t)(g.n_x[0] * g.n_x[1] * g.n_x[2] + g.n_y[0] * g.n_y[1] * g.n_y[2]);
+}
+
 cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStream_t s) {
   const int64_t cx = job.core_hi[2] - job.core_lo[2];
   const int64_t cy = job.core_hi[1] - job.core_lo[1];
@@ -684,6 +863,15 @@ cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStr
   if (e16 != cudaErrorNotSupported) return e16;
   const int ball = se == HP_SE_BALL;
   const bool tiled = rad >= 1 && rad <= kMaxTiledR && job.gdims[2] >= rad && job.gdims[1] >= rad;
+  if (!tiled && morph_uses_vhgw(job, se, rad)) {
+    switch (job.in.dtype) {
+      case HP_U8: return vhgw_cube<uint8_t>(job, rad, is_dilate, s);
+      case HP_U16: return vhgw_cube<uint16_t>(job, rad, is_dilate, s);
+      case HP_F16: return vhgw_cube<__half>(job, rad, is_dilate, s);
+      case HP_F32: return vhgw_cube<float>(job, rad, is_dilate, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (!tiled) {
     const int64_t total = cx * cy * cz;
     const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)num_sms() * 32);

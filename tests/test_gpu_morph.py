@@ -105,3 +105,44 @@ def test_full_size_sampled_ball3_1024():
             got = y[lo[0]:lo[0] + 8, lo[1]:lo[1] + 8, lo[2]:lo[2] + 8].cpu().numpy()
             assert np.array_equal(got, ref), (dil, lo)
         del y
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.float16, np.float32])
+@pytest.mark.parametrize("rad", [7, 9, 12, 16])
+def test_cube_large_radius_van_herk(dtype, rad):
+    """Cube radii above the tiled kernels run three van Herk / Gil-Werman
+    line passes: bit-exact against the oracle's brute force, on a volume
+    with ragged line tiles (130 = 128 + 2 outputs along x) and extents
+    shorter than the window (every sample reflected several times)."""
+    for shape in [(21, 35, 130), (5, 40, 9)]:
+        f = rand_volume(dtype, shape, 30 + rad)
+        x = to_dev(f)
+        e = to_np(hp.erode3d(x, "cube", rad))
+        d = to_np(hp.dilate3d(x, "cube", rad))
+        assert np.array_equal(e.view(np.uint8), oracle.erode3d(f, oracle.SE_CUBE, rad).view(np.uint8))
+        assert np.array_equal(d.view(np.uint8), oracle.dilate3d(f, oracle.SE_CUBE, rad).view(np.uint8))
+
+
+@pytest.mark.parametrize("rad", [2, 4])
+def test_cube_thin_volume_van_herk(rad):
+    """Volumes thinner than the radius in y skip the tiled kernels; the cube
+    takes the line passes there as well."""
+    f = rand_volume(np.float32, (12, rad - 1 if rad > 2 else 1, 50), 40 + rad)
+    x = to_dev(f)
+    assert np.array_equal(to_np(hp.erode3d(x, "cube", rad)), oracle.erode3d(f, oracle.SE_CUBE, rad))
+    assert np.array_equal(to_np(hp.dilate3d(x, "cube", rad)), oracle.dilate3d(f, oracle.SE_CUBE, rad))
+
+
+def test_cube_van_herk_out_of_core_within_budget():
+    f = synth.porous((80, 96, 112), 33)[0]
+    budget = 12_000_000
+    old = hp.get_memory_budget()
+    try:
+        hp.set_memory_budget(budget)
+        host = hp.erode3d(f, "cube", 9)
+        st = hp.stats()
+    finally:
+        hp.set_memory_budget(old)
+    assert st["bricks"] >= 4 and 0 < st["peak_device_bytes"] <= budget and st["live_device_bytes"] == 0
+    assert np.array_equal(host, to_np(hp.erode3d(to_dev(f), "cube", 9)))
+    assert np.array_equal(host, oracle.erode3d(f, oracle.SE_CUBE, 9))

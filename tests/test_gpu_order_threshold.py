@@ -47,7 +47,7 @@ def _bits(a):
 @pytest.mark.parametrize("dtype", [np.float16, np.float32])
 @pytest.mark.parametrize("shape", [(9, 13, 64), (12, 33, 72), (6, 5, 8)])
 @pytest.mark.parametrize("se,rad", [(oracle.SE_CUBE, 1), (oracle.SE_BALL, 2), (oracle.SE_BALL, 3),
-                                    (oracle.SE_CUBE, 4)])
+                                    (oracle.SE_CUBE, 4), (oracle.SE_CUBE, 8), (oracle.SE_BALL, 7)])
 def test_morph_total_order(dtype, shape, se, rad):
     for frac in (0.02, 0.3):
         f = _special_volume(dtype, shape, 3 + rad, frac)

@@ -705,9 +705,10 @@ __global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, 
   constexpr int axis = AXIS;
   extern __shared__ uint32_t vsm[];
   const int W = kVS + 2 * L;  // staged samples per line
+  const int WS = W | 1;       // row stride: odd, so the lines of a warp's scans fall in distinct banks
   uint32_t* E = vsm;
-  uint32_t* G = E + kVL * W;
-  uint32_t* H = G + kVL * W;
+  uint32_t* G = E + kVL * WS;
+  uint32_t* H = G + kVL * WS;
   const int64_t line0 = (int64_t)blockIdx.x * kVL;
   const int64_t seg0 = (int64_t)blockIdx.y * kVS;  // first output along the axis (region index)
   const int tid = threadIdx.x;
@@ -739,7 +740,7 @@ __global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, 
       if constexpr (RAW) key = to_key<TIN>(src[q]) ^ flip;
       else key = (uint32_t)src[q];
     }
-    E[ln * W + pos] = key;
+    E[ln * WS + pos] = key;
   }
   __syncthreads();
   // prefix / suffix minima per block of k = 2L + 1 samples
@@ -747,9 +748,9 @@ __global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, 
   const int nb = (W + k - 1) / k;
   for (int t = tid; t < kVL * nb; t += kVT) {
     const int ln = t / nb, b0 = (t % nb) * k, b1 = min(b0 + k, W);
-    const uint32_t* e = E + ln * W;
-    uint32_t* g = G + ln * W;
-    uint32_t* h = H + ln * W;
+    const uint32_t* e = E + ln * WS;
+    uint32_t* g = G + ln * WS;
+    uint32_t* h = H + ln * WS;
     uint32_t m = 0xFFFFFFFFu;
     for (int j = b0; j < b1; ++j) {
       m = min(m, e[j]);
@@ -774,7 +775,7 @@ __global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, 
     }
     const int64_t l = line0 + ln;
     if (l >= nlines || seg0 + o >= nseg) continue;
-    const uint32_t m = min(H[ln * W + o], G[ln * W + o + 2 * L]);
+    const uint32_t m = min(H[ln * WS + o], G[ln * WS + o + 2 * L]);
     int64_t c[3];
     line_coords(l, c);
     c[axis] = D.lo[axis] + seg0 + o;
@@ -789,7 +790,7 @@ __global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, 
   }
 }
 
-size_t vhgw_smem(int L) { return (size_t)3 * kVL * (kVS + 2 * L) * sizeof(uint32_t); }
+size_t vhgw_smem(int L) { return (size_t)3 * kVL * ((kVS + 2 * L) | 1) * sizeof(uint32_t); }
 
 template <typename TIN, bool RAW, int AXIS>
 cudaError_t vhgw_launch(const TIN* src, const VBox& S, void* dst, const VBox& D, int dst_dtype,

@@ -107,14 +107,16 @@ def test_full_size_sampled_ball3_1024():
         del y
 
 
-@pytest.mark.parametrize("dtype", [np.uint8, np.uint16, np.float16, np.float32])
-@pytest.mark.parametrize("rad", [7, 9, 12, 16])
+@pytest.mark.parametrize("dtype,rad", [(np.uint8, 7), (np.uint16, 9), (np.float16, 12),
+                                       (np.float32, 16), (np.uint16, 16)])
 def test_cube_large_radius_van_herk(dtype, rad):
     """Cube radii above the tiled kernels run three van Herk / Gil-Werman
     line passes: bit-exact against the oracle's brute force, on a volume
-    with ragged line tiles (130 = 128 + 2 outputs along x) and extents
-    shorter than the window (every sample reflected several times)."""
-    for shape in [(21, 35, 130), (5, 40, 9)]:
+    with ragged line tiles (130 = 128 + 2 outputs along x, 33 lines of a
+    32-line tile) and extents shorter than the window (every sample
+    reflected several times). Small volumes: the oracle visits (2r + 1)^3
+    sources per voxel."""
+    for shape in [(4, 33, 130), (5, 11, 9)]:
         f = rand_volume(dtype, shape, 30 + rad)
         x = to_dev(f)
         e = to_np(hp.erode3d(x, "cube", rad))

@@ -147,4 +147,11 @@ def test_cube_van_herk_out_of_core_within_budget():
         hp.set_memory_budget(old)
     assert st["bricks"] >= 4 and 0 < st["peak_device_bytes"] <= budget and st["live_device_bytes"] == 0
     assert np.array_equal(host, to_np(hp.erode3d(to_dev(f), "cube", 9)))
-    assert np.array_equal(host, oracle.erode3d(f, oracle.SE_CUBE, 9))
+    # the oracle on sampled boxes (corners, faces, interior), from the input box with halo
+    r, b = 9, 8
+    for lo in [(0, 0, 0), (72, 88, 104), (36, 0, 50), (10, 45, 0), (60, 20, 99)]:
+        ilo = [max(0, c - r) for c in lo]
+        ihi = [min(n, c + b + r) for c, n in zip(lo, f.shape)]
+        ref = oracle.erode3d(f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]], oracle.SE_CUBE, r,
+                             gdims=f.shape, in_lo=ilo, out_lo=lo, out_shape=(b, b, b))
+        assert np.array_equal(host[lo[0]:lo[0] + b, lo[1]:lo[1] + b, lo[2]:lo[2] + b], ref), lo

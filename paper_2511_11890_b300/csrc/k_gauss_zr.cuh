@@ -82,7 +82,10 @@ struct ZrShape {
   static constexpr int ZP = R <= 6 ? 2 : 1;
   static constexpr int NT = TX * TY / (2 * ZP);
   static constexpr int NY = (R <= 3 || R >= 7) ? 8 : 16;
-  static constexpr int MINB = NT >= 512 ? 1 : 2;
+  // radii <= 3 (HBM-bound): a two-group stage ring, so that three CTAs fit
+  // an SM; larger radii keep three groups in flight
+  static constexpr int MINB = NT >= 512 ? 1 : (R <= 3 ? 3 : 2);
+  static constexpr int NSG = R <= 3 ? 2 : kNSG;
 };
 
 template <int R, typename TIN>
@@ -121,7 +124,8 @@ struct ZrGeom {
   static constexpr int NC = TX + 2 * R;       // raw columns P1 reads
   static constexpr int MI1 = (kKP * NI1 + NT - 1) / NT;  // P1 items per thread and group
   static constexpr int MI2 = (kKP * NI2 + NT - 1) / NT;  // P2 items per thread and group
-  static constexpr int SMEM = 128 + kNSG * GB + kKP * XP * 4 + kKP * ZPL * 8;
+  static constexpr int NSG = S::NSG;
+  static constexpr int SMEM = 128 + NSG * GB + kKP * XP * 4 + kKP * ZPL * 8;
   static_assert(BH % 2 == 0 && TY % NY == 0 && NY % 2 == 0 && G1 % 4 == 0 && NI1 % 8 == 0, "tile shape");
   static_assert((RPS / 4) % 2 == 1 && XS % 4 == 0, "X layout");
   static_assert(PB % 128 == 0, "stage planes on 128-byte boundaries");
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
   using G = ZrGeom<R, TIN>;
   constexpr int NT = G::NT, TX = G::TX, TY = G::TY, ZP = G::ZP, NY = G::NY, L = G::L;
   constexpr int BW = G::BW, BH = G::BH, RA = G::RA, ES = G::ES, XS = G::XS, ZW = G::ZW;
-  constexpr int KP = kKP, NSG = kNSG;
+  constexpr int KP = kKP, NSG = G::NSG;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ int s_abort, s_fixovf;
   __shared__ int s_frow[BH], s_fcol[BW], s_brow[BH], s_bcol[BW];

@@ -109,3 +109,32 @@ def test_full_size_sampled_parity_1024():
         ref = np.stack(refs)
         assert_filter_close(np.stack(gots), ref, f"1024^3 sigma {sigma}")
         del y
+
+
+def test_full_size_face_planes_and_interior_block_1024():
+    """The 1024^3 step's Gaussians on whole face planes (z = 0, y = n - 1,
+    x = 0: every face tile path and the reflected z groups) and one interior
+    64^3 block (several tiles and z chunks in full), against the oracle
+    (its OpenMP build: the same operations in the same order)."""
+    n = 1024
+    f, _ = synth.porous(n, synth.SEED_BASE + 1)
+    x = to_dev(f)
+    oracle.use_threads(True)
+    try:
+        for sigma in (1.0, 2.0, 4.0):
+            y = hp.gaussian3d(x, sigma)
+            torch.cuda.synchronize()
+            r = oracle.radius(sigma)
+            boxes = [((0, 0, 0), (1, n, n)), ((0, n - 1, 0), (n, 1, n)), ((0, 0, 0), (n, n, 1)),
+                     ((480, 300, 700), (64, 64, 64))]
+            for lo, shp in boxes:
+                ilo = [max(0, c - r) for c in lo]
+                ihi = [min(n, c + s + r) for c, s in zip(lo, shp)]
+                part = f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]]
+                ref = oracle.gaussian3d(part, sigma, gdims=f.shape, in_lo=ilo, out_lo=lo,
+                                        out_shape=shp)
+                got = y[lo[0]:lo[0] + shp[0], lo[1]:lo[1] + shp[1], lo[2]:lo[2] + shp[2]]
+                assert_filter_close(got.cpu().numpy(), ref, f"1024^3 sigma {sigma} box {lo}+{shp}")
+            del y
+    finally:
+        oracle.use_threads(False)

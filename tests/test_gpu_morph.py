@@ -155,3 +155,30 @@ def test_cube_van_herk_out_of_core_within_budget():
         ref = oracle.erode3d(f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]], oracle.SE_CUBE, r,
                              gdims=f.shape, in_lo=ilo, out_lo=lo, out_shape=(b, b, b))
         assert np.array_equal(host[lo[0]:lo[0] + b, lo[1]:lo[1] + b, lo[2]:lo[2] + b], ref), lo
+
+
+def test_full_size_face_planes_ball3_1024():
+    """Erosion and dilation (ball r = 3) of the 1024^3 step on whole face
+    planes and an interior 64^3 block, bit for bit against the oracle."""
+    n = 1024
+    f, _ = synth.porous(n, synth.SEED_BASE + 1)
+    x = to_dev(f)
+    rad = 3
+    boxes = [((0, 0, 0), (1, n, n)), ((n - 1, 0, 0), (1, n, n)), ((0, 0, n - 1), (n, n, 1)),
+             ((0, 0, 0), (n, 1, n)), ((200, 600, 900), (64, 64, 64))]
+    oracle.use_threads(True)
+    try:
+        for fn, dil in ((hp.erode3d, False), (hp.dilate3d, True)):
+            y = fn(x, "ball", rad)
+            torch.cuda.synchronize()
+            for lo, shp in boxes:
+                ilo = [max(0, c - rad) for c in lo]
+                ihi = [min(n, c + s + rad) for c, s in zip(lo, shp)]
+                part = f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]]
+                ref = oracle.morph3d(part, oracle.SE_BALL, rad, dil, gdims=f.shape, in_lo=ilo,
+                                     out_lo=lo, out_shape=shp)
+                got = y[lo[0]:lo[0] + shp[0], lo[1]:lo[1] + shp[1], lo[2]:lo[2] + shp[2]]
+                assert np.array_equal(got.cpu().numpy(), ref), (dil, lo, shp)
+            del y
+    finally:
+        oracle.use_threads(False)

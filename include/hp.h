@@ -159,6 +159,28 @@ int hp_filterbank3d(const hp_volume* in, hp_volume* const* outs, const hp_filter
 int hp_filterbank3d_bricks(const hp_volume* in, hp_volume* const* outs, const hp_filter* f, int n,
                            const hp_box* bricks, int nbricks, void* stream);
 
+/* Several filters of one volume in one pass (Sec. III-D applied to a set
+ * of filters): out k holds op k. Host volumes run out of core with one
+ * brick plan for all ops (halo = the largest radius): each brick's input
+ * crosses the host link once and every op runs on it; device volumes run
+ * the ops one after another on `stream`. Results equal the single-op calls
+ * bit for bit.
+ *   HP_OP_GAUSSIAN: as hp_gaussian3d (sigma, order {oz, oy, ox}, truncate
+ *     3); output f32 or f16.
+ *   HP_OP_ERODE / HP_OP_DILATE: as hp_erode3d / hp_dilate3d (se, radius);
+ *     output dtype = input dtype.
+ * 1 <= n <= 64; every output has the input's extents and location. */
+typedef enum { HP_OP_GAUSSIAN = 0, HP_OP_ERODE = 1, HP_OP_DILATE = 2 } hp_op_kind;
+typedef struct {
+  int kind;     /* hp_op_kind */
+  double sigma; /* Gaussian: sigma > 0 */
+  int order[3]; /* Gaussian: derivative orders (z, y, x), each 0..2 */
+  int se;       /* morphology: hp_se */
+  int radius;   /* morphology: 0..16 */
+} hp_op;
+int hp_multi3d(const hp_volume* in, hp_volume* const* outs, const hp_op* ops, int n,
+               void* stream);
+
 /* Grayscale erosion / dilation with a cube (half-width radius) or ball
  * (radius) structuring element (Sec. III-C, label-editing morphology).
  * Output dtype equals input dtype; results are exact. radius in [0, 16]. */

@@ -28,7 +28,7 @@ EXPORTS = [
     "hp_volume_create", "hp_volume_destroy", "hp_set_memory_budget", "hp_get_memory_budget",
     "hp_gaussian3d", "hp_filterbank3d", "hp_filterbank3d_bricks", "hp_erode3d", "hp_dilate3d",
     "hp_open3d", "hp_close3d", "hp_tophat3d", "hp_unsharp3d", "hp_threshold_local3d",
-    "hp_threshold3d", "hp_threshold_box3d", "hp_hessian3d", "hp_filterbank3d_adjoint",
+    "hp_threshold3d", "hp_threshold_box3d", "hp_hessian3d", "hp_multi3d", "hp_filterbank3d_adjoint",
     "hp_morph3d_backward",
     "hp_morph3d_backward_noalloc", "hp_set_devices", "hp_get_devices", "hp_set_brick_shard",
     "hp_plan_bricks",
@@ -44,6 +44,14 @@ class HPError(RuntimeError):
 
 class hp_filter(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double)]
+
+
+class hp_op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("order", ctypes.c_int * 3),
+                ("se", ctypes.c_int), ("radius", ctypes.c_int)]
+
+
+HP_OP_GAUSSIAN, HP_OP_ERODE, HP_OP_DILATE = 0, 1, 2
 
 
 class hp_box(ctypes.Structure):
@@ -83,6 +91,7 @@ def _load() -> ctypes.CDLL:
         "hp_threshold3d": [vp, vp, d, vp],
         "hp_threshold_box3d": [vp, vp, i, i, d, d, vp],
         "hp_hessian3d": [vp, pvp, i, d, vp],
+        "hp_multi3d": [vp, pvp, ctypes.POINTER(hp_op), i, vp],
         "hp_filterbank3d_adjoint": [vp, pvp, ctypes.POINTER(hp_filter), i, vp, vp],
         "hp_morph3d_backward": [vp, vp, i, i, i, vp, i, vp],
         "hp_morph3d_backward_noalloc": [vp, vp, i, i, i, vp, i, vp],

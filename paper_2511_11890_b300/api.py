@@ -198,6 +198,42 @@ def hessian3d(x, sigma: float, eigenvalues: bool = False, outs=None, out_dtype: 
     return outs
 
 
+def multi3d(x, ops, outs=None, stream=None):
+    """Several filters of x in one pass: ops is a list of
+    ("gauss", sigma[, (oz, oy, ox)][, out_dtype]) and ("erode" | "dilate",
+    se, radius); outputs default to float32 (Gaussians) and x's dtype
+    (morphology). Host inputs stream through the device once for all ops."""
+    arr = (_lib.hp_op * len(ops))()
+    made = []
+    for i, q in enumerate(ops):
+        kind = q[0]
+        if kind == "gauss":
+            arr[i].kind = _lib.HP_OP_GAUSSIAN
+            arr[i].sigma = float(q[1])
+            order = q[2] if len(q) > 2 else (0, 0, 0)
+            for a in range(3):
+                arr[i].order[a] = int(order[a])
+            made.append(q[3] if len(q) > 3 else HP_F32)
+        elif kind in ("erode", "dilate"):
+            arr[i].kind = _lib.HP_OP_ERODE if kind == "erode" else _lib.HP_OP_DILATE
+            arr[i].se = SE[q[1]]
+            arr[i].radius = int(q[2])
+            made.append(_dtype_code(x))
+        else:
+            raise ValueError(f"unknown op {kind!r}")
+    if outs is None:
+        outs = [_empty_like(x, dt) for dt in made]
+    views = [_View(o) for o in outs]
+    try:
+        handles = (ctypes.c_void_p * len(outs))(*[v.h.value for v in views])
+        with _ctx(x), _View(x) as vi:
+            check(lib.hp_multi3d(vi, handles, arr, len(ops), _stream(x, stream)))
+    finally:
+        for v in views:
+            v.__exit__()
+    return outs
+
+
 def _filters(filters):
     arr = (hp_filter * len(filters))()
     for i, (k, s) in enumerate(filters):

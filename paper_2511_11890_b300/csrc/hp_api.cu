@@ -397,6 +397,7 @@ struct Op {
   int halo;
   int out_dtype;
   int nout = 1;         // outputs per voxel (filter bank: one per filter)
+  std::vector<int> out_dtypes;  // per-output dtypes when they differ (else out_dtype)
   bool z_only = false;  // plan Z slabs only (whole x/y planes per brick)
   // planning bound of the kernel scratch, bytes per voxel of the input box
   size_t scratch_per_in_voxel = 0;
@@ -519,8 +520,12 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
   auto t0 = std::chrono::steady_clock::now();
   Faults faults;
   const int64_t n[3] = {in->nz, in->ny, in->nx};
-  const size_t ies = dtype_size(in->dtype), oes = dtype_size(op.out_dtype);
   const int nout = op.nout;
+  const size_t ies = dtype_size(in->dtype);
+  std::vector<int> odt(nout, op.out_dtype);
+  if ((int)op.out_dtypes.size() == nout) odt = op.out_dtypes;
+  size_t out_bpv = 0;  // output bytes per voxel, all outputs
+  for (int k = 0; k < nout; ++k) out_bpv += dtype_size(odt[k]);
   int caller_dev = 0;
   cudaError_t ce = cudaGetDevice(&caller_dev);
   if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
@@ -560,7 +565,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
                      "that every process plans the same bricks");
   const int S = 3;
   std::vector<Brick> all;
-  int st = plan(n, op.halo, ies, oes * nout, op.scratch_per_in_voxel, budget, S, 8 * ndev * world,
+  int st = plan(n, op.halo, ies, out_bpv, op.scratch_per_in_voxel, budget, S, 8 * ndev * world,
                 op.z_only, &all);
   if (st != HP_OK) return st;
   std::vector<Brick> bricks;  // this process's shard
@@ -583,17 +588,22 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
     }
     return job;
   };
-  size_t max_in = 0, max_out = 0, max_scr = 0;
+  size_t max_in = 0, max_vox = 0, max_scr = 0;
   for (auto& b : bricks) {
-    size_t vi = ies, vo = oes;
+    size_t vi = ies, vo = 1;
     for (int a = 0; a < 3; ++a) {
       vi *= (size_t)(b.in.hi[a] - b.in.lo[a]);
       vo *= (size_t)(b.core.hi[a] - b.core.lo[a]);
     }
     max_in = std::max(max_in, vi);
-    max_out = std::max(max_out, vo);
+    max_vox = std::max(max_vox, vo);
     if (op.scratch_bytes) max_scr = std::max(max_scr, op.scratch_bytes(brick_job(b, nullptr, nullptr)));
   }
+  // stage output layout: output k at off[k] (256-byte aligned), max_vox voxels each
+  std::vector<size_t> off(nout + 1, 0);
+  for (int k = 0; k < nout; ++k)
+    off[k + 1] = (off[k] + max_vox * dtype_size(odt[k]) + 255) / 256 * 256;
+  const size_t out_stage = off[nout];
   const bool in_pinned = is_pinned(in->data);
   bool out_pinned = true;
   for (int k = 0; k < nout; ++k) out_pinned = out_pinned && is_pinned(outs[k]->data);
@@ -601,7 +611,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
   struct Stage {
     int dev = 0;
     void* din = nullptr;
-    void* dout = nullptr;  // nout core boxes of max_out bytes
+    void* dout = nullptr;  // nout core boxes (layout off[])
     void* dscr = nullptr;
     void* hscr = nullptr;
     void* hin = nullptr;
@@ -634,8 +644,8 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
     if ((e = cudaMalloc(&x.din, max_in)) != cudaSuccess) { cfail(e, "cudaMalloc(in stage)"); x.din = nullptr; break; }
     track_alloc((int64_t)max_in);
     if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
-    if ((e = cudaMalloc(&x.dout, max_out * nout)) != cudaSuccess) { cfail(e, "cudaMalloc(out stage)"); x.dout = nullptr; break; }
-    track_alloc((int64_t)(max_out * nout));
+    if ((e = cudaMalloc(&x.dout, out_stage)) != cudaSuccess) { cfail(e, "cudaMalloc(out stage)"); x.dout = nullptr; break; }
+    track_alloc((int64_t)out_stage);
     if (max_scr > 0) {
       if (faults.fail_alloc()) { fail(HP_ERR_OOM, "injected allocation failure"); break; }
       if ((e = cudaMalloc(&x.dscr, max_scr)) != cudaSuccess) { cfail(e, "cudaMalloc(scratch stage)"); x.dscr = nullptr; break; }
@@ -650,8 +660,8 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
       pinned += max_in;
     }
     if (!out_pinned) {
-      if ((e = cudaHostAlloc(&x.hout, max_out * nout, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); x.hout = nullptr; break; }
-      pinned += max_out * nout;
+      if ((e = cudaHostAlloc(&x.hout, out_stage, cudaHostAllocDefault)) != cudaSuccess) { cfail(e, "cudaHostAlloc"); x.hout = nullptr; break; }
+      pinned += out_stage;
     }
     if ((e = cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking)) != cudaSuccess) { cfail(e, "cudaStreamCreate"); x.s = nullptr; break; }
     if ((e = cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming)) != cudaSuccess) { cfail(e, "cudaEventCreate"); x.ev = nullptr; break; }
@@ -667,7 +677,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
       const int64_t cd[3] = {b.core.hi[0] - b.core.lo[0], b.core.hi[1] - b.core.lo[1],
                              b.core.hi[2] - b.core.lo[2]};
       for (int k = 0; k < nout; ++k)
-        host_copy_box(outs[k]->data, (const char*)x.hout + k * max_out, oes, cd, b.core.lo, n,
+        host_copy_box(outs[k]->data, (const char*)x.hout + off[k], dtype_size(odt[k]), cd, b.core.lo, n,
                       vol_lo, b.core.lo, b.core.hi);
     }
     x.brick = -1;
@@ -685,7 +695,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
     const int64_t idims[3] = {b.in.hi[0] - b.in.lo[0], b.in.hi[1] - b.in.lo[1], b.in.hi[2] - b.in.lo[2]};
     const int64_t cdims[3] = {b.core.hi[0] - b.core.lo[0], b.core.hi[1] - b.core.lo[1],
                               b.core.hi[2] - b.core.lo[2]};
-    const size_t cbytes = oes * (size_t)(cdims[0] * cdims[1] * cdims[2]);
+    const size_t cvox = (size_t)(cdims[0] * cdims[1] * cdims[2]);
     if (faults.fail_copy()) { fail(HP_ERR_CUDA, "injected memcpy failure"); break; }
     if (in_pinned) {
       e = copy_box_async(x.din, idims, b.in.lo, in->data, n, vol_lo, b.in.lo, b.in.hi, ies,
@@ -702,18 +712,19 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
     job.scratch_bytes = max_scr;
     job.host_scratch = x.hscr;
     std::vector<void*> souts(nout);
-    for (int k = 0; k < nout; ++k) souts[k] = (char*)x.dout + k * max_out;
+    for (int k = 0; k < nout; ++k) souts[k] = (char*)x.dout + off[k];
     if ((st = op.launch(job, souts.data(), x.s)) != HP_OK) { if (rc == HP_OK) rc = st; break; }
     if (faults.fail_copy()) { fail(HP_ERR_CUDA, "injected memcpy failure"); break; }
     for (int k = 0; k < nout && e == cudaSuccess; ++k) {
+      const size_t es = dtype_size(odt[k]);
       if (out_pinned)
         e = copy_box_async(outs[k]->data, n, vol_lo, souts[k], cdims, b.core.lo, b.core.lo,
-                           b.core.hi, oes, cudaMemcpyDeviceToHost, x.s);
+                           b.core.hi, es, cudaMemcpyDeviceToHost, x.s);
       else
-        e = cudaMemcpyAsync((char*)x.hout + k * max_out, souts[k], cbytes, cudaMemcpyDeviceToHost, x.s);
+        e = cudaMemcpyAsync((char*)x.hout + off[k], souts[k], es * cvox, cudaMemcpyDeviceToHost, x.s);
+      d2h += es * cvox;
     }
     if (e != cudaSuccess) { cfail(e, "D2H copy"); break; }
-    d2h += cbytes * nout;
     if ((e = cudaEventRecord(x.ev, x.s)) != cudaSuccess) { cfail(e, "cudaEventRecord"); break; }
     x.brick = (int)i;
   }
@@ -736,7 +747,7 @@ static int run_host(const Op& op, const hp_volume* in, hp_volume* const* outs) {
     if (x.ev) cudaEventDestroy(x.ev);
     if (x.s) cudaStreamDestroy(x.s);
     if (x.din) { cudaFree(x.din); track_free((int64_t)max_in); }
-    if (x.dout) { cudaFree(x.dout); track_free((int64_t)(max_out * nout)); }
+    if (x.dout) { cudaFree(x.dout); track_free((int64_t)out_stage); }
     if (x.dscr) { cudaFree(x.dscr); track_free((int64_t)max_scr); }
     if (x.hscr) cudaFreeHost(x.hscr);
     if (x.hin) cudaFreeHost(x.hin);
@@ -1069,6 +1080,73 @@ int hp_hessian3d(const hp_volume* in, hp_volume* const* outs, int what, double s
     return HP_OK;
   };
   (void)r;
+  return run_multi(op, in, outs, stream);
+}
+
+int hp_multi3d(const hp_volume* in, hp_volume* const* outs, const hp_op* ops, int n,
+               void* stream) {
+  if (!in || !outs || !ops || n < 1 || n > 64)
+    return set_error(HP_ERR_INVALID_ARG, "multi: null argument or n outside [1, 64]");
+  auto taps = std::make_shared<std::vector<Taps>>(n);
+  std::vector<int> odt(n);
+  int halo = 0;
+  bool scratch = false;
+  for (int k = 0; k < n; ++k) {
+    int st = check_pair(in, outs[k]);
+    if (st != HP_OK) return st;
+    const hp_op& q = ops[k];
+    odt[k] = outs[k]->dtype;
+    if (q.kind == HP_OP_GAUSSIAN) {
+      if (!(q.sigma > 0) || !std::isfinite(q.sigma)) return set_error(HP_ERR_INVALID_ARG, "multi: sigma must be > 0");
+      for (int a = 0; a < 3; ++a)
+        if (q.order[a] < 0 || q.order[a] > 2) return set_error(HP_ERR_INVALID_ARG, "multi: order must be 0, 1 or 2");
+      if (odt[k] != HP_F32 && odt[k] != HP_F16)
+        return set_error(HP_ERR_UNSUPPORTED, "multi: Gaussian outputs must be f32 or f16");
+      make_taps(q.sigma, 3.0, q.order, &(*taps)[k]);
+      if ((*taps)[k].r > kMaxRGeneric) return set_error(HP_ERR_UNSUPPORTED, "multi: radius exceeds 32");
+      halo = std::max(halo, (*taps)[k].r);
+      scratch = scratch || gauss_scratch_bytes(whole_job(in, outs[k], odt[k]), (*taps)[k].r) > 0;
+    } else if (q.kind == HP_OP_ERODE || q.kind == HP_OP_DILATE) {
+      if (q.se != HP_SE_CUBE && q.se != HP_SE_BALL) return set_error(HP_ERR_INVALID_ARG, "multi: unknown structuring element");
+      if (q.radius < 0 || q.radius > kMaxMorphR) return set_error(HP_ERR_INVALID_ARG, "multi: radius must be in [0, 16]");
+      if (odt[k] != in->dtype) return set_error(HP_ERR_UNSUPPORTED, "multi: morphology output dtype must equal the input's");
+      halo = std::max(halo, q.radius);
+      scratch = scratch || morph_scratch_bytes(whole_job(in, outs[k], odt[k]), q.se, q.radius) > 0;
+    } else {
+      return set_error(HP_ERR_INVALID_ARG, "multi: unknown op kind");
+    }
+  }
+  auto opsv = std::make_shared<std::vector<hp_op>>(ops, ops + n);
+  Op op;
+  op.halo = halo;
+  op.out_dtype = odt[0];
+  op.out_dtypes = odt;
+  op.nout = n;
+  if (scratch) {
+    op.scratch_per_in_voxel = 8;
+    op.scratch_bytes = [opsv, taps](const Job& j) {
+      size_t m = 0;
+      for (size_t k = 0; k < opsv->size(); ++k) {
+        const hp_op& q = (*opsv)[k];
+        m = std::max(m, q.kind == HP_OP_GAUSSIAN ? gauss_scratch_bytes(j, (*taps)[k].r)
+                                                 : morph_scratch_bytes(j, q.se, q.radius));
+      }
+      return m;
+    };
+  }
+  op.launch = [opsv, taps, odt](const Job& j, void* const* o, cudaStream_t s) -> int {
+    for (size_t k = 0; k < opsv->size(); ++k) {
+      const hp_op& q = (*opsv)[k];
+      Job jk = j;
+      jk.out.ptr = o[k];
+      jk.out.dtype = odt[k];
+      const cudaError_t e = q.kind == HP_OP_GAUSSIAN
+                                ? launch_gauss(jk, (*taps)[k], s)
+                                : launch_morph(jk, q.se, q.radius, q.kind == HP_OP_DILATE, s);
+      if (e != cudaSuccess) return cuda_fail(e, "multi: kernel launch");
+    }
+    return HP_OK;
+  };
   return run_multi(op, in, outs, stream);
 }
 

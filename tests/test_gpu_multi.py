@@ -1,0 +1,60 @@
+"""Several filters in one chunked pass (hp_multi3d, Sec. III-D applied to a
+set of filters): every output equals the single-op call bit for bit, on
+device volumes and out of core, where the input crosses the host link about
+once for all ops and the budget holds."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from gpu_util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+hp = pytest.importorskip("paper_2511_11890_b300")
+
+STEP = [("gauss", 1.0), ("gauss", 2.0), ("gauss", 4.0), ("erode", "ball", 3), ("dilate", "ball", 3)]
+
+
+def _single(x, q):
+    if q[0] == "gauss":
+        return hp.gaussian3d(x, q[1], order=q[2] if len(q) > 2 else (0, 0, 0))
+    fn = hp.erode3d if q[0] == "erode" else hp.dilate3d
+    return fn(x, q[1], q[2])
+
+
+def _bits(a):
+    a = a.cpu().numpy() if isinstance(a, torch.Tensor) else a
+    return a.view(np.uint16 if a.dtype.itemsize == 2 else (np.uint32 if a.dtype.itemsize == 4 else np.uint8))
+
+
+@pytest.mark.parametrize("ops", [STEP, [("gauss", 1.5, (0, 1, 2)), ("erode", "cube", 9),
+                                         ("gauss", 5.0), ("dilate", "cube", 2)]])
+def test_multi_equals_single_calls_device_and_host(ops):
+    f = synth.porous((56, 72, 96), 71)[0]
+    x = to_dev(f)
+    dev = hp.multi3d(x, ops)
+    refs = [_single(x, q) for q in ops]
+    torch.cuda.synchronize()
+    for d, r in zip(dev, refs):
+        assert np.array_equal(_bits(d), _bits(r))
+    budget = 30_000_000
+    old = hp.get_memory_budget()
+    try:
+        hp.set_memory_budget(budget)
+        host = hp.multi3d(f, ops)
+        st = hp.stats()
+    finally:
+        hp.set_memory_budget(old)
+    assert st["bricks"] >= 4 and st["peak_device_bytes"] <= budget and st["live_device_bytes"] == 0
+    assert f.nbytes <= st["h2d_bytes"] < 2.5 * f.nbytes      # the input about once, for all ops
+    for h, r in zip(host, refs):
+        assert np.array_equal(_bits(h), _bits(r))
+
+
+def test_multi_errors():
+    x = torch.zeros((4, 8, 8), dtype=torch.uint16, device="cuda")
+    with pytest.raises(hp.HPError):
+        hp.multi3d(x, [("gauss", -1.0)])
+    with pytest.raises(hp.HPError, match="HP_ERR_UNSUPPORTED"):
+        hp.multi3d(x, [("erode", "ball", 1)], outs=[torch.zeros((4, 8, 8), dtype=torch.float32, device="cuda")])

@@ -17,7 +17,8 @@ FP64 C) on bounded sub-boxes of the same workload.
 The default line also carries, besides the step: the FP32 FMA roofline of
 the dominant kernel against the derived peak (this device's SM count x 128
 lanes x 2 x max clock) and libhp's measured FMA probe; `bank` (the 512^3
-float16 12-filter bank over 37 bricks, one graph launch); `ooc` (2048^3
+float16 12-filter bank over 37 bricks, one graph launch); `spheres128` and
+`autograd256` (the 128^3 pipeline and the 256^3 forward + backward); `ooc` (2048^3
 uint16 out of core under an 8e9-byte budget, with a host-link probe at each
 op's brick size and byte mix and the fraction of the link bound reached;
 `--no-ooc` skips it); and the oracle timed single-threaded (`cpu_baseline`)
@@ -365,11 +366,15 @@ def run_hp(args):
 
     del outs_g, out_e, out_d
     torch.cuda.empty_cache()
-    # configuration 4: the filter bank (one graph launch per bank)
-    bank = None
+    # configuration 4: the filter bank (one graph launch per bank); configs 1
+    # and 5: the 128^3 pipeline and the 256^3 forward + backward
+    bank = cfg1 = cfg5 = None
     if rank == 0 and not args.no_bank:
         bank = bank_measure(hp, torch, synth, args.steps, args.warmup, fma_peak_tflops,
                             fma_measured_tflops, hbm_gbs)
+        torch.cuda.empty_cache()
+        cfg1 = spheres128_measure(hp, torch, synth, args.steps, args.warmup)
+        cfg5 = autograd256_measure(hp, torch, synth, args.steps, args.warmup)
         torch.cuda.empty_cache()
 
     # end to end through the C ABI with pinned host buffers
@@ -436,7 +441,7 @@ def run_hp(args):
                        "hbm_frac_of_step": hbm_step_frac},
             "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "cpu_baseline_mt": cpu_mt,
             "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk.summary(),
-            "bank": bank, "ooc": ooc,
+            "bank": bank, "ooc": ooc, "spheres128": cfg1, "autograd256": cfg5,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -666,13 +671,10 @@ def run_open1024(args):
     return 0
 
 
-def run_spheres128(args):
+def spheres128_measure(hp, torch, synth, steps: int, warmup: int):
     """128^3 float32 spheres: Gaussian sigma 2 -> threshold 0.5 to uint8 ->
-    erosion and dilation with the 3^3 cube (the unchunked pipeline)."""
-    import torch
-
-    import paper_2511_11890_b300 as hp
-    import synth
+    erosion and dilation with the 3^3 cube (the unchunked pipeline): ms per
+    pipeline (four launches through the C ABI)."""
     n = 128
     f = synth.spheres(n, 40, synth.SEED_BASE + 0)
     x = torch.from_numpy(f).cuda()
@@ -688,15 +690,26 @@ def run_spheres128(args):
         hp.erode3d(t, "cube", 1, out=e)
         hp.dilate3d(t, "cube", 1, out=d)
 
-    ms, clk = _timed(step, args.steps, max(3, args.warmup), stream)
+    ms, clk = _timed(step, steps, max(3, warmup), stream)
     hp.stream_status(stream)
+    return {"ms": ms, "voxels_per_s": n ** 3 / (ms / 1e3), "launches": 4, "clocks": clk,
+            "workload": "spheres 128^3 f32: gaussian s=2, threshold 0.5, cube-3 erode + dilate",
+            "note": "8 MiB volume, L2-resident: bound by host launch latency"}
+
+
+def run_spheres128(args):
+    import torch
+
+    import paper_2511_11890_b300 as hp
+    import synth
+    m = spheres128_measure(hp, torch, synth, args.steps, args.warmup)
     line = {"metric": "voxels/s, 128^3 float32 pipeline: gaussian s=2, threshold 0.5, cube-3 erode+dilate",
-            "value": n ** 3 / (ms / 1e3), "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
-            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+            "value": m["voxels_per_s"], "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
+            "ms_per_step": m["ms"], "higher_is_better": True, "dtype": "f32",
             "data": "synthetic spheres (seeded)",
             "config": {"workload": "spheres 128^3 f32, 40 balls r 4-16, sigma 0.05 noise",
                        "l2": "8 MiB volume: L2-resident, latency-bound (voxels/s only)"},
-            "gpu_launches": 4 * args.steps, "clocks": clk}
+            "gpu_launches": 4 * args.steps, "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -730,14 +743,10 @@ def run_bank512(args):
     return 0
 
 
-def run_autograd256(args):
+def autograd256_measure(hp, torch, synth, steps: int, warmup: int):
     """256^3 float32 spheres: forward 12-filter bank + erosion (5^3 cube),
     loss = sum of w * features with seeded N(0,1) fields, hand-written
-    backward through torch.autograd."""
-    import torch
-
-    import paper_2511_11890_b300 as hp
-    import synth
+    backward through torch.autograd: ms per forward + backward."""
     from paper_2511_11890_b300 import autograd as hpa
     n = 256
     f = synth.spheres(n, 320, synth.SEED_BASE + 4)
@@ -753,15 +762,27 @@ def run_autograd256(args):
         loss = sum((F * w).sum() for F, w in zip(feats, ws))
         loss.backward()
 
-    ms, clk = _timed(step, args.steps, max(3, args.warmup), stream)
+    ms, clk = _timed(step, steps, max(3, warmup), stream)
     hp.stream_status(stream)
+    del x, ws
+    return {"ms": ms, "voxels_per_s": n ** 3 / (ms / 1e3), "clocks": clk,
+            "workload": "spheres 256^3 f32: 12-filter bank + cube-5 erosion, forward + backward",
+            "note": "the weighted sums of the loss run as torch reductions"}
+
+
+def run_autograd256(args):
+    import torch
+
+    import paper_2511_11890_b300 as hp
+    import synth
+    m = autograd256_measure(hp, torch, synth, args.steps, args.warmup)
     line = {"metric": "voxels/s, 256^3 float32 forward + backward (12-filter bank + cube-5 erosion)",
-            "value": n ** 3 / (ms / 1e3), "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
-            "ms_per_step": ms, "higher_is_better": True, "dtype": "f32",
+            "value": m["voxels_per_s"], "unit": "voxels/s", "n_gpus": 1, "steps": args.steps,
+            "ms_per_step": m["ms"], "higher_is_better": True, "dtype": "f32",
             "data": "synthetic spheres (seeded), seeded N(0,1) loss weights",
             "config": {"workload": "spheres 256^3 f32, 320 balls; loss = sum w_k * feature_k",
-                       "note": "the weighted sums of the loss run as torch reductions"},
-            "clocks": clk}
+                       "note": m["note"]},
+            "clocks": m["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -1079,7 +1079,6 @@ int hp_hessian3d(const hp_volume* in, hp_volume* const* outs, int what, double s
     if (eig) return launched(launch_hessian_eig(comps, nv, o, j.out.dtype, s));
     return HP_OK;
   };
-  (void)r;
   return run_multi(op, in, outs, stream);
 }
 

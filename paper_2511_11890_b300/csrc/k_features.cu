@@ -87,11 +87,6 @@ __global__ void k_hessian_eig(const float* __restrict__ comps, int64_t n, void* 
 
 // ----------------------------------------------------------- box statistics
 
-template <typename T>
-__device__ __forceinline__ T load_t(const void* p, int64_t i) {
-  return static_cast<const T*>(p)[i];
-}
-
 // Integer sums: S1 in int32, S2 in int64 (exact: u16 values, windows of at
 // most 31^3 voxels).
 struct ISum {

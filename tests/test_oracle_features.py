@@ -154,8 +154,12 @@ def test_threshold_box_vs_numpy_definition(method, k, c):
     win = np.lib.stride_tricks.sliding_window_view(p, (2 * w + 1,) * 3)
     m = win.mean(axis=(-3, -2, -1))
     s = win.std(axis=(-3, -2, -1))
-    t = {oracle.LOCAL_MEAN: m - c, oracle.LOCAL_NIBLACK: m + k * s,
-         oracle.LOCAL_SAUVOLA: m * (1 + k * (s / max(c, 1e-300) - 1))}[method]
+    if method == oracle.LOCAL_MEAN:
+        t = m - c
+    elif method == oracle.LOCAL_NIBLACK:
+        t = m + k * s
+    else:
+        t = m * (1 + k * (s / c - 1))
     assert np.allclose(thr, t, rtol=1e-9, atol=1e-6)
     far = np.abs(f - t) > 1e-6 * (1 + np.abs(t))
     assert np.array_equal(out[far], (f > t)[far].astype(np.uint8))

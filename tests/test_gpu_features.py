@@ -107,3 +107,16 @@ def test_box_threshold_radius_beyond_extent_and_errors():
         hp.threshold_box3d(x, "sauvola", 2, 0.2, 0.0)
     with pytest.raises(hp.HPError, match="HP_ERR_INVALID_ARG"):
         hp.threshold_box3d(x, "mean", 16)
+
+
+def test_box_threshold_radius_zero_and_hessian_small_sigma_f16():
+    f = rand_volume(np.uint16, (6, 9, 20), 80)
+    x = to_dev(f)
+    # a 1-voxel window: m = f, s = 0
+    assert not to_np(hp.threshold_box3d(x, "niblack", 0, 0.7)).any()          # f > f is false
+    assert to_np(hp.threshold_box3d(x, "mean", 0, 0.0, 1.0)).all()             # f > f - 1
+    g = rand_volume(np.float32, (10, 12, 16), 81)
+    for sigma in (0.4, 0.7):
+        got = [to_np(t) for t in hp.hessian3d(to_dev(g), sigma, out_dtype=hp.HP_F16)]
+        for a, r in zip(got, oracle.hessian3d(g, sigma)):
+            assert_filter_close(a, r, f"Hessian f16 sigma {sigma}")

@@ -68,3 +68,32 @@ def test_multi_errors():
         hp.multi3d(x, [("gauss", -1.0)])
     with pytest.raises(hp.HPError, match="HP_ERR_UNSUPPORTED"):
         hp.multi3d(x, [("erode", "ball", 1)], outs=[torch.zeros((4, 8, 8), dtype=torch.float32, device="cuda")])
+
+
+def test_multi_f16_thin_volume_and_device_list():
+    """float16 input with float16 Gaussian outputs, on a volume thinner than
+    the radius in y (generic Gaussian path and van Herk cube passes), device
+    and out of core over a two-slot device list."""
+    rng = np.random.default_rng(72)
+    f = (rng.standard_normal((40, 5, 64)) * 3).astype(np.float16)
+    ops = [("gauss", 2.0, (0, 0, 0), hp.HP_F16), ("gauss", 1.0, (1, 0, 0)), ("erode", "cube", 6),
+           ("dilate", "ball", 2)]
+    x = to_dev(f)
+    dev = hp.multi3d(x, ops)
+    refs = [hp.gaussian3d(x, 2.0, out_dtype=hp.HP_F16), hp.gaussian3d(x, 1.0, order=(1, 0, 0)),
+            hp.erode3d(x, "cube", 6), hp.dilate3d(x, "ball", 2)]
+    torch.cuda.synchronize()
+    for d, r in zip(dev, refs):
+        assert np.array_equal(_bits(d), _bits(r))
+    old = hp.get_memory_budget()
+    try:
+        hp.set_memory_budget(2_000_000)
+        hp.set_devices([0, 0])
+        host = hp.multi3d(f, ops)
+        st = hp.stats()
+    finally:
+        hp.set_devices([])
+        hp.set_memory_budget(old)
+    assert st["bricks"] >= 4 and st["peak_device_bytes"] <= 2_000_000
+    for h, r in zip(host, refs):
+        assert np.array_equal(_bits(h), _bits(r))

@@ -43,7 +43,8 @@ constexpr int kTY = 32;
 constexpr int kYB = 4;
 constexpr int kNS = 4;
 constexpr int kThreads = 256;
-constexpr int kMaxTiledR = 6;
+constexpr int kMaxTiledR = 6;      // cube (larger cubes: van Herk / Gil-Werman passes)
+constexpr int kMaxTiledBallR = 10;  // ball: its x-line levels fit shared memory up to 10
 
 struct MorphParams {
   Job job;
@@ -562,6 +563,14 @@ cudaError_t dispatch_r(int r, const MorphParams& P, const CUtensorMap& map, dim3
     case 5: return launch_mzm<5, BALL>(P, map, grid, s);
     case 6: return launch_mzm<6, BALL>(P, map, grid, s);
   }
+  if constexpr (BALL) {
+    switch (r) {
+      case 7: return launch_mzm<7, BALL>(P, map, grid, s);
+      case 8: return launch_mzm<8, BALL>(P, map, grid, s);
+      case 9: return launch_mzm<9, BALL>(P, map, grid, s);
+      case 10: return launch_mzm<10, BALL>(P, map, grid, s);
+    }
+  }
   return cudaErrorInvalidValue;
 }
 
@@ -863,7 +872,8 @@ cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStr
   const cudaError_t e16 = launch_morph16(job, se, rad, is_dilate, s);
   if (e16 != cudaErrorNotSupported) return e16;
   const int ball = se == HP_SE_BALL;
-  const bool tiled = rad >= 1 && rad <= kMaxTiledR && job.gdims[2] >= rad && job.gdims[1] >= rad;
+  const bool tiled = rad >= 1 && rad <= (ball ? kMaxTiledBallR : kMaxTiledR) &&
+                     job.gdims[2] >= rad && job.gdims[1] >= rad;
   if (!tiled && morph_uses_vhgw(job, se, rad)) {
     switch (job.in.dtype) {
       case HP_U8: return vhgw_cube<uint8_t>(job, rad, is_dilate, s);

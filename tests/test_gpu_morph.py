@@ -182,3 +182,19 @@ def test_full_size_face_planes_ball3_1024():
             del y
     finally:
         oracle.use_threads(False)
+
+
+@pytest.mark.parametrize("dtype,rad", [(np.uint8, 7), (np.uint16, 8), (np.float16, 9),
+                                       (np.float32, 10), (np.uint16, 10)])
+def test_ball_radius_7_to_10_tiled(dtype, rad):
+    """Balls of radius 7-10 run the tiled z-march (x-line levels in shared
+    memory, disks per |dz|, register z ring): bit-exact against the oracle
+    on ragged tiles (70 = 2 x 32 + 6 columns, 36 = 32 + 4 rows) and a volume
+    as thin as the radius allows."""
+    for shape in [(8, 36, 70), (5, rad, rad + 1)]:
+        f = rand_volume(dtype, shape, 50 + rad)
+        x = to_dev(f)
+        e = to_np(hp.erode3d(x, "ball", rad))
+        d = to_np(hp.dilate3d(x, "ball", rad))
+        assert np.array_equal(e.view(np.uint8), oracle.erode3d(f, oracle.SE_BALL, rad).view(np.uint8))
+        assert np.array_equal(d.view(np.uint8), oracle.dilate3d(f, oracle.SE_BALL, rad).view(np.uint8))

@@ -44,7 +44,12 @@ constexpr int kYB = 4;
 constexpr int kNS = 4;
 constexpr int kThreads = 256;
 constexpr int kMaxTiledR = 6;      // cube (larger cubes: van Herk / Gil-Werman passes)
-constexpr int kMaxTiledBallR = 10;  // ball: its x-line levels fit shared memory up to 10
+constexpr int kMaxTiledBallR = kMaxMorphR;  // ball: every accepted radius
+// Balls above this radius take 16-row tiles with two output rows per thread
+// (so that the z ring of 2r + 1 slots stays in registers) and a single
+// line-minimum buffer (the r + 1 levels of the tile's rows fill ~108 KB at
+// r = 16), with a second barrier per phase.
+constexpr int kMaxDblR = 10;
 
 struct MorphParams {
   Job job;
@@ -168,7 +173,11 @@ struct KeyMask {
 // row <-> y = cy0 - R + row; M (x-line minima, double-buffered) [NL][BH][kMS].
 template <int R, int BALL>
 struct MGeom {
-  static constexpr int BH = kTY + 2 * R;
+  static constexpr bool BIG = BALL && R > kMaxDblR;
+  static constexpr int TY = BIG ? 16 : kTY;   // tile rows
+  static constexpr int YB = BIG ? 2 : kYB;    // output rows per thread (disks, z ring)
+  static constexpr int NMB = BIG ? 1 : 2;     // line-minimum buffers
+  static constexpr int BH = TY + 2 * R;
   static constexpr int KWN = kTX + 2 * R;
   static constexpr int KW = key_stride(KWN);
   static constexpr int NC = (KWN + 31) / 32;
@@ -176,7 +185,8 @@ struct MGeom {
   static constexpr int NR = 2 * R + 1;         // z accumulator ring
   static constexpr int KSZ = BH * KW;
   static constexpr int MSZ = NL * BH * kMS;
-  static constexpr int TAIL = (2 * KSZ + 2 * MSZ) * 4 + BH * 4;
+  static constexpr int TAIL = (2 * KSZ + NMB * MSZ) * 4 + BH * 4;
+  static_assert(kThreads == kTX * TY / YB && BH <= kThreads / (kTX / 8), "thread map");
 };
 
 __host__ __device__ inline void mbox_geom(int r, int es, int* ra, int* bw) {
@@ -185,15 +195,15 @@ __host__ __device__ inline void mbox_geom(int r, int es, int* ra, int* bw) {
   *bw = round_up(kTX + *ra + r, al);
 }
 
-__host__ __device__ inline int mstage_bytes(int r, int es) {
+__host__ __device__ inline int mstage_bytes(int r, int es, int ty) {
   int ra, bw;
   mbox_geom(r, es, &ra, &bw);
-  return round_up(bw * (kTY + 2 * r) * es, 128);
+  return round_up(bw * (ty + 2 * r) * es, 128);
 }
 
 template <int R, int BALL>
 __host__ __device__ inline int mzm_smem_bytes(int es) {
-  return 128 + kNS * mstage_bytes(R, es) + MGeom<R, BALL>::TAIL;
+  return 128 + kNS * mstage_bytes(R, es, MGeom<R, BALL>::TY) + MGeom<R, BALL>::TAIL;
 }
 
 template <typename TIN, int R, int BALL>
@@ -319,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
   const int64_t cx0 = J.core_lo[2] + (int64_t)tx * kTX;
-  const int64_t cy0 = J.core_lo[1] + (int64_t)ty * kTY;
+  const int64_t cy0 = J.core_lo[1] + (int64_t)ty * G::TY;
   const int64_t cz0 = J.core_lo[0] + (int64_t)blockIdx.y * P.zchunk;
   const int64_t cz1 = min(cz0 + (int64_t)P.zchunk, J.core_hi[0]);
   if (cz0 >= cz1) return;
@@ -330,16 +340,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int es = dt == HP_U8 ? 1 : (dt == HP_F32 ? 4 : 2);
   int ra, bw;
   mbox_geom(R, es, &ra, &bw);
-  const int sbytes = mstage_bytes(R, es);
+  const int sbytes = mstage_bytes(R, es, G::TY);
   const bool tma = P.use_tma != 0;
   const uint32_t flip = P.is_dilate ? key_mask(dt) : 0u;
-  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + kTY + R > Gy);
+  const bool face = (cx0 - R < 0) || (cx0 + kTX + R > Gx) || (cy0 - R < 0) || (cy0 + G::TY + R > Gy);
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   unsigned char* stages = smem + 128;
   uint32_t* K = reinterpret_cast<uint32_t*>(stages + kNS * sbytes);
   uint32_t* M = K + 2 * G::KSZ;
-  int* srow = reinterpret_cast<int*>(M + 2 * G::MSZ);
+  int* srow = reinterpret_cast<int*>(M + G::NMB * G::MSZ);
 
   for (int row = tid; row < G::BH; row += kThreads) {
     const int64_t sy = reflect(cy0 - R + row, Gy);
@@ -392,16 +402,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   const int xrow = tid / (kTX / 8), xg = (tid % (kTX / 8)) * 8;
-  const int yx = tid % kTX, yb = (tid / kTX) * kYB;
+  constexpr int YB = G::YB;
+  const int yx = tid % kTX, yb = (tid / kTX) * YB;
 
-  uint32_t acc[G::NR][kYB];
+  uint32_t acc[G::NR][YB];
 #pragma unroll
   for (int s = 0; s < G::NR; ++s)
 #pragma unroll
-    for (int i = 0; i < kYB; ++i) acc[s][i] = 0xFFFFFFFFu;
+    for (int i = 0; i < YB; ++i) acc[s][i] = 0xFFFFFFFFu;
 
   // phase p: stage keys of plane p, x-line minima of plane p-1, disk minima
-  // and z push of plane p-2; one barrier per phase.
+  // and z push of plane p-2; one barrier per phase. With one line-minimum
+  // buffer (large balls) the disks of plane p-2 come first, then a barrier,
+  // then the x-line minima of plane p-1 overwrite the buffer.
   int p = 0;
   for (; p < total + 2; ++p) {
     if (p < total) {
@@ -434,60 +447,84 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-    if (p >= 1 && p - 1 < total && xrow < G::BH) {
-      const uint32_t* Kb = K + ((p - 1) & 1) * G::KSZ;
-      uint32_t* Mb = M + ((p - 1) & 1) * G::MSZ;
-      uint32_t w[8 + 2 * R];
+    auto xline_part = [&]() {
+      if (p >= 1 && p - 1 < total && xrow < G::BH) {
+        const uint32_t* Kb = K + ((p - 1) & 1) * G::KSZ;
+        uint32_t* Mb = M + (G::BIG ? 0 : ((p - 1) & 1) * G::MSZ);
+        uint32_t w[8 + 2 * R];
 #pragma unroll
-      for (int j = 0; j < 8 + 2 * R; ++j) w[j] = Kb[xrow * G::KW + xg + j];
-      // window index j <-> x = cx0 + xg - R + j. Line minima of growing
-      // half-length: M1 = min of 3, then M_L[j] = min(M_{L-1}[j-1], M_{L-1}[j+1])
-      // (the two windows of half-length L-1 cover the one of half-length L).
-      uint32_t m[8 + 2 * R];
+        for (int j = 0; j < 8 + 2 * R; ++j) w[j] = Kb[xrow * G::KW + xg + j];
+        // window index j <-> x = cx0 + xg - R + j. Line minima of growing
+        // half-length: M1 = min of 3, then M_L[j] = min(M_{L-1}[j-1], M_{L-1}[j+1])
+        // (the two windows of half-length L-1 cover the one of half-length L).
+        uint32_t m[8 + 2 * R];
 #pragma unroll
-      for (int j = 0; j < 8 + 2 * R; ++j) m[j] = w[j];
+        for (int j = 0; j < 8 + 2 * R; ++j) m[j] = w[j];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (BALL) Mb[(0 * G::BH + xrow) * kMS + xg + i] = w[i + R];
+        for (int i = 0; i < 8; ++i)
+          if (BALL) Mb[(0 * G::BH + xrow) * kMS + xg + i] = w[i + R];
 #pragma unroll
-      for (int L = 1; L <= R; ++L) {
-        uint32_t t[8 + 2 * R];
+        for (int L = 1; L <= R; ++L) {
+          uint32_t t[8 + 2 * R];
 #pragma unroll
-        for (int j = L; j < 8 + 2 * R - L; ++j)
-          t[j] = L == 1 ? min(min(m[j - 1], m[j]), m[j + 1]) : min(m[j - 1], m[j + 1]);
+          for (int j = L; j < 8 + 2 * R - L; ++j)
+            t[j] = L == 1 ? min(min(m[j - 1], m[j]), m[j + 1]) : min(m[j - 1], m[j + 1]);
 #pragma unroll
-        for (int j = L; j < 8 + 2 * R - L; ++j) m[j] = t[j];
-        if (BALL || L == R) {
+          for (int j = L; j < 8 + 2 * R - L; ++j) m[j] = t[j];
+          if (BALL || L == R) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            Mb[((BALL ? L : 0) * G::BH + xrow) * kMS + xg + i] = m[i + R];
-        }
-      }
-    }
-    if (p >= 2) {
-      const int n = p - 2;
-      const uint32_t* Mb = M + (n & 1) * G::MSZ;
-      uint32_t D[BALL ? R + 1 : 1][kYB];
-      static_assert(kMS == 32 + 1, "disk_min assumes the line-minimum row stride");
-      if constexpr (BALL && R == 3)
-        disk_rows_ball3<G::BH, kYB>(D, Mb + yb * kMS + yx);
-      else
-        disk_rows<R, BALL, G::BH, 0, kYB>(D, Mb + yb * kMS + yx);
-      uint32_t done[kYB];
-      push_dispatch<R, BALL>(n % G::NR, acc, D, done);
-      const int64_t gz = cz0 - R + n - R, gx = cx0 + yx;  // plane n's input z minus R
-      if (gz >= cz0 && gz < cz1 && gx < J.core_hi[2]) {
-        const DevOut& O = J.out;
-#pragma unroll
-        for (int i = 0; i < kYB; ++i) {
-          const int64_t gy = cy0 + yb + i;
-          if (gy < J.core_hi[1]) {
-            const int64_t idx =
-                ((gz - O.lo[0]) * O.dims[1] + (gy - O.lo[1])) * O.dims[2] + (gx - O.lo[2]);
-            store_key(O.ptr, dt, idx, done[i] ^ flip);
+            for (int i = 0; i < 8; ++i)
+              Mb[((BALL ? L : 0) * G::BH + xrow) * kMS + xg + i] = m[i + R];
           }
         }
       }
+    };
+    auto disk_part = [&]() {
+      if (p >= 2) {
+        const int n = p - 2;
+        const uint32_t* Mb = M + (G::BIG ? 0 : (n & 1) * G::MSZ);
+        uint32_t D[BALL ? R + 1 : 1][YB];
+        static_assert(kMS == 32 + 1, "disk_min assumes the line-minimum row stride");
+        if constexpr (BALL && R == 3)
+          disk_rows_ball3<G::BH, YB>(D, Mb + yb * kMS + yx);
+        else
+          disk_rows<R, BALL, G::BH, 0, YB>(D, Mb + yb * kMS + yx);
+        uint32_t done[YB];
+        if constexpr (G::BIG) {
+          // shift ring: acc[s] holds the output centred on plane n - R + s;
+          // plane n adds its disk at |s - R|, the output of slot 0 is complete
+#pragma unroll
+          for (int i = 0; i < YB; ++i) {
+            done[i] = min(acc[0][i], D[R][i]);
+#pragma unroll
+            for (int s2 = 1; s2 <= 2 * R; ++s2) acc[s2 - 1][i] = min(acc[s2][i], D[s2 > R ? s2 - R : R - s2][i]);
+            acc[2 * R][i] = 0xFFFFFFFFu;
+          }
+        } else {
+          push_dispatch<R, BALL>(n % G::NR, acc, D, done);
+        }
+        const int64_t gz = cz0 - R + n - R, gx = cx0 + yx;  // plane n's input z minus R
+        if (gz >= cz0 && gz < cz1 && gx < J.core_hi[2]) {
+          const DevOut& O = J.out;
+#pragma unroll
+          for (int i = 0; i < YB; ++i) {
+            const int64_t gy = cy0 + yb + i;
+            if (gy < J.core_hi[1]) {
+              const int64_t idx =
+                  ((gz - O.lo[0]) * O.dims[1] + (gy - O.lo[1])) * O.dims[2] + (gx - O.lo[2]);
+              store_key(O.ptr, dt, idx, done[i] ^ flip);
+            }
+          }
+        }
+      }
+    };
+    if constexpr (G::BIG) {
+      disk_part();
+      __syncthreads();
+      xline_part();
+    } else {
+      xline_part();
+      disk_part();
     }
     __syncthreads();
     if (s_abort) break;
@@ -569,6 +606,12 @@ cudaError_t dispatch_r(int r, const MorphParams& P, const CUtensorMap& map, dim3
       case 8: return launch_mzm<8, BALL>(P, map, grid, s);
       case 9: return launch_mzm<9, BALL>(P, map, grid, s);
       case 10: return launch_mzm<10, BALL>(P, map, grid, s);
+      case 11: return launch_mzm<11, BALL>(P, map, grid, s);
+      case 12: return launch_mzm<12, BALL>(P, map, grid, s);
+      case 13: return launch_mzm<13, BALL>(P, map, grid, s);
+      case 14: return launch_mzm<14, BALL>(P, map, grid, s);
+      case 15: return launch_mzm<15, BALL>(P, map, grid, s);
+      case 16: return launch_mzm<16, BALL>(P, map, grid, s);
     }
   }
   return cudaErrorInvalidValue;
@@ -899,8 +942,9 @@ cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStr
   P.job = job;
   P.is_dilate = is_dilate;
   P.err = device_error_word();
+  const int ty_rows = (ball && rad > kMaxDblR) ? 16 : kTY;  // MGeom<rad, ball>::TY
   P.tiles_x = (int)((cx + kTX - 1) / kTX);
-  const int64_t tiles = (int64_t)P.tiles_x * ((cy + kTY - 1) / kTY);
+  const int64_t tiles = (int64_t)P.tiles_x * ((cy + ty_rows - 1) / ty_rows);
   const int64_t want = (int64_t)num_sms() * 8;
   int64_t nchunks = std::max<int64_t>(1, (want + tiles - 1) / tiles);
   int64_t zc = (cz + nchunks - 1) / nchunks;
@@ -918,7 +962,7 @@ cudaError_t launch_morph(const Job& job, int se, int rad, int is_dilate, cudaStr
     int ra = 0, bw = 0;
     mbox_geom(rad, (int)es, &ra, &bw);
     const int64_t dims[3] = {job.in.dims[2], job.in.dims[1], job.in.dims[0]};
-    use_tma = make_tmap_3d(&map, job.in.ptr, job.in.dtype, dims, bw, kTY + 2 * rad);
+    use_tma = make_tmap_3d(&map, job.in.ptr, job.in.dtype, dims, bw, ty_rows + 2 * rad);
   }
   P.use_tma = use_tma ? 1 : 0;
   if (log_level() > 0)

@@ -198,3 +198,46 @@ def test_ball_radius_7_to_10_tiled(dtype, rad):
         d = to_np(hp.dilate3d(x, "ball", rad))
         assert np.array_equal(e.view(np.uint8), oracle.erode3d(f, oracle.SE_BALL, rad).view(np.uint8))
         assert np.array_equal(d.view(np.uint8), oracle.dilate3d(f, oracle.SE_BALL, rad).view(np.uint8))
+
+
+@pytest.mark.parametrize("dtype,rad", [(np.uint8, 11), (np.float32, 12), (np.uint16, 13),
+                                       (np.float16, 14), (np.float32, 16), (np.uint16, 16)])
+def test_ball_radius_11_to_16_tiled(dtype, rad):
+    """Balls of radius 11-16 run the tiled z-march on 16-row tiles (two
+    output rows per thread, one line-minimum buffer, a shift ring in z):
+    bit-exact against the oracle's brute force on ragged tiles (20 = 16 + 4
+    rows, 40 = 32 + 8 columns), a volume as thin as the radius allows, and
+    (r = 12) a z extent split into chunks of 32 and 8 planes."""
+    shapes = [(8, 20, 40), (6, rad, rad + 1)] + ([(40, 20, 40)] if rad == 12 else [])
+    for shape in shapes:
+        f = rand_volume(dtype, shape, 70 + rad)
+        x = to_dev(f)
+        e = to_np(hp.erode3d(x, "ball", rad))
+        d = to_np(hp.dilate3d(x, "ball", rad))
+        assert np.array_equal(e.view(np.uint8), oracle.erode3d(f, oracle.SE_BALL, rad).view(np.uint8)), shape
+        assert np.array_equal(d.view(np.uint8), oracle.dilate3d(f, oracle.SE_BALL, rad).view(np.uint8)), shape
+
+
+def test_large_ball_out_of_core_within_budget():
+    """Host-mode dilation with the r = 13 ball under a budget that forces
+    several bricks: equal bit for bit to the device-mode call, within the
+    budget, and equal to the oracle on sampled boxes (corners, faces,
+    interior)."""
+    f = synth.porous((64, 72, 80), 35)[0]
+    r, b = 13, 8
+    budget = 2_400_000
+    old = hp.get_memory_budget()
+    try:
+        hp.set_memory_budget(budget)
+        host = hp.dilate3d(f, "ball", r)
+        st = hp.stats()
+    finally:
+        hp.set_memory_budget(old)
+    assert st["bricks"] >= 3 and 0 < st["peak_device_bytes"] <= budget and st["live_device_bytes"] == 0
+    assert np.array_equal(host, to_np(hp.dilate3d(to_dev(f), "ball", r)))
+    for lo in [(0, 0, 0), (56, 64, 72), (30, 0, 40), (5, 40, 0), (44, 17, 71)]:
+        ilo = [max(0, c - r) for c in lo]
+        ihi = [min(n, c + b + r) for c, n in zip(lo, f.shape)]
+        ref = oracle.dilate3d(f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]], oracle.SE_BALL, r,
+                              gdims=f.shape, in_lo=ilo, out_lo=lo, out_shape=(b, b, b))
+        assert np.array_equal(host[lo[0]:lo[0] + b, lo[1]:lo[1] + b, lo[2]:lo[2] + b], ref), lo

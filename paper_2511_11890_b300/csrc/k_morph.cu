@@ -734,104 +734,55 @@ cudaError_t launch_local_threshold(const void* f, int dtype, const float* m, flo
 // starting at j is then min(H[j], G[j + 2L]) (it spans at most two adjacent
 // blocks). Three comparisons per sample and axis, whatever L.
 //
-// A CTA takes kVL lines x kVS outputs of one axis: it stages the kVS + 2L
-// reflected samples of each line in shared memory (keys), scans the blocks
-// (one thread per block) and writes the outputs. The x and y passes write
-// keys to scratch regions (sep_regions); the z pass writes the output dtype.
+// Each line streams through registers in blocks of 2L + 1 (k_vhgw_col for
+// z and y lines, one thread per line with coalesced rows; k_vhgw_rows for x
+// lines, staged through shared memory). The x and y passes write keys to
+// scratch regions (sep_regions); the z pass writes the output dtype.
 namespace {
-constexpr int kVL = 32;   // lines per CTA
-constexpr int kVS = 128;  // outputs per line per CTA
-constexpr int kVT = 256;  // threads per CTA
-
 struct VBox {
   int64_t lo[3], dims[3];  // dense box of the global volume
 };
 
-// Source of a pass: the job's input (element type TIN, keys formed and
-// flipped on load) or a key scratch region (TIN = uint32_t, keys as stored).
-template <typename TIN, bool RAW, int AXIS>
-__global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, VBox S,
+// Running min along z or y, one thread per line: consecutive threads take
+// consecutive x, so every load and store of a warp is one coalesced row. A thread streams its line's samples (a segment of kVC
+// outputs plus 2L on each side) in blocks of K = 2L + 1 kept in registers:
+// the suffix minima h of the current block and the next block's samples c;
+// the output at block offset t is h[0] for t = 0, else min(h[t], c[0..t-1]).
+// No shared memory; the K loads of a block are issued before they are used.
+constexpr int kVC = 256;  // outputs per line segment
+constexpr int kVCT = 128; // threads per CTA
+
+template <typename TIN, bool RAW, int AXIS, int L>
+__global__ void __launch_bounds__(kVCT) k_vhgw_col(const TIN* __restrict__ src, VBox S,
                                                    void* __restrict__ dst, VBox D, int dst_dtype,
-                                                   int L, int64_t Gn, uint32_t flip,
-                                                   int64_t nlines, int64_t nseg) {
-  constexpr int axis = AXIS;
-  extern __shared__ uint32_t vsm[];
-  const int W = kVS + 2 * L;  // staged samples per line
-  const int WS = W | 1;       // row stride: odd, so the lines of a warp's scans fall in distinct banks
-  uint32_t* E = vsm;
-  uint32_t* G = E + kVL * WS;
-  uint32_t* H = G + kVL * WS;
-  const int64_t line0 = (int64_t)blockIdx.x * kVL;
-  const int64_t seg0 = (int64_t)blockIdx.y * kVS;  // first output along the axis (region index)
-  const int tid = threadIdx.x;
-  // region of this pass = D's box; lines enumerate the other two axes of D
-  // (x fastest), so consecutive lines are consecutive x for the y and z passes
-  constexpr int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;  // the other axes, slow then fast
-  auto line_coords = [&](int64_t l, int64_t c[3]) {
-    c[a2] = D.lo[a2] + l % D.dims[a2];
-    c[a1] = D.lo[a1] + l / D.dims[a2];
+                                                   int64_t Gn, uint32_t flip, int64_t nlines,
+                                                   int64_t nseg) {
+  constexpr int K = 2 * L + 1;
+  constexpr int a1 = AXIS == 0 ? 1 : 0, a2 = AXIS == 2 ? 1 : 2;  // the other axes, slow then fast
+  const int64_t l = (int64_t)blockIdx.x * kVCT + threadIdx.x;
+  if (l >= nlines) return;
+  const int64_t s0 = (int64_t)blockIdx.y * kVC;  // first output of the segment (region index)
+  const int n = (int)min((int64_t)kVC, nseg - s0);
+  int64_t c3[3];
+  c3[a2] = D.lo[a2] + l % D.dims[a2];
+  c3[a1] = D.lo[a1] + l / D.dims[a2];
+  c3[AXIS] = S.lo[AXIS];
+  const int64_t sb = ((c3[0] - S.lo[0]) * S.dims[1] + (c3[1] - S.lo[1])) * S.dims[2] + (c3[2] - S.lo[2]);
+  c3[AXIS] = D.lo[AXIS];
+  const int64_t db = ((c3[0] - D.lo[0]) * D.dims[1] + (c3[1] - D.lo[1])) * D.dims[2] + (c3[2] - D.lo[2]);
+  const int64_t sstr = AXIS == 2 ? 1 : (AXIS == 1 ? S.dims[2] : S.dims[1] * S.dims[2]);
+  const int64_t dstr = AXIS == 2 ? 1 : (AXIS == 1 ? D.dims[2] : D.dims[1] * D.dims[2]);
+  const int64_t p0 = D.lo[AXIS] + s0 - L;  // global axis coordinate of sample 0
+  const int ns = n + 2 * L;                // samples of the segment
+  const bool inner = p0 >= 0 && p0 + ns <= Gn;  // the same for the whole CTA
+  const TIN* sp = src + sb - S.lo[AXIS] * sstr;
+  auto load = [&](int i) -> uint32_t {
+    const int64_t g = inner ? p0 + i : reflect(p0 + i, Gn);
+    if constexpr (RAW) return to_key<TIN>(sp[g * sstr]) ^ flip;
+    else return (uint32_t)sp[g * sstr];
   };
-  // stage: along x, consecutive threads walk a line; along y and z they walk
-  // the lines (adjacent x)
-  for (int i = tid; i < kVL * W; i += kVT) {
-    int ln, pos;
-    if (axis == 2) {
-      ln = i / W;
-      pos = i % W;
-    } else {
-      ln = i % kVL;
-      pos = i / kVL;
-    }
-    const int64_t l = line0 + ln;
-    uint32_t key = 0xFFFFFFFFu;  // identity of min: samples no output reads
-    if (l < nlines && seg0 + pos < nseg + 2 * L) {
-      int64_t c[3];
-      line_coords(l, c);
-      c[axis] = reflect(D.lo[axis] + seg0 - L + pos, Gn);
-      const int64_t q = ((c[0] - S.lo[0]) * S.dims[1] + (c[1] - S.lo[1])) * S.dims[2] + (c[2] - S.lo[2]);
-      if constexpr (RAW) key = to_key<TIN>(src[q]) ^ flip;
-      else key = (uint32_t)src[q];
-    }
-    E[ln * WS + pos] = key;
-  }
-  __syncthreads();
-  // prefix / suffix minima per block of k = 2L + 1 samples
-  const int k = 2 * L + 1;
-  const int nb = (W + k - 1) / k;
-  for (int t = tid; t < kVL * nb; t += kVT) {
-    const int ln = t / nb, b0 = (t % nb) * k, b1 = min(b0 + k, W);
-    const uint32_t* e = E + ln * WS;
-    uint32_t* g = G + ln * WS;
-    uint32_t* h = H + ln * WS;
-    uint32_t m = 0xFFFFFFFFu;
-    for (int j = b0; j < b1; ++j) {
-      m = min(m, e[j]);
-      g[j] = m;
-    }
-    m = 0xFFFFFFFFu;
-    for (int j = b1 - 1; j >= b0; --j) {
-      m = min(m, e[j]);
-      h[j] = m;
-    }
-  }
-  __syncthreads();
-  // outputs: window [o, o + 2L] of the staged line
-  for (int i = tid; i < kVL * kVS; i += kVT) {
-    int ln, o;
-    if (axis == 2) {
-      ln = i / kVS;
-      o = i % kVS;
-    } else {
-      ln = i % kVL;
-      o = i / kVL;
-    }
-    const int64_t l = line0 + ln;
-    if (l >= nlines || seg0 + o >= nseg) continue;
-    const uint32_t m = min(H[ln * WS + o], G[ln * WS + o + 2 * L]);
-    int64_t c[3];
-    line_coords(l, c);
-    c[axis] = D.lo[axis] + seg0 + o;
-    const int64_t q = ((c[0] - D.lo[0]) * D.dims[1] + (c[1] - D.lo[1])) * D.dims[2] + (c[2] - D.lo[2]);
+  auto put = [&](int j, uint32_t m) {
+    const int64_t q = db + (s0 + j) * dstr;
     switch (dst_dtype) {
       case -1: static_cast<uint32_t*>(dst)[q] = m; break;  // keys (scratch)
       case HP_U8: static_cast<uint8_t*>(dst)[q] = from_key<uint8_t>(m ^ flip); break;
@@ -839,30 +790,214 @@ __global__ void __launch_bounds__(kVT) k_vhgw_pass(const TIN* __restrict__ src, 
       case HP_F16: static_cast<__half*>(dst)[q] = from_key<__half>(m ^ flip); break;
       default: static_cast<float*>(dst)[q] = from_key<float>(m ^ flip); break;
     }
+  };
+  uint32_t h[K];
+#pragma unroll
+  for (int t = 0; t < K; ++t) h[t] = load(t);  // ns >= K: a segment has n >= 1
+#pragma unroll
+  for (int t = K - 2; t >= 0; --t) h[t] = min(h[t], h[t + 1]);
+  for (int b0 = 0; b0 < n; b0 += K) {
+    uint32_t c[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) c[t] = b0 + K + t < ns ? load(b0 + K + t) : 0xFFFFFFFFu;
+    put(b0, h[0]);
+    uint32_t g = 0xFFFFFFFFu;
+#pragma unroll
+    for (int t = 1; t < K; ++t) {
+      g = min(g, c[t - 1]);
+      if (b0 + t < n) put(b0 + t, min(h[t], g));
+    }
+#pragma unroll
+    for (int t = K - 1; t >= 0; --t) h[t] = t == K - 1 ? c[t] : min(c[t], h[t + 1]);
   }
 }
 
-size_t vhgw_smem(int L) { return (size_t)3 * kVL * ((kVS + 2 * L) | 1) * sizeof(uint32_t); }
-
-template <typename TIN, bool RAW, int AXIS>
-cudaError_t vhgw_launch(const TIN* src, const VBox& S, void* dst, const VBox& D, int dst_dtype,
-                        int L, int64_t Gn, uint32_t flip, cudaStream_t s) {
+template <typename TIN, bool RAW, int AXIS, int L>
+cudaError_t vhgw_col_launch_l(const TIN* src, const VBox& S, void* dst, const VBox& D,
+                              int dst_dtype, int64_t Gn, uint32_t flip, cudaStream_t s) {
   constexpr int a1 = AXIS == 0 ? 1 : 0, a2 = AXIS == 2 ? 1 : 2;
   const int64_t nlines = D.dims[a1] * D.dims[a2], nseg = D.dims[AXIS];
   if (nlines <= 0 || nseg <= 0) return cudaSuccess;
-  const size_t smem = vhgw_smem(L);
+  const dim3 grid((unsigned)((nlines + kVCT - 1) / kVCT), (unsigned)((nseg + kVC - 1) / kVC));
+  k_vhgw_col<TIN, RAW, AXIS, L><<<grid, kVCT, 0, s>>>(src, S, dst, D, dst_dtype, Gn, flip, nlines,
+                                                      nseg);
+  return cudaGetLastError();
+}
+
+template <typename TIN, bool RAW, int AXIS>
+cudaError_t vhgw_col_launch(const TIN* src, const VBox& S, void* dst, const VBox& D,
+                            int dst_dtype, int L, int64_t Gn, uint32_t flip, cudaStream_t s) {
+  switch (L) {
+#define HP_VC(LL) \
+  case LL: return vhgw_col_launch_l<TIN, RAW, AXIS, LL>(src, S, dst, D, dst_dtype, Gn, flip, s);
+    HP_VC(1) HP_VC(2) HP_VC(3) HP_VC(4) HP_VC(5) HP_VC(6) HP_VC(7) HP_VC(8)
+    HP_VC(9) HP_VC(10) HP_VC(11) HP_VC(12) HP_VC(13) HP_VC(14) HP_VC(15) HP_VC(16)
+#undef HP_VC
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The x pass of the same recurrence: a CTA stages kVR rows x (kVX + 2L)
+// samples as keys in shared memory with coalesced loads, one thread then
+// streams each row through the register recurrence (threads of a warp read
+// one column of 32 rows: an odd row stride puts them in distinct banks) and
+// writes its outputs over the samples it has consumed, and the CTA stores
+// the outputs with coalesced writes.
+constexpr int kVR = 128;  // rows per CTA, one thread each
+constexpr int kVX = 64;   // outputs per row per CTA
+
+template <int L>
+constexpr int vhgw_rows_ws() { return (kVX + 2 * L) | 1; }
+
+template <typename TIN, int L>
+__global__ void __launch_bounds__(kVR) k_vhgw_rows(const TIN* __restrict__ src, VBox S,
+                                                   uint32_t* __restrict__ dst, VBox D, int64_t Gn,
+                                                   uint32_t flip, int64_t nlines, int64_t nseg,
+                                                   int vec_rows) {
+  constexpr int K = 2 * L + 1, W = kVX + 2 * L, WS = vhgw_rows_ws<L>();
+  constexpr int EPV = 16 / (int)sizeof(TIN);  // elements per 16-byte word
+  extern __shared__ uint32_t Er[];
+  __shared__ int64_t s_sb[kVR], s_db[kVR];
+  const int tid = threadIdx.x;
+  // segments are the fast grid index: CTAs that run together take adjacent
+  // segments of the same rows and share their halo lines in L2; row groups
+  // beyond the grid's y extent are taken in further rounds
+  const int64_t s0 = (int64_t)blockIdx.x * kVX;  // first output of the segment (region index)
+  for (int64_t line0 = (int64_t)blockIdx.y * kVR; line0 < nlines; line0 += (int64_t)gridDim.y * kVR) {
+    const int nlin = (int)min((int64_t)kVR, nlines - line0);
+    const int n = (int)min((int64_t)kVX, nseg - s0);
+    const int ns = n + 2 * L;
+    {
+      // this thread's row: lines enumerate (z, y) of D, y fastest
+      const int64_t l = min(line0 + tid, nlines - 1);
+      const int64_t z = D.lo[0] + l / D.dims[1], y = D.lo[1] + l % D.dims[1];
+      s_sb[tid] = ((z - S.lo[0]) * S.dims[1] + (y - S.lo[1])) * S.dims[2] - S.lo[2];
+      s_db[tid] = ((z - D.lo[0]) * D.dims[1] + (y - D.lo[1])) * D.dims[2];
+    }
+    const int64_t p0 = D.lo[2] + s0 - L;  // global x of sample 0
+    const bool inner = p0 >= 0 && p0 + ns <= Gn;
+    __syncthreads();
+    if (inner && vec_rows) {
+      // rows start on 16-byte boundaries (vec_rows): stage whole aligned
+      // 16-byte words covering samples [0, ns) of each row; a word never
+      // crosses the end of its row (row lengths are whole words)
+      const int64_t off0 = p0 - S.lo[2];               // element offset of sample 0 in its row
+      const int64_t w0 = off0 & ~(int64_t)(EPV - 1);   // first word's element offset
+      const int nw = (int)((off0 + ns - w0 + EPV - 1) / EPV);
+      constexpr int kU = 4;  // 16-byte loads in flight per thread
+      for (int i0 = tid; i0 < nlin * nw; i0 += kVR * kU) {
+        uint4 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int i = i0 + u * kVR;
+          if (i < nlin * nw) {
+            const int r = i / nw, k = i - r * nw;
+            v[u] = *reinterpret_cast<const uint4*>(src + s_sb[r] + S.lo[2] + w0 + (int64_t)k * EPV);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int i = i0 + u * kVR;
+          if (i < nlin * nw) {
+            const int r = i / nw, k = i - r * nw;
+            const TIN* el = reinterpret_cast<const TIN*>(&v[u]);
+            const int pos0 = (int)(w0 - off0) + k * EPV;
+#pragma unroll
+            for (int q = 0; q < EPV; ++q)
+              if (pos0 + q >= 0 && pos0 + q < ns) Er[r * WS + pos0 + q] = to_key<TIN>(el[q]) ^ flip;
+          }
+        }
+      }
+      // rows past the last line and samples past ns keep the identity
+      for (int i = tid; i < kVR * W; i += kVR) {
+        const int r = i / W, pos = i - r * W;
+        if (r >= nlin || pos >= ns) Er[r * WS + pos] = 0xFFFFFFFFu;
+      }
+    } else {
+      constexpr int kU = 8;  // loads in flight per thread
+      for (int i0 = tid; i0 < kVR * W; i0 += kVR * kU) {
+        uint32_t key[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int i = i0 + u * kVR, r = i / W, pos = i - r * W;
+          key[u] = 0xFFFFFFFFu;
+          if (i < kVR * W && r < nlin && pos < ns) {
+            const int64_t g = inner ? p0 + pos : reflect(p0 + pos, Gn);
+            key[u] = to_key<TIN>(src[s_sb[r] + g]) ^ flip;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int i = i0 + u * kVR;
+          if (i < kVR * W) Er[(i / W) * WS + (i % W)] = key[u];
+        }
+      }
+    }
+    __syncthreads();
+    {
+      uint32_t* e = Er + tid * WS;
+      uint32_t h[K];
+#pragma unroll
+      for (int t = 0; t < K; ++t) h[t] = e[t];
+#pragma unroll
+      for (int t = K - 2; t >= 0; --t) h[t] = min(h[t], h[t + 1]);
+      for (int b0 = 0; b0 < n; b0 += K) {
+        uint32_t c[K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) c[t] = b0 + K + t < ns ? e[b0 + K + t] : 0xFFFFFFFFu;
+        // outputs b0 .. b0 + K - 1 overwrite samples this thread has consumed
+        e[b0] = h[0];
+        uint32_t g = 0xFFFFFFFFu;
+#pragma unroll
+        for (int t = 1; t < K; ++t) {
+          g = min(g, c[t - 1]);
+          if (b0 + t < n) e[b0 + t] = min(h[t], g);
+        }
+#pragma unroll
+        for (int t = K - 1; t >= 0; --t) h[t] = t == K - 1 ? c[t] : min(c[t], h[t + 1]);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < kVR * kVX; i += kVR) {
+      const int r = i / kVX, o = i - r * kVX;
+      if (r < nlin && o < n) dst[s_db[r] + s0 + o] = Er[r * WS + o];
+    }
+    __syncthreads();  // the next round restages Er and the row offsets
+  }
+}
+
+template <typename TIN, int L>
+cudaError_t vhgw_rows_launch_l(const TIN* src, const VBox& S, uint32_t* dst, const VBox& D,
+                               int64_t Gn, uint32_t flip, cudaStream_t s) {
+  const int64_t nlines = D.dims[0] * D.dims[1], nseg = D.dims[2];
+  if (nlines <= 0 || nseg <= 0) return cudaSuccess;
+  const int smem = kVR * vhgw_rows_ws<L>() * 4;
   static bool attr = false;  // per instantiation
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_vhgw_pass<TIN, RAW, AXIS>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)vhgw_smem(kMaxMorphR));
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_vhgw_rows<TIN, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const dim3 grid((unsigned)((nlines + kVL - 1) / kVL), (unsigned)((nseg + kVS - 1) / kVS));
-  k_vhgw_pass<TIN, RAW, AXIS><<<grid, kVT, smem, s>>>(src, S, dst, D, dst_dtype, L, Gn, flip,
-                                                      nlines, nseg);
+  const dim3 grid((unsigned)((nseg + kVX - 1) / kVX),
+                  (unsigned)std::min<int64_t>((nlines + kVR - 1) / kVR, 65535));
+  // 16-byte staging where every row of the source box starts on a 16-byte boundary
+  const int vec_rows = (reinterpret_cast<uintptr_t>(src) % 16 == 0 && (S.dims[2] * (int64_t)sizeof(TIN)) % 16 == 0);
+  k_vhgw_rows<TIN, L><<<grid, kVR, smem, s>>>(src, S, dst, D, Gn, flip, nlines, nseg, vec_rows);
   return cudaGetLastError();
+}
+
+template <typename TIN>
+cudaError_t vhgw_rows_launch(const TIN* src, const VBox& S, uint32_t* dst, const VBox& D, int L,
+                             int64_t Gn, uint32_t flip, cudaStream_t s) {
+  switch (L) {
+#define HP_VR(LL) \
+  case LL: return vhgw_rows_launch_l<TIN, LL>(src, S, dst, D, Gn, flip, s);
+    HP_VR(1) HP_VR(2) HP_VR(3) HP_VR(4) HP_VR(5) HP_VR(6) HP_VR(7) HP_VR(8)
+    HP_VR(9) HP_VR(10) HP_VR(11) HP_VR(12) HP_VR(13) HP_VR(14) HP_VR(15) HP_VR(16)
+#undef HP_VR
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename TIN>
@@ -881,16 +1016,16 @@ cudaError_t vhgw_cube(const Job& job, int rad, int is_dilate, cudaStream_t s) {
   const VBox core{{job.core_lo[0], job.core_lo[1], job.core_lo[2]},
                   {job.core_hi[0] - job.core_lo[0], job.core_hi[1] - job.core_lo[1],
                    job.core_hi[2] - job.core_lo[2]}};
-  cudaError_t e = vhgw_launch<TIN, true, 2>(static_cast<const TIN*>(job.in.ptr), in, k1, rx, -1,
-                                            rad, job.gdims[2], flip, s);
+  cudaError_t e = vhgw_rows_launch<TIN>(static_cast<const TIN*>(job.in.ptr), in, k1, rx, rad,
+                                        job.gdims[2], flip, s);
   if (e == cudaSuccess)
-    e = vhgw_launch<uint32_t, false, 1>(k1, rx, k2, ry, -1, rad, job.gdims[1], 0u, s);
+    e = vhgw_col_launch<uint32_t, false, 1>(k1, rx, k2, ry, -1, rad, job.gdims[1], 0u, s);
   if (e != cudaSuccess) return e;
   // z pass: region = core, written into the output box (which contains it)
   if (core.lo[0] == out.lo[0] && core.lo[1] == out.lo[1] && core.lo[2] == out.lo[2] &&
       core.dims[0] == out.dims[0] && core.dims[1] == out.dims[1] && core.dims[2] == out.dims[2])
-    return vhgw_launch<uint32_t, false, 0>(k2, ry, job.out.ptr, out, job.out.dtype, rad,
-                                           job.gdims[0], flip, s);
+    return vhgw_col_launch<uint32_t, false, 0>(k2, ry, job.out.ptr, out, job.out.dtype, rad,
+                                               job.gdims[0], flip, s);
   return cudaErrorInvalidValue;  // output boxes equal the core on every path that gets here
 }
 }  // namespace

@@ -2,7 +2,8 @@
 in pinned host memory, processed under hp_set_memory_budget(8e9) as
 halo-padded bricks streamed through the device. Gaussian sigma = 3 (f32
 output, 32 GiB) and ball-radius-5 dilation (u16): chunked output equals the
-unchunked in-HBM result bit for bit, sampled boxes match the oracle, and the
+unchunked in-HBM result bit for bit, sampled boxes (corners, face centres,
+boxes straddling brick boundaries, random) match the oracle, and the
 library never holds more device memory than the budget."""
 import numpy as np
 import pytest
@@ -37,10 +38,22 @@ def _compare_slabs(host_out: torch.Tensor, dev_out: torch.Tensor, slab=64):
     return None
 
 
-def _sample_boxes(rng, k=12, b=16):
-    los = [(0, 0, 0), (N - b, N - b, N - b), (N // 2 - b // 2, 0, N - b)]
-    los += [tuple(int(v) for v in rng.integers(0, N - b, 3)) for _ in range(k - len(los))]
-    return los
+def _sample_boxes(rng, k=12, b=16, halo=9, in_bytes=2, out_bytes=4):
+    """All 8 corners, the 6 face centres, boxes straddling each brick
+    boundary of the executor's plan (same budget, halo and element sizes),
+    and random boxes: k of them on top of the fixed ones."""
+    e, m = N - b, N // 2 - b // 2
+    los = [(z, y, x) for z in (0, e) for y in (0, e) for x in (0, e)]
+    los += [(0, m, m), (e, m, m), (m, 0, m), (m, e, m), (m, m, 0), (m, m, e)]
+    cores, _ = hp.plan_bricks((N, N, N), halo, in_bytes, out_bytes, BUDGET)
+    for c in cores:
+        for ax in range(3):
+            if c[3 + ax] < N:  # an interior face of this brick's core
+                lo = [int(v) for v in rng.integers(0, N - b, 3)]
+                lo[ax] = int(c[3 + ax]) - b // 2
+                los.append(tuple(lo))
+    los += [tuple(int(v) for v in rng.integers(0, N - b, 3)) for _ in range(k)]
+    return list(dict.fromkeys(los))
 
 
 def _run_budgeted(fn):
@@ -71,7 +84,7 @@ def test_gaussian_sigma3_out_of_core(volume):
     # sampled oracle boxes
     r = oracle.radius(3.0)
     refs, gots = [], []
-    for lo in _sample_boxes(np.random.default_rng(2)):
+    for lo in _sample_boxes(np.random.default_rng(2), k=12):
         ilo = [max(0, c - r) for c in lo]
         ihi = [min(N, c + 16 + r) for c in lo]
         part = f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]]
@@ -93,7 +106,7 @@ def test_dilation_ball5_out_of_core(volume):
     assert _compare_slabs(out_h, dd) is None
     del dd, xd
     torch.cuda.empty_cache()
-    for lo in _sample_boxes(np.random.default_rng(3), k=6):
+    for lo in _sample_boxes(np.random.default_rng(3), k=6, halo=5, out_bytes=2):
         ilo = [max(0, c - 5) for c in lo]
         ihi = [min(N, c + 16 + 5) for c in lo]
         part = f[ilo[0]:ihi[0], ilo[1]:ihi[1], ilo[2]:ihi[2]]

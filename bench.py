@@ -27,8 +27,10 @@ and as its OpenMP build on every host core (`cpu_baseline_mt`).
 Other measured configurations, one JSON line each (not the benchmark step):
 `--workload ooc2048` (2048^3 uint16 out-of-core under an 8e9-byte budget,
 host-link efficiency), `spheres128` (128^3 float32 Gaussian -> threshold ->
-cube morphology), `open1024` (1024^3 uint16 opening, closing, top-hat and
-unsharp mask),
+cube morphology), `open1024` (1024^3 uint16 opening, closing, top-hat,
+unsharp mask and Gaussian local threshold), `features1024` (1024^3 uint16
+Hessian components and eigenvalues, box-window mean / Niblack / Sauvola
+thresholds),
 `sweep` (out-of-core Gaussian on 1 to 16 GiB slabs under an 8e9-byte budget),
 `bank512` (512^3 float16 12-filter bank over 37 bricks,
 FMA roofline), `autograd256` (256^3 float32 forward + backward).
@@ -671,6 +673,66 @@ def run_open1024(args):
     return 0
 
 
+def run_features1024(args):
+    """1024^3 uint16 porous volume: the Hessian feature set at sigma 2 (the
+    six second-derivative components to float32, and the three ascending
+    eigenvalues per voxel) and the box-window local thresholds (mean,
+    Niblack, Sauvola; radius 7, a 15^3 window) to uint8."""
+    import torch
+
+    import paper_2511_11890_b300 as hp
+    import synth
+    n = N
+    f, _ = synth.porous(n, SEED)
+    x = torch.from_numpy(f).cuda()
+    stream = torch.cuda.current_stream()
+    hbm_gbs, sm_max_mhz, peak_kind = _peaks()
+    fma_derived, fma_measured, _ = fma_peaks(hp, torch, sm_max_mhz)
+    nvox = n ** 3
+    res, clks = {}, {}
+    # Hessian components: six separable passes of r = 6 (13 taps per axis,
+    # 3 x 13 FMAs per voxel each), 2 B in and 4 B out per component
+    outs = [torch.empty((n, n, n), dtype=torch.float32, device="cuda") for _ in range(6)]
+    ms, clks["hessian"] = _timed(lambda: hp.hessian3d(x, 2.0, outs=outs), args.steps, max(3, args.warmup), stream)
+    fma = 6 * 3 * 13
+    tflops = 2 * fma * nvox / (ms / 1e3) / 1e12
+    res["hessian_components_s2"] = {"ms": ms, "fma_per_voxel": fma, "TFLOP/s": tflops,
+                                    "alu_frac": tflops / fma_derived,
+                                    "alu_frac_of_measured": tflops / fma_measured,
+                                    "GB/s": nvox * 36 / (ms / 1e3) / 1e9}
+    del outs
+    # eigenvalues: the six components into library scratch, then the
+    # closed-form 3 x 3 symmetric eigenvalues (24 B in, 12 B out per voxel)
+    eig = [torch.empty((n, n, n), dtype=torch.float32, device="cuda") for _ in range(3)]
+    ms, _ = _timed(lambda: hp.hessian3d(x, 2.0, eigenvalues=True, outs=eig), args.steps,
+                   max(3, args.warmup), stream)
+    res["hessian_eigenvalues_s2"] = {"ms": ms, "voxels_per_s": nvox / (ms / 1e3),
+                                     "note": "components (6 x 39 FMA/voxel) + eigenvalue epilogue"}
+    del eig
+    # box-window thresholds, three passes through scratch: x (2 B in, 12 B
+    # out: the window sum as u32 and the sum of squares as u64), y (12 in,
+    # 12 out), z fused with the decision (12 + 2 in, 1 out): 53 B/voxel
+    u = torch.empty((n, n, n), dtype=torch.uint8, device="cuda")
+    for method, k, c in (("mean", 0.0, 0.0), ("niblack", -0.2, 0.0), ("sauvola", 0.34, 32768.0)):
+        ms, clks[method] = _timed(lambda: hp.threshold_box3d(x, method, 7, k, c, out=u), args.steps,
+                                  max(3, args.warmup), stream)
+        gbs = nvox * 53 / (ms / 1e3) / 1e9
+        res[f"threshold_box_{method}_r7"] = {"ms": ms, "voxels_per_s": nvox / (ms / 1e3),
+                                             "GB/s": gbs, "hbm_frac": gbs / hbm_gbs}
+    hp.stream_status(stream)
+    h = res["hessian_components_s2"]
+    line = {"metric": "voxels/s, 1024^3 uint16 Hessian components (sigma 2)", "value": nvox / (h["ms"] / 1e3),
+            "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": h["ms"],
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic porous tomogram (seeded)",
+            "config": {"workload": "porous 1024^3 u16: Hessian components and eigenvalues (sigma 2); "
+                                   "box-window mean / Niblack / Sauvola thresholds (radius 7)"},
+            "ops": res, "hbm_peak_kind": peak_kind,
+            "fma_peak_tflops": {"derived": fma_derived, "measured": fma_measured},
+            "gpu_launches": 6 * args.steps, "clocks": clks["hessian"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def spheres128_measure(hp, torch, synth, steps: int, warmup: int):
     """128^3 float32 spheres: Gaussian sigma 2 -> threshold 0.5 to uint8 ->
     erosion and dilation with the 3^3 cube (the unchunked pipeline): ms per
@@ -800,7 +862,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="porous1024",
                     choices=["porous1024", "ooc2048", "spheres128", "bank512", "autograd256",
-                             "open1024", "sweep"])
+                             "open1024", "features1024", "sweep"])
     ap.add_argument("--size", type=int, default=N,
                     help="edge of the in-HBM volume (1024 is the benchmark; smaller sizes "
                          "are for profiling captures)")
@@ -815,6 +877,8 @@ def main():
         return run_autograd256(args)
     if args.workload == "open1024":
         return run_open1024(args)
+    if args.workload == "features1024":
+        return run_features1024(args)
     if args.workload == "sweep":
         return run_sweep(args)
     if args.impl == "reference":

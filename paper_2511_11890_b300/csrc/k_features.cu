@@ -11,13 +11,16 @@
 //
 // Box statistics: the window sums S1 = sum f and S2 = sum f^2 over the
 // (2w+1)^3 cube with reflect boundaries are formed separably, x then y then
-// z, each 1D window summed in increasing source coordinate. Integer inputs
-// (u8, u16) sum in 32/64-bit integers (exact); floating-point inputs in FP64
-// with explicitly rounded operations. The decision epilogue evaluates
+// z. Integer inputs (u8, u16) sum in 32/64-bit integers, exactly, as running
+// sums along each line; floating-point inputs sum each 1D window in
+// increasing source coordinate in FP64 with explicitly rounded operations.
+// The decision epilogue evaluates
 //   m = S1/N, v = max(S2/N - m*m, 0), s = sqrt(v),
 //   T = m - c (mean) | m + k s (Niblack) | m (1 + k (s/c - 1)) (Sauvola)
 // in FP64, one IEEE-rounded operation at a time (no contraction), and
-// writes f > T.
+// writes f > T; for integer inputs an FP32 evaluation with a proven error
+// margin settles every voxel whose f is clear of T, and the FP64 sequence
+// the rest.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -87,40 +90,15 @@ __global__ void k_hessian_eig(const float* __restrict__ comps, int64_t n, void* 
 
 // ----------------------------------------------------------- box statistics
 
-// Integer sums: S1 in int32, S2 in int64 (exact: u16 values, windows of at
-// most 31^3 voxels).
-struct ISum {
-  int32_t* s1;
-  int64_t* s2;
-};
 // Floating-point sums: FP64.
 struct FSum {
   double* s1;
   double* s2;
 };
 
-// x pass over the region [off, off + n) of the global volume: window sums
-// along x of the input (a dense box at in_lo with in_dims).
-template <typename TIN>
-__global__ void k_box_x_int(const TIN* __restrict__ in, DevBox B, ISum dst, int64_t n0, int64_t n1,
-                            int64_t n2, int64_t off0, int64_t off1, int64_t off2, int64_t Gx, int w) {
-  const int64_t total = n0 * n1 * n2;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
-    const int64_t row = ((off0 + z - B.lo[0]) * B.dims[1] + (off1 + y - B.lo[1])) * B.dims[2];
-    int32_t t1 = 0;
-    int64_t t2 = 0;
-    for (int k = -w; k <= w; ++k) {
-      const int32_t v = (int32_t)in[row + reflect(off2 + x + k, Gx) - B.lo[2]];
-      t1 += v;
-      t2 += (int64_t)(v * (uint32_t)v);
-    }
-    dst.s1[q] = t1;
-    dst.s2[q] = t2;
-  }
-}
-
+// Floating-point inputs: direct window sums in FP64, each 1D window summed in
+// increasing source coordinate with explicitly rounded additions. x pass over
+// the region [off, off + n) of the global volume (input: a dense box).
 template <typename TIN>
 __global__ void k_box_x_fp(const TIN* __restrict__ in, DevBox B, FSum dst, int64_t n0, int64_t n1,
                            int64_t n2, int64_t off0, int64_t off1, int64_t off2, int64_t Gx, int w) {
@@ -216,6 +194,203 @@ __global__ void k_box_z_decide(const S1* __restrict__ b1, const S2* __restrict__
   }
 }
 
+// Integer inputs (u8, u16): window sums are exact integers, so each line
+// forms them as a running sum (S(j) = S(j-1) + entering - leaving sample),
+// one thread per line, O(1) per output; the result is the same sum in any
+// order. The x pass takes rows (one thread each); the y and z passes take
+// lines of consecutive x, so their loads and stores are coalesced.
+template <typename TIN>
+__global__ void k_boxi_x(const TIN* __restrict__ in, DevBox B, int32_t* __restrict__ s1,
+                         int64_t* __restrict__ s2, Reg R, int64_t Gx, int w) {
+  const int64_t nrows = R.dims[0] * R.dims[1];
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nrows) return;
+  const int64_t z = R.lo[0] + l / R.dims[1], y = R.lo[1] + l % R.dims[1];
+  const TIN* row = in + ((z - B.lo[0]) * B.dims[1] + (y - B.lo[1])) * B.dims[2] - B.lo[2];
+  const int n = (int)R.dims[2];
+  const int64_t x0 = R.lo[2] - w;  // global x of sample 0
+  const bool inner = x0 >= 0 && x0 + n + 2 * w <= Gx;
+  auto ld = [&](int i) -> int32_t { return (int32_t)row[inner ? x0 + i : reflect(x0 + i, Gx)]; };
+  int32_t a = 0;
+  int64_t b = 0;
+  for (int i = 0; i <= 2 * w; ++i) {
+    const int32_t v = ld(i);
+    a += v;
+    b += (int64_t)v * v;
+  }
+  int32_t* o1 = s1 + l * n;
+  int64_t* o2 = s2 + l * n;
+  // lanes walk different rows: each writes whole 32-byte sectors (8 outputs
+  // as two 16-byte S1 stores and four 16-byte S2 stores), so that no sector
+  // reaches DRAM partly written (rows of n % 8 == 0 outputs; others store
+  // one output at a time)
+  int j = 0;
+  if (n % 8 == 0) {
+    for (; j < n; j += 8) {
+      int32_t v1[8];
+      int64_t v2[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (j + u > 0) {
+          const int32_t vi = ld(j + u + 2 * w), vo = ld(j + u - 1);
+          a += vi - vo;
+          b += (int64_t)vi * vi - (int64_t)vo * vo;
+        }
+        v1[u] = a;
+        v2[u] = b;
+      }
+      reinterpret_cast<int4*>(o1 + j)[0] = make_int4(v1[0], v1[1], v1[2], v1[3]);
+      reinterpret_cast<int4*>(o1 + j)[1] = make_int4(v1[4], v1[5], v1[6], v1[7]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        reinterpret_cast<longlong2*>(o2 + j)[u] = make_longlong2(v2[2 * u], v2[2 * u + 1]);
+    }
+    return;
+  }
+  o1[0] = a;
+  o2[0] = b;
+#pragma unroll 4
+  for (j = 1; j < n; ++j) {
+    const int32_t vi = ld(j + 2 * w), vo = ld(j - 1);
+    a += vi - vo;
+    b += (int64_t)vi * vi - (int64_t)vo * vo;
+    o1[j] = a;
+    o2[j] = b;
+  }
+}
+
+// y (AXIS 1) or z (AXIS 0) running sums of the source region S into the
+// region D (lines of D enumerate its other two axes, x fastest); with
+// DECIDE (z pass) the sums feed the threshold decision of the output box.
+struct BoxDecide {
+  const void* in;  // the job's input, element type of the kernel
+  DevBox B;
+  DevOut O;
+  int method;
+  double k, c;
+};
+
+// Exact decision f > T, T from the FP64 sequence of the oracle (one IEEE
+// rounding per operation). Out of line: the integer path reaches it only for
+// voxels next to their threshold.
+__device__ __noinline__ bool decide_fp64(double s1, double s2, double nw, double f, int method,
+                                            double k, double c) {
+  const double m = __ddiv_rn(s1, nw);
+  double v = __dsub_rn(__ddiv_rn(s2, nw), __dmul_rn(m, m));
+  if (v < 0.0) v = 0.0;
+  const double sd = __dsqrt_rn(v);
+  double t;
+  if (method == HP_LOCAL_MEAN) t = __dsub_rn(m, c);
+  else if (method == HP_LOCAL_NIBLACK) t = __dadd_rn(m, __dmul_rn(k, sd));
+  else t = __dmul_rn(m, __dadd_rn(1.0, __dmul_rn(k, __dsub_rn(__ddiv_rn(sd, c), 1.0))));
+  return f > t;
+}
+
+// The same decision from exact integer sums, settled in FP32 where the
+// threshold is clear of f and in FP64 (decide_fp64) otherwise. With
+// u = 2^-24, the FP32 threshold t32 takes at most 14 roundings over terms of
+// size at most |m| + |c| + |k| (sd + |m|)(1 + r), r = |m|/c for Sauvola and
+// 0 otherwise: m = S1 * (1/N) three, sd = sqrt(N S2 - S1^2) * (1/N) (the
+// numerator exact in int64, converted in two halves) five relative to sd,
+// k, c and 1/c one each, the formulas at most five; 14 u < 8.4e-7. The
+// oracle's FP64 threshold differs from the exact t through its cancellation
+// in S2/N - m^2: at most 4 ulp of S2/N <= top^2 (top: the dtype's largest
+// value), so its sd moves by at most 2.2e-8 top, reaching t times
+// |k| (1 + r). E takes 1.2e-6 for the first, twice the second and 1e-6;
+// where |f - t32| > E, f > t32 and f > T agree.
+struct DecideConst {
+  float inv_nw, kf, cf, inv_c, top;
+};
+
+__device__ __forceinline__ bool decide_int(int32_t S1, int64_t S2, int nwi, int32_t f, int method,
+                                           double k, double c, const DecideConst& Q) {
+  const int64_t vn = (int64_t)nwi * S2 - (int64_t)S1 * S1;  // exact, >= 0
+  const float m = (float)S1 * Q.inv_nw;
+  const int64_t v0 = max(vn, (int64_t)0);
+  const float vnf = fmaf((float)(int32_t)(v0 >> 31), 2147483648.0f, (float)(int32_t)(v0 & 0x7FFFFFFF));
+  const float sd = sqrtf(vnf) * Q.inv_nw;
+  float t, r = 0.0f;
+  if (method == HP_LOCAL_MEAN) {
+    t = m - Q.cf;
+  } else if (method == HP_LOCAL_NIBLACK) {
+    t = fmaf(Q.kf, sd, m);
+  } else {
+    r = fabsf(m) * Q.inv_c;
+    t = m * (1.0f + Q.kf * fmaf(sd, Q.inv_c, -1.0f));
+  }
+  const float ak = fabsf(Q.kf) * (1.0f + r);
+  const float E = 1.2e-6f * (fabsf(m) + fabsf(Q.cf) + ak * (sd + fabsf(m))) + 4.5e-8f * ak * Q.top + 1e-6f;
+  const float d = (float)f - t;
+  if (d > E) return true;
+  if (d < -E) return false;
+  return decide_fp64((double)S1, (double)S2, (double)nwi, (double)f, method, k, c);
+}
+
+template <int AXIS, bool DECIDE, typename TIN>
+__global__ void k_boxi_line(const int32_t* __restrict__ a1, const int64_t* __restrict__ a2, Reg S,
+                            int32_t* __restrict__ b1, int64_t* __restrict__ b2, Reg D, int64_t Gn,
+                            int w, BoxDecide P) {
+  constexpr int a1x = AXIS == 0 ? 1 : 0;  // the other axes: a1x slow, x fast
+  const int64_t nlines = D.dims[a1x] * D.dims[2];
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nlines) return;
+  int64_t c3[3];
+  c3[2] = D.lo[2] + l % D.dims[2];
+  c3[a1x] = D.lo[a1x] + l / D.dims[2];
+  c3[AXIS] = S.lo[AXIS];
+  const int64_t sstr = AXIS == 1 ? S.dims[2] : S.dims[1] * S.dims[2];
+  const int64_t sb = ((c3[0] - S.lo[0]) * S.dims[1] + (c3[1] - S.lo[1])) * S.dims[2] + (c3[2] - S.lo[2]) -
+                     S.lo[AXIS] * sstr;
+  const int n = (int)D.dims[AXIS];
+  const int64_t p0 = D.lo[AXIS] - w;  // global coordinate of sample 0
+  const bool inner = p0 >= 0 && p0 + n + 2 * w <= Gn;
+  auto at = [&](int i) -> int64_t { return sb + (inner ? p0 + i : reflect(p0 + i, Gn)) * sstr; };
+  int32_t a = 0;
+  int64_t b = 0;
+  for (int i = 0; i <= 2 * w; ++i) {
+    const int64_t q = at(i);
+    a += a1[q];
+    b += a2[q];
+  }
+  // output j of this line (global coordinate D.lo[AXIS] + j)
+  const int nwi = (2 * w + 1) * (2 * w + 1) * (2 * w + 1);
+  DecideConst Q;
+  Q.inv_nw = 1.0f / (float)nwi;
+  Q.kf = (float)P.k;
+  Q.cf = (float)P.c;
+  Q.inv_c = P.method == HP_LOCAL_SAUVOLA ? 1.0f / Q.cf : 0.0f;
+  Q.top = sizeof(TIN) == 1 ? 255.0f : 65535.0f;
+  int64_t ob = 0, ib = 0, dstr = 0, istr = 0;
+  if constexpr (DECIDE) {
+    c3[AXIS] = D.lo[AXIS];
+    ob = ((c3[0] - P.O.lo[0]) * P.O.dims[1] + (c3[1] - P.O.lo[1])) * P.O.dims[2] + (c3[2] - P.O.lo[2]);
+    ib = ((c3[0] - P.B.lo[0]) * P.B.dims[1] + (c3[1] - P.B.lo[1])) * P.B.dims[2] + (c3[2] - P.B.lo[2]);
+    dstr = AXIS == 1 ? P.O.dims[2] : P.O.dims[1] * P.O.dims[2];
+    istr = AXIS == 1 ? P.B.dims[2] : P.B.dims[1] * P.B.dims[2];
+  } else {
+    c3[AXIS] = D.lo[AXIS];
+    ob = ((c3[0] - D.lo[0]) * D.dims[1] + (c3[1] - D.lo[1])) * D.dims[2] + (c3[2] - D.lo[2]);
+    dstr = AXIS == 1 ? D.dims[2] : D.dims[1] * D.dims[2];
+  }
+  auto emit = [&](int j) {
+    if constexpr (DECIDE) {
+      const int32_t f = (int32_t) static_cast<const TIN*>(P.in)[ib + j * istr];
+      static_cast<uint8_t*>(P.O.ptr)[ob + j * dstr] = decide_int(a, b, nwi, f, P.method, P.k, P.c, Q) ? 1 : 0;
+    } else {
+      b1[ob + j * dstr] = a;
+      b2[ob + j * dstr] = b;
+    }
+  };
+  emit(0);
+#pragma unroll 4
+  for (int j = 1; j < n; ++j) {
+    const int64_t qi = at(j + 2 * w), qo = at(j - 1);
+    a += a1[qi] - a1[qo];
+    b += a2[qi] - a2[qo];
+    emit(j);
+  }
+}
+
 unsigned grid_for(int64_t t) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((t + kBlk - 1) / kBlk, (int64_t)num_sms() * 32));
 }
@@ -237,20 +412,29 @@ cudaError_t box_launch(const Job& job, int method, int w, double k, double c, cu
   const TIN* in = static_cast<const TIN*>(job.in.ptr);
   const Reg rx{{g.rlo[0], g.rlo[1], job.core_lo[2]}, {g.n_x[0], g.n_x[1], g.n_x[2]}};
   const Reg ry{{g.rlo[0], job.core_lo[1], job.core_lo[2]}, {g.n_y[0], g.n_y[1], g.n_y[2]}};
-  if constexpr (FP)
+  if constexpr (!FP) {
+    // integer inputs: running sums along lines (k_boxi_*)
+    const Reg core{{job.core_lo[0], job.core_lo[1], job.core_lo[2]}, {cz, cy, cx}};
+    const BoxDecide P{job.in.ptr, job.in, job.out, method, k, c};
+    const int64_t rows = g.n_x[0] * g.n_x[1];
+    k_boxi_x<TIN><<<(unsigned)((rows + kBlk - 1) / kBlk), kBlk, 0, s>>>(in, job.in, a1, a2, rx, job.gdims[2], w);
+    const int64_t ly = g.n_y[0] * g.n_y[2];
+    k_boxi_line<1, false, TIN><<<(unsigned)((ly + kBlk - 1) / kBlk), kBlk, 0, s>>>(
+        a1, a2, rx, b1, b2, ry, job.gdims[1], w, P);
+    const int64_t lz = cy * cx;
+    k_boxi_line<0, true, TIN><<<(unsigned)((lz + kBlk - 1) / kBlk), kBlk, 0, s>>>(
+        b1, b2, ry, nullptr, nullptr, core, job.gdims[0], w, P);
+  } else {
     k_box_x_fp<TIN><<<grid_for(vx), kBlk, 0, s>>>(in, job.in, FSum{a1, a2}, g.n_x[0], g.n_x[1],
                                                   g.n_x[2], g.rlo[0], g.rlo[1], job.core_lo[2],
                                                   job.gdims[2], w);
-  else
-    k_box_x_int<TIN><<<grid_for(vx), kBlk, 0, s>>>(in, job.in, ISum{a1, a2}, g.n_x[0], g.n_x[1],
-                                                   g.n_x[2], g.rlo[0], g.rlo[1], job.core_lo[2],
-                                                   job.gdims[2], w);
-  k_box_y<S1, S2, FP><<<grid_for(vy), kBlk, 0, s>>>(a1, a2, rx, b1, b2, g.n_y[0], g.n_y[1], g.n_y[2],
-                                                    g.rlo[0], job.core_lo[1], job.core_lo[2],
-                                                    job.gdims[1], w);
-  k_box_z_decide<TIN, S1, S2, FP><<<grid_for(cz * cy * cx), kBlk, 0, s>>>(
-      b1, b2, ry, in, job.in, job.out, cz, cy, cx, job.core_lo[0], job.core_lo[1], job.core_lo[2],
-      job.gdims[0], w, method, k, c);
+    k_box_y<S1, S2, FP><<<grid_for(vy), kBlk, 0, s>>>(a1, a2, rx, b1, b2, g.n_y[0], g.n_y[1], g.n_y[2],
+                                                      g.rlo[0], job.core_lo[1], job.core_lo[2],
+                                                      job.gdims[1], w);
+    k_box_z_decide<TIN, S1, S2, FP><<<grid_for(cz * cy * cx), kBlk, 0, s>>>(
+        b1, b2, ry, in, job.in, job.out, cz, cy, cx, job.core_lo[0], job.core_lo[1], job.core_lo[2],
+        job.gdims[0], w, method, k, c);
+  }
   return cudaGetLastError();
 }
 

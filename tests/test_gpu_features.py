@@ -120,3 +120,33 @@ def test_box_threshold_radius_zero_and_hessian_small_sigma_f16():
         got = [to_np(t) for t in hp.hessian3d(to_dev(g), sigma, out_dtype=hp.HP_F16)]
         for a, r in zip(got, oracle.hessian3d(g, sigma)):
             assert_filter_close(a, r, f"Hessian f16 sigma {sigma}")
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_box_threshold_near_ties_and_integer_extremes(dtype):
+    """Integer inputs decide in FP32 where f is clear of the threshold and in
+    FP64 (the oracle's sequence) otherwise. Piecewise-constant 4^3 blocks with
+    sparse +-1 perturbations put many voxels at or next to the threshold
+    (windows of zero or tiny variance, f equal to the mean); an all-maximum
+    volume at radius 15 takes the window sums to their largest values
+    (S1 = 29791 x 65535 < 2^31; the variance numerator N S2 - S1^2 in int64)."""
+    rng = np.random.default_rng(90)
+    top = np.iinfo(dtype).max
+    blocks = rng.integers(1, top - 1, size=(4, 6, 9))
+    f = np.kron(blocks, np.ones((4, 4, 4), np.int64))[:15, :22, :33]
+    bump = rng.random(f.shape)
+    f = (f + (bump < 0.05) - (bump > 0.95)).astype(dtype)
+    x = to_dev(f)
+    cases = [("mean", 0.0, 0.0), ("mean", 0.0, 1.0), ("niblack", 0.0, 0.0), ("niblack", 0.5, 0.0),
+             ("niblack", -1.0, 0.0), ("sauvola", 0.0, 128.0), ("sauvola", 0.25, float(top) / 2)]
+    for w in (1, 2):
+        for method, k, c in cases:
+            got = to_np(hp.threshold_box3d(x, method, w, k, c))
+            ref = oracle.threshold_box(f, MCODE[method], w, k, c)
+            assert np.array_equal(got, ref), (w, method, k, c)
+    g = np.full((5, 7, 9), top, dtype)
+    g[2, 3, 4] = top - 1
+    xg = to_dev(g)
+    for method, k, c in [("mean", 0.0, 0.0), ("niblack", 0.3, 0.0), ("sauvola", 0.3, float(top))]:
+        got = to_np(hp.threshold_box3d(xg, method, 15, k, c))
+        assert np.array_equal(got, oracle.threshold_box(g, MCODE[method], 15, k, c)), method

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "hp_device.cuh"
 #include "hp_internal.h"
@@ -220,17 +221,18 @@ __global__ void k_boxi_x(const TIN* __restrict__ in, DevBox B, int32_t* __restri
   }
   int32_t* o1 = s1 + l * n;
   int64_t* o2 = s2 + l * n;
-  // lanes walk different rows: each writes whole 32-byte sectors (8 outputs
-  // as two 16-byte S1 stores and four 16-byte S2 stores), so that no sector
-  // reaches DRAM partly written (rows of n % 8 == 0 outputs; others store
-  // one output at a time)
+  // lanes walk different rows: each writes whole 32-byte sectors (chunks of
+  // 16 or 8 outputs as 16-byte S1 and S2 stores), so that no sector reaches
+  // DRAM partly written; the 2 x 16 loads of a 16-output chunk are in flight
+  // together (rows of n % 8 != 0 outputs store one output at a time)
   int j = 0;
-  if (n % 8 == 0) {
-    for (; j < n; j += 8) {
-      int32_t v1[8];
-      int64_t v2[8];
+  auto run = [&](auto CH) {
+    constexpr int C = decltype(CH)::value;  // outputs per chunk: C/8 whole sectors of S1
+    for (; j < n; j += C) {
+      int32_t v1[C];
+      int64_t v2[C];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < C; ++u) {
         if (j + u > 0) {
           const int32_t vi = ld(j + u + 2 * w), vo = ld(j + u - 1);
           a += vi - vo;
@@ -239,12 +241,20 @@ __global__ void k_boxi_x(const TIN* __restrict__ in, DevBox B, int32_t* __restri
         v1[u] = a;
         v2[u] = b;
       }
-      reinterpret_cast<int4*>(o1 + j)[0] = make_int4(v1[0], v1[1], v1[2], v1[3]);
-      reinterpret_cast<int4*>(o1 + j)[1] = make_int4(v1[4], v1[5], v1[6], v1[7]);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < C / 4; ++u)
+        reinterpret_cast<int4*>(o1 + j)[u] = make_int4(v1[4 * u], v1[4 * u + 1], v1[4 * u + 2], v1[4 * u + 3]);
+#pragma unroll
+      for (int u = 0; u < C / 2; ++u)
         reinterpret_cast<longlong2*>(o2 + j)[u] = make_longlong2(v2[2 * u], v2[2 * u + 1]);
     }
+  };
+  if (n % 16 == 0) {
+    run(std::integral_constant<int, 16>());
+    return;
+  }
+  if (n % 8 == 0) {
+    run(std::integral_constant<int, 8>());
     return;
   }
   o1[0] = a;

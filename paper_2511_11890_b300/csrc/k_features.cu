@@ -76,16 +76,31 @@ __device__ __forceinline__ void sym3_eig(float a, float b, float c, float d, flo
 
 // comps: six dense FP32 volumes of n voxels (Dzz, Dyy, Dxx, Dzy, Dzx, Dyx),
 // one after another; outs: three volumes of out_dtype.
+// A thread takes kEigU voxels a grid stride apart per round and issues
+// their 6 x kEigU loads before solving any of them.
+constexpr int kEigU = 4;
+
 __global__ void k_hessian_eig(const float* __restrict__ comps, int64_t n, void* o1, void* o2,
                               void* o3, int dt) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float l1, l2, l3;
-    sym3_eig(comps[i], comps[n + i], comps[2 * n + i], comps[3 * n + i], comps[4 * n + i],
-             comps[5 * n + i], l1, l2, l3);
-    store_f(o1, dt, i, l1);
-    store_f(o2, dt, i, l2);
-    store_f(o3, dt, i, l3);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += kEigU * stride) {
+    float h[kEigU][6];
+#pragma unroll
+    for (int u = 0; u < kEigU; ++u) {
+      const int64_t i = i0 + u * stride;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) h[u][c] = i < n ? comps[c * n + i] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kEigU; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i >= n) break;
+      float l1, l2, l3;
+      sym3_eig(h[u][0], h[u][1], h[u][2], h[u][3], h[u][4], h[u][5], l1, l2, l3);
+      store_f(o1, dt, i, l1);
+      store_f(o2, dt, i, l2);
+      store_f(o3, dt, i, l3);
+    }
   }
 }
 

@@ -215,9 +215,24 @@ __global__ void k_box_z_decide(const S1* __restrict__ b1, const S2* __restrict__
 // one thread per line, O(1) per output; the result is the same sum in any
 // order. The x pass takes rows (one thread each); the y and z passes take
 // lines of consecutive x, so their loads and stores are coalesced.
+// Eight 16-bit samples starting at sample p (0..7) of the 16 held by the
+// 16-byte words A, B, as four 32-bit words (two samples each).
+__device__ __forceinline__ void take8(const uint4& A, const uint4& B, int p, uint32_t (&o)[4]) {
+  const uint32_t w[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
+  switch (p) {
+#define HP_T8(P)                                                                          \
+  case P:                                                                                 \
+    _Pragma("unroll") for (int m = 0; m < 4; ++m) o[m] =                                  \
+        (P % 2 == 0) ? w[m + P / 2] : __byte_perm(w[m + P / 2], w[m + P / 2 + 1], 0x5432); \
+    break;
+    HP_T8(0) HP_T8(1) HP_T8(2) HP_T8(3) HP_T8(4) HP_T8(5) HP_T8(6) HP_T8(7)
+#undef HP_T8
+  }
+}
+
 template <typename TIN>
 __global__ void k_boxi_x(const TIN* __restrict__ in, DevBox B, int32_t* __restrict__ s1,
-                         int64_t* __restrict__ s2, Reg R, int64_t Gx, int w) {
+                         int64_t* __restrict__ s2, Reg R, int64_t Gx, int w, int vec) {
   const int64_t nrows = R.dims[0] * R.dims[1];
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (l >= nrows) return;
@@ -264,6 +279,56 @@ __global__ void k_boxi_x(const TIN* __restrict__ in, DevBox B, int32_t* __restri
         reinterpret_cast<longlong2*>(o2 + j)[u] = make_longlong2(v2[2 * u], v2[2 * u + 1]);
     }
   };
+  // 16-bit rows that start on 16-byte boundaries (vec, uniform): a chunk of
+  // 8 outputs whose entering samples j + 2w + u and leaving samples j - 1 + u
+  // all lie inside the volume reads them as two aligned 16-byte words per
+  // stream (4 loads per lane and 8 outputs instead of 16 element loads); the
+  // windows start at the same sample phase in every row. Chunks at the
+  // volume faces take element loads with reflection.
+  if (sizeof(TIN) == 2 && vec && n % 8 == 0) {
+    const uint16_t* r16 = reinterpret_cast<const uint16_t*>(row);
+    for (j = 0; j < n; j += 8) {
+      const int64_t e0 = x0 + j + 2 * w, l0 = x0 + j - 1;  // first entering / leaving sample (global x)
+      int32_t vi8[8], vo8[8];
+      if (j > 0 && l0 >= 0 && e0 + 7 <= Gx - 1) {
+        const int64_t fe = e0 & ~(int64_t)7, fl = l0 & ~(int64_t)7;
+        const int pe = (int)(e0 - fe), pl = (int)(l0 - fl);
+        const uint4 E0 = *reinterpret_cast<const uint4*>(r16 + fe);
+        const uint4 E1 = pe ? *reinterpret_cast<const uint4*>(r16 + fe + 8) : E0;
+        const uint4 L0 = *reinterpret_cast<const uint4*>(r16 + fl);
+        const uint4 L1 = pl ? *reinterpret_cast<const uint4*>(r16 + fl + 8) : L0;
+        uint32_t ev[4], lv[4];
+        take8(E0, E1, pe, ev);
+        take8(L0, L1, pl, lv);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          vi8[u] = (int32_t)((ev[u >> 1] >> (16 * (u & 1))) & 0xFFFFu);
+          vo8[u] = (int32_t)((lv[u >> 1] >> (16 * (u & 1))) & 0xFFFFu);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          vi8[u] = j + u > 0 ? ld(j + u + 2 * w) : 0;
+          vo8[u] = j + u > 0 ? ld(j + u - 1) : 0;
+        }
+      }
+      int32_t v1[8];
+      int64_t v2[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a += vi8[u] - vo8[u];
+        b += (int64_t)vi8[u] * vi8[u] - (int64_t)vo8[u] * vo8[u];
+        v1[u] = a;
+        v2[u] = b;
+      }
+      reinterpret_cast<int4*>(o1 + j)[0] = make_int4(v1[0], v1[1], v1[2], v1[3]);
+      reinterpret_cast<int4*>(o1 + j)[1] = make_int4(v1[4], v1[5], v1[6], v1[7]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        reinterpret_cast<longlong2*>(o2 + j)[u] = make_longlong2(v2[2 * u], v2[2 * u + 1]);
+    }
+    return;
+  }
   if (n % 16 == 0) {
     run(std::integral_constant<int, 16>());
     return;
@@ -442,7 +507,12 @@ cudaError_t box_launch(const Job& job, int method, int w, double k, double c, cu
     const Reg core{{job.core_lo[0], job.core_lo[1], job.core_lo[2]}, {cz, cy, cx}};
     const BoxDecide P{job.in.ptr, job.in, job.out, method, k, c};
     const int64_t rows = g.n_x[0] * g.n_x[1];
-    k_boxi_x<TIN><<<(unsigned)((rows + kBlk - 1) / kBlk), kBlk, 0, s>>>(in, job.in, a1, a2, rx, job.gdims[2], w);
+    // rows on 16-byte boundaries: every row of the input box is a whole number
+    // of 16-byte words from an aligned base
+    const int vec = (reinterpret_cast<uintptr_t>(in) % 16 == 0 &&
+                     (job.in.dims[2] * (int64_t)sizeof(TIN)) % 16 == 0 && (job.in.lo[2] % 8) == 0);
+    k_boxi_x<TIN><<<(unsigned)((rows + kBlk - 1) / kBlk), kBlk, 0, s>>>(in, job.in, a1, a2, rx,
+                                                                       job.gdims[2], w, vec);
     const int64_t ly = g.n_y[0] * g.n_y[2];
     k_boxi_line<1, false, TIN><<<(unsigned)((ly + kBlk - 1) / kBlk), kBlk, 0, s>>>(
         a1, a2, rx, b1, b2, ry, job.gdims[1], w, P);

@@ -132,18 +132,21 @@ def test_box_threshold_near_ties_and_integer_extremes(dtype):
     (S1 = 29791 x 65535 < 2^31; the variance numerator N S2 - S1^2 in int64)."""
     rng = np.random.default_rng(90)
     top = np.iinfo(dtype).max
-    blocks = rng.integers(1, top - 1, size=(4, 6, 9))
-    f = np.kron(blocks, np.ones((4, 4, 4), np.int64))[:15, :22, :33]
-    bump = rng.random(f.shape)
-    f = (f + (bump < 0.05) - (bump > 0.95)).astype(dtype)
-    x = to_dev(f)
     cases = [("mean", 0.0, 0.0), ("mean", 0.0, 1.0), ("niblack", 0.0, 0.0), ("niblack", 0.5, 0.0),
              ("niblack", -1.0, 0.0), ("sauvola", 0.0, 128.0), ("sauvola", 0.25, float(top) / 2)]
-    for w in (1, 2):
-        for method, k, c in cases:
-            got = to_np(hp.threshold_box3d(x, method, w, k, c))
-            ref = oracle.threshold_box(f, MCODE[method], w, k, c)
-            assert np.array_equal(got, ref), (w, method, k, c)
+    # 33 columns: element loads along x; 64 columns (whole 16-byte words per
+    # row): 16-byte loads for uint16
+    for shape in [(15, 22, 33), (12, 20, 64)]:
+        blocks = rng.integers(1, top - 1, size=(4, 6, 16))
+        f = np.kron(blocks, np.ones((4, 4, 4), np.int64))[:shape[0], :shape[1], :shape[2]]
+        bump = rng.random(f.shape)
+        f = (f + (bump < 0.05) - (bump > 0.95)).astype(dtype)
+        x = to_dev(f)
+        for w in (1, 2, 5):
+            for method, k, c in cases:
+                got = to_np(hp.threshold_box3d(x, method, w, k, c))
+                ref = oracle.threshold_box(f, MCODE[method], w, k, c)
+                assert np.array_equal(got, ref), (shape, w, method, k, c)
     g = np.full((5, 7, 9), top, dtype)
     g[2, 3, 4] = top - 1
     xg = to_dev(g)

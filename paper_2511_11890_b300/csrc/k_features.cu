@@ -472,7 +472,7 @@ __global__ void k_boxi_line(const int32_t* __restrict__ a1, const int64_t* __res
     }
   };
   emit(0);
-#pragma unroll 4
+#pragma unroll (DECIDE ? 1 : 4)
   for (int j = 1; j < n; ++j) {
     const int64_t qi = at(j + 2 * w), qo = at(j - 1);
     a += a1[qi] - a1[qo];

@@ -237,6 +237,26 @@ def cpu_oracle_sample(budget_s: float, seed_volume=None):
     return voxels / dt, f"{boxes} random {b}^3 output boxes (with halos) of the step, {dt:.1f} s"
 
 
+def cpu_ops_sample(ops, seconds_per_op: float = 3.0, n: int = 48):
+    """Time the oracle (single-threaded FP64 C) on each named op of a
+    workload, on an n^3 drawing of the same porous generator, for about
+    seconds_per_op each: {name: voxels/s} and the sample description."""
+    import oracle
+    import synth
+    f, _ = synth.porous((n, n, n), SEED)
+    res = {}
+    for name, fn in ops:
+        calls, t0 = 0, time.perf_counter()
+        while True:
+            fn(f)
+            calls += 1
+            dt = time.perf_counter() - t0
+            if dt >= seconds_per_op:
+                break
+        res[name] = calls * n ** 3 / dt
+    return res, f"the oracle on a {n}^3 drawing of the same porous generator, ~{seconds_per_op:.0f} s per op"
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -663,12 +683,21 @@ def run_open1024(args):
     res["threshold_local_s2"] = {"ms": ms, "GB/s": nvox * 13 / (ms / 1e3) / 1e9,
                                  "hbm_frac": nvox * 13 / (ms / 1e3) / 1e9 / hbm_gbs}
     hp.stream_status(stream)
+    import oracle
+    cpu, sample = cpu_ops_sample([
+        ("open", lambda v: oracle.open3d(v, oracle.SE_BALL, BALL_R)),
+        ("close", lambda v: oracle.close3d(v, oracle.SE_BALL, BALL_R)),
+        ("tophat", lambda v: oracle.tophat3d(v, oracle.SE_BALL, BALL_R)),
+        ("unsharp_s2", lambda v: oracle.unsharp3d(v, 2.0, 1.0)),
+        ("threshold_local_s2", lambda v: oracle.threshold_local(v, 2.0, 0.0))])
     line = {"metric": "voxels/s, 1024^3 uint16 opening (ball r = 3)", "value": nvox / (res["open"]["ms"] / 1e3),
             "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": res["open"]["ms"],
             "higher_is_better": True, "dtype": "u16", "data": "synthetic porous tomogram (seeded)",
             "config": {"workload": "porous 1024^3 u16: opening, closing, white top-hat, ball r = 3"},
             "ops": res, "hbm_peak_kind": peak_kind, "gpu_launches": 2 * args.steps,
-            "clocks": clks["open"]}
+            "clocks": clks["open"],
+            "cpu_baseline": {"value": cpu["open"], "unit": "voxels/s", "cores": 1, "kind": "oracle",
+                             "sample": sample, "ops": cpu}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -720,6 +749,13 @@ def run_features1024(args):
         res[f"threshold_box_{method}_r7"] = {"ms": ms, "voxels_per_s": nvox / (ms / 1e3),
                                              "GB/s": gbs, "hbm_frac": gbs / hbm_gbs}
     hp.stream_status(stream)
+    import oracle
+    cpu, sample = cpu_ops_sample([
+        ("hessian_components_s2", lambda v: oracle.hessian3d(v, 2.0)),
+        ("hessian_eigenvalues_s2", lambda v: oracle.hessian_eigenvalues(v, 2.0)),
+        ("threshold_box_mean_r7", lambda v: oracle.threshold_box(v, oracle.LOCAL_MEAN, 7, 0.0, 0.0)),
+        ("threshold_box_niblack_r7", lambda v: oracle.threshold_box(v, oracle.LOCAL_NIBLACK, 7, -0.2, 0.0)),
+        ("threshold_box_sauvola_r7", lambda v: oracle.threshold_box(v, oracle.LOCAL_SAUVOLA, 7, 0.34, 32768.0))])
     h = res["hessian_components_s2"]
     line = {"metric": "voxels/s, 1024^3 uint16 Hessian components (sigma 2)", "value": nvox / (h["ms"] / 1e3),
             "unit": "voxels/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": h["ms"],
@@ -728,7 +764,9 @@ def run_features1024(args):
                                    "box-window mean / Niblack / Sauvola thresholds (radius 7)"},
             "ops": res, "hbm_peak_kind": peak_kind,
             "fma_peak_tflops": {"derived": fma_derived, "measured": fma_measured},
-            "gpu_launches": 6 * args.steps, "clocks": clks["hessian"]}
+            "gpu_launches": 6 * args.steps, "clocks": clks["hessian"],
+            "cpu_baseline": {"value": cpu["hessian_components_s2"], "unit": "voxels/s", "cores": 1,
+                             "kind": "oracle", "sample": sample, "ops": cpu}}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -17,8 +17,8 @@ void bank_release_cache();
 cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3],
                                const Taps& taps, float* t1, float* t2, int accumulate,
                                cudaStream_t s);
-cudaError_t launch_gm_chain(const float* w, const float* dz, const float* dy, const float* dx,
-                            const float* da, float* v, int64_t total, cudaStream_t s);
+cudaError_t launch_gm_chain3(const float* w, float* dz, float* dy, float* dx, int64_t total,
+                             cudaStream_t s);
 cudaError_t launch_morph_arg(const void* in, int dt, const int64_t dims[3], int ball, int rad,
                              int is_dilate, int32_t* arg, cudaStream_t s);
 cudaError_t launch_morph_gather(const int32_t* arg, const float* gout, float* gin,
@@ -171,10 +171,10 @@ int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
     if (f[i].kind == HP_FILTER_GM)
       gscr = std::max(gscr, gauss_scratch_bytes(whole_job_of(in, gin->data, HP_F32),
                                                 radius_of(f[i].sigma, 3.0)));
-  int st = check_scratch_budget(vb * (any_gm ? 6 : 2) + gscr);
+  int st = check_scratch_budget(vb * (any_gm ? 5 : 2) + gscr);
   if (st != HP_OK) return st;
   Scratch sc(s);
-  float *t1 = nullptr, *t2 = nullptr, *dz = nullptr, *dy = nullptr, *dx = nullptr, *v = nullptr;
+  float *t1 = nullptr, *t2 = nullptr, *dz = nullptr, *dy = nullptr, *dx = nullptr;
   void* gs = nullptr;
   cudaError_t e = sc.alloc((void**)&t1, vb);
   if (e == cudaSuccess && gscr > 0) e = sc.alloc(&gs, gscr);
@@ -182,7 +182,6 @@ int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
   if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dz, vb);
   if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dy, vb);
   if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&dx, vb);
-  if (e == cudaSuccess && any_gm) e = sc.alloc((void**)&v, vb);
   if (e != cudaSuccess) return cuda_fail(e, "adjoint scratch");
   float* g = static_cast<float*>(gin->data);
   if ((e = cudaMemsetAsync(g, 0, vb, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -212,12 +211,13 @@ int hp_filterbank3d_adjoint(const hp_volume* in, const hp_volume* const* gouts,
         j.scratch_bytes = gscr;
         e = launch_gauss(j, taps, s);
       }
+      // the chain rule through GM for all three axes in one pass, in place
+      if (e == cudaSuccess) e = launch_gm_chain3(w, dz, dy, dx, total, s);
       for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         int ord[3] = {0, 0, 0};
         ord[a] = 1;
         make_taps(sigma, 3.0, ord, &taps);
-        e = launch_gm_chain(w, dz, dy, dx, D[a], v, total, s);
-        if (e == cudaSuccess) e = launch_sep_adjoint(v, g, dims, taps, t1, t2, 1, s);
+        e = launch_sep_adjoint(D[a], g, dims, taps, t1, t2, 1, s);
       }
     }
   }

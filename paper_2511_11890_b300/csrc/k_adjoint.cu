@@ -321,15 +321,19 @@ cudaError_t launch_axis_r(const float* src, float* dst, const int64_t dims[3], i
   return cudaGetLastError();
 }
 
-// v = w * D_a / GM (0 where GM = 0), GM = sqrt(Dx^2 + Dy^2 + Dz^2) formed
-// as in the forward bank.
-__global__ void k_gm_chain(const float* __restrict__ w, const float* __restrict__ dz,
-                           const float* __restrict__ dy, const float* __restrict__ dx,
-                           const float* __restrict__ da, float* __restrict__ v, int64_t total) {
+// Chain rule through the gradient magnitude, in place for the three axes:
+// D_a <- w * D_a / GM (0 where GM = 0), GM = sqrt(Dx^2 + Dy^2 + Dz^2) formed
+// as in the forward bank; each volume is read once.
+__global__ void k_gm_chain3(const float* __restrict__ w, float* __restrict__ dz,
+                            float* __restrict__ dy, float* __restrict__ dx, int64_t total) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
-    const float gm = sqrtf(fmaf(dz[q], dz[q], fmaf(dy[q], dy[q], dx[q] * dx[q])));
-    v[q] = gm > 0.0f ? w[q] * da[q] / gm : 0.0f;
+    const float z = dz[q], y = dy[q], x = dx[q], wq = w[q];
+    const float gm = sqrtf(fmaf(z, z, fmaf(y, y, x * x)));
+    const bool nz = gm > 0.0f;
+    dz[q] = nz ? wq * z / gm : 0.0f;
+    dy[q] = nz ? wq * y / gm : 0.0f;
+    dx[q] = nz ? wq * x / gm : 0.0f;
   }
 }
 
@@ -610,9 +614,9 @@ cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3]
   return cudaGetLastError();
 }
 
-cudaError_t launch_gm_chain(const float* w, const float* dz, const float* dy, const float* dx,
-                            const float* da, float* v, int64_t total, cudaStream_t s) {
-  k_gm_chain<<<grid_for(total), kBlock, 0, s>>>(w, dz, dy, dx, da, v, total);
+cudaError_t launch_gm_chain3(const float* w, float* dz, float* dy, float* dx, int64_t total,
+                             cudaStream_t s) {
+  k_gm_chain3<<<grid_for(total), kBlock, 0, s>>>(w, dz, dy, dx, total);
   return cudaGetLastError();
 }
 

@@ -144,69 +144,69 @@ __device__ __forceinline__ int64_t reg_index(const Reg& R, int64_t z, int64_t y,
   return ((z - R.lo[0]) * R.dims[1] + (y - R.lo[1])) * R.dims[2] + (x - R.lo[2]);
 }
 
-template <typename S1, typename S2, bool FP>
-__device__ __forceinline__ void axis_sum(const S1* s1, const S2* s2, const Reg& R, int axis,
-                                         int64_t c0, int64_t c1, int64_t c2, int64_t Gn, int w,
-                                         S1& t1, S2& t2) {
-  t1 = 0;
-  t2 = 0;
+// Exact decision f > T, T from the FP64 sequence of the oracle (one IEEE
+// rounding per operation). Out of line: the integer path reaches it only for
+// voxels next to their threshold.
+__device__ __noinline__ bool decide_fp64(double s1, double s2, double nw, double f, int method,
+                                            double k, double c) {
+  const double m = __ddiv_rn(s1, nw);
+  double v = __dsub_rn(__ddiv_rn(s2, nw), __dmul_rn(m, m));
+  if (v < 0.0) v = 0.0;
+  const double sd = __dsqrt_rn(v);
+  double t;
+  if (method == HP_LOCAL_MEAN) t = __dsub_rn(m, c);
+  else if (method == HP_LOCAL_NIBLACK) t = __dadd_rn(m, __dmul_rn(k, sd));
+  else t = __dmul_rn(m, __dadd_rn(1.0, __dmul_rn(k, __dsub_rn(__ddiv_rn(sd, c), 1.0))));
+  return f > t;
+}
+
+// Floating-point inputs: y (axis 1) or z (axis 0) window sums from a dense
+// source region, each window summed in increasing source coordinate.
+__device__ __forceinline__ void axis_sum_fp(const double* s1, const double* s2, const Reg& R,
+                                            int axis, int64_t c0, int64_t c1, int64_t c2,
+                                            int64_t Gn, int w, double& t1, double& t2) {
+  t1 = 0.0;
+  t2 = 0.0;
   for (int k = -w; k <= w; ++k) {
     int64_t c[3] = {c0, c1, c2};
     c[axis] = reflect(c[axis] + k, Gn);
     const int64_t i = reg_index(R, c[0], c[1], c[2]);
-    if constexpr (FP) {
-      t1 = (S1)__dadd_rn((double)t1, (double)s1[i]);
-      t2 = (S2)__dadd_rn((double)t2, (double)s2[i]);
-    } else {
-      t1 += s1[i];
-      t2 += s2[i];
-    }
+    t1 = __dadd_rn(t1, s1[i]);
+    t2 = __dadd_rn(t2, s2[i]);
   }
 }
 
-template <typename S1, typename S2, bool FP>
-__global__ void k_box_y(const S1* __restrict__ a1, const S2* __restrict__ a2, Reg src, S1* b1, S2* b2,
-                        int64_t n0, int64_t n1, int64_t n2, int64_t off0, int64_t off1, int64_t off2,
-                        int64_t Gy, int w) {
+__global__ void k_box_y_fp(const double* __restrict__ a1, const double* __restrict__ a2, Reg src,
+                           double* b1, double* b2, int64_t n0, int64_t n1, int64_t n2, int64_t off0,
+                           int64_t off1, int64_t off2, int64_t Gy, int w) {
   const int64_t total = n0 * n1 * n2;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = q % n2, y = (q / n2) % n1, z = q / (n1 * n2);
-    S1 t1;
-    S2 t2;
-    axis_sum<S1, S2, FP>(a1, a2, src, 1, off0 + z, off1 + y, off2 + x, Gy, w, t1, t2);
+    double t1, t2;
+    axis_sum_fp(a1, a2, src, 1, off0 + z, off1 + y, off2 + x, Gy, w, t1, t2);
     b1[q] = t1;
     b2[q] = t2;
   }
 }
 
 // z pass and decision: out (u8, the job's output box) = f > T.
-template <typename TIN, typename S1, typename S2, bool FP>
-__global__ void k_box_z_decide(const S1* __restrict__ b1, const S2* __restrict__ b2, Reg src,
-                               const TIN* __restrict__ in, DevBox B, DevOut O, int64_t n0, int64_t n1,
-                               int64_t n2, int64_t off0, int64_t off1, int64_t off2, int64_t Gz,
-                               int w, int method, double k, double c) {
+template <typename TIN>
+__global__ void k_box_z_decide_fp(const double* __restrict__ b1, const double* __restrict__ b2,
+                                  Reg src, const TIN* __restrict__ in, DevBox B, DevOut O,
+                                  int64_t n0, int64_t n1, int64_t n2, int64_t off0, int64_t off1,
+                                  int64_t off2, int64_t Gz, int w, int method, double k, double c) {
   const int64_t total = n0 * n1 * n2;
   const double nw = (double)(2 * w + 1) * (double)(2 * w + 1) * (double)(2 * w + 1);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t x = off2 + q % n2, y = off1 + (q / n2) % n1, z = off0 + q / (n1 * n2);
-    S1 t1;
-    S2 t2;
-    axis_sum<S1, S2, FP>(b1, b2, src, 0, z, y, x, Gz, w, t1, t2);
-    const double s1 = (double)t1, s2 = (double)t2;
-    const double m = __ddiv_rn(s1, nw);
-    double v = __dsub_rn(__ddiv_rn(s2, nw), __dmul_rn(m, m));
-    if (v < 0.0) v = 0.0;
-    const double sd = __dsqrt_rn(v);
-    double t;
-    if (method == HP_LOCAL_MEAN) t = __dsub_rn(m, c);
-    else if (method == HP_LOCAL_NIBLACK) t = __dadd_rn(m, __dmul_rn(k, sd));
-    else t = __dmul_rn(m, __dadd_rn(1.0, __dmul_rn(k, __dsub_rn(__ddiv_rn(sd, c), 1.0))));
+    double t1, t2;
+    axis_sum_fp(b1, b2, src, 0, z, y, x, Gz, w, t1, t2);
     const double f = (double)to_f32<TIN>(
         in[((z - B.lo[0]) * B.dims[1] + (y - B.lo[1])) * B.dims[2] + (x - B.lo[2])]);
     static_cast<uint8_t*>(O.ptr)[((z - O.lo[0]) * O.dims[1] + (y - O.lo[1])) * O.dims[2] +
-                                 (x - O.lo[2])] = f > t ? 1 : 0;
+                                 (x - O.lo[2])] = decide_fp64(t1, t2, nw, f, method, k, c) ? 1 : 0;
   }
 }
 
@@ -360,22 +360,6 @@ struct BoxDecide {
   double k, c;
 };
 
-// Exact decision f > T, T from the FP64 sequence of the oracle (one IEEE
-// rounding per operation). Out of line: the integer path reaches it only for
-// voxels next to their threshold.
-__device__ __noinline__ bool decide_fp64(double s1, double s2, double nw, double f, int method,
-                                            double k, double c) {
-  const double m = __ddiv_rn(s1, nw);
-  double v = __dsub_rn(__ddiv_rn(s2, nw), __dmul_rn(m, m));
-  if (v < 0.0) v = 0.0;
-  const double sd = __dsqrt_rn(v);
-  double t;
-  if (method == HP_LOCAL_MEAN) t = __dsub_rn(m, c);
-  else if (method == HP_LOCAL_NIBLACK) t = __dadd_rn(m, __dmul_rn(k, sd));
-  else t = __dmul_rn(m, __dadd_rn(1.0, __dmul_rn(k, __dsub_rn(__ddiv_rn(sd, c), 1.0))));
-  return f > t;
-}
-
 // The same decision from exact integer sums, settled in FP32 where the
 // threshold is clear of f and in FP64 (decide_fp64) otherwise. With
 // u = 2^-24, the FP32 threshold t32 takes at most 14 roundings over terms of
@@ -523,10 +507,9 @@ cudaError_t box_launch(const Job& job, int method, int w, double k, double c, cu
     k_box_x_fp<TIN><<<grid_for(vx), kBlk, 0, s>>>(in, job.in, FSum{a1, a2}, g.n_x[0], g.n_x[1],
                                                   g.n_x[2], g.rlo[0], g.rlo[1], job.core_lo[2],
                                                   job.gdims[2], w);
-    k_box_y<S1, S2, FP><<<grid_for(vy), kBlk, 0, s>>>(a1, a2, rx, b1, b2, g.n_y[0], g.n_y[1], g.n_y[2],
-                                                      g.rlo[0], job.core_lo[1], job.core_lo[2],
-                                                      job.gdims[1], w);
-    k_box_z_decide<TIN, S1, S2, FP><<<grid_for(cz * cy * cx), kBlk, 0, s>>>(
+    k_box_y_fp<<<grid_for(vy), kBlk, 0, s>>>(a1, a2, rx, b1, b2, g.n_y[0], g.n_y[1], g.n_y[2],
+                                             g.rlo[0], job.core_lo[1], job.core_lo[2], job.gdims[1], w);
+    k_box_z_decide_fp<TIN><<<grid_for(cz * cy * cx), kBlk, 0, s>>>(
         b1, b2, ry, in, job.in, job.out, cz, cy, cx, job.core_lo[0], job.core_lo[1], job.core_lo[2],
         job.gdims[0], w, method, k, c);
   }

@@ -30,7 +30,8 @@ host-link efficiency), `spheres128` (128^3 float32 Gaussian -> threshold ->
 cube morphology), `open1024` (1024^3 uint16 opening, closing, top-hat,
 unsharp mask and Gaussian local threshold), `features1024` (1024^3 uint16
 Hessian components and eigenvalues, box-window mean / Niblack / Sauvola
-thresholds),
+thresholds), `morph512` (512^3 uint16 erosion with cubes and balls of
+radius 7 to 16),
 `sweep` (out-of-core Gaussian on 1 to 16 GiB slabs under an 8e9-byte budget),
 `bank512` (512^3 float16 12-filter bank over 37 bricks,
 FMA roofline), `autograd256` (256^3 float32 forward + backward).
@@ -702,6 +703,48 @@ def run_open1024(args):
     return 0
 
 
+def run_morph512(args):
+    """512^3 uint16 porous volume: erosion with large structuring elements,
+    cubes of radius 7 and 16 (van Herk / Gil-Werman line passes through key
+    scratch, 20 B/voxel) and balls of radius 7, 10, 13 and 16 (tiled z-march,
+    2 B in and 2 B out per voxel)."""
+    import torch
+
+    import paper_2511_11890_b300 as hp
+    import synth
+    n = 512
+    f, _ = synth.porous(n, 5)
+    x = torch.from_numpy(f).cuda()
+    o = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    hbm_gbs, _, peak_kind = _peaks()
+    nvox = n ** 3
+    res, clks = {}, {}
+    for se, r, bpv in (("cube", 7, 20), ("cube", 16, 20), ("ball", 7, 4), ("ball", 10, 4),
+                       ("ball", 13, 4), ("ball", 16, 4)):
+        ms, clks[f"{se}{r}"] = _timed(lambda: hp.erode3d(x, se, r, out=o), args.steps,
+                                      max(3, args.warmup), stream)
+        gbs = nvox * bpv / (ms / 1e3) / 1e9
+        res[f"erode_{se}{r}"] = {"ms": ms, "voxels_per_s": nvox / (ms / 1e3), "GB/s": gbs,
+                                 "hbm_frac": gbs / hbm_gbs}
+    hp.stream_status(stream)
+    import oracle
+    cpu, sample = cpu_ops_sample([("erode_cube7", lambda v: oracle.erode3d(v, oracle.SE_CUBE, 7)),
+                                  ("erode_ball7", lambda v: oracle.erode3d(v, oracle.SE_BALL, 7))],
+                                 3.0, 32)
+    line = {"metric": "voxels/s, 512^3 uint16 erosion with the radius-7 cube", "unit": "voxels/s",
+            "value": res["erode_cube7"]["voxels_per_s"], "n_gpus": 1, "steps": args.steps,
+            "ms_per_step": res["erode_cube7"]["ms"], "higher_is_better": True, "dtype": "u16",
+            "data": "synthetic porous tomogram (seeded)",
+            "config": {"workload": "porous 512^3 u16: erosion, cube r = 7, 16; ball r = 7, 10, 13, 16"},
+            "ops": res, "hbm_peak_kind": peak_kind, "gpu_launches": 3 * args.steps,
+            "clocks": clks["cube7"],
+            "cpu_baseline": {"value": cpu["erode_cube7"], "unit": "voxels/s", "cores": 1,
+                             "kind": "oracle", "sample": sample, "ops": cpu}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_features1024(args):
     """1024^3 uint16 porous volume: the Hessian feature set at sigma 2 (the
     six second-derivative components to float32, and the three ascending
@@ -900,7 +943,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="porous1024",
                     choices=["porous1024", "ooc2048", "spheres128", "bank512", "autograd256",
-                             "open1024", "features1024", "sweep"])
+                             "open1024", "features1024", "morph512", "sweep"])
     ap.add_argument("--size", type=int, default=N,
                     help="edge of the in-HBM volume (1024 is the benchmark; smaller sizes "
                          "are for profiling captures)")
@@ -917,6 +960,8 @@ def main():
         return run_open1024(args)
     if args.workload == "features1024":
         return run_features1024(args)
+    if args.workload == "morph512":
+        return run_morph512(args)
     if args.workload == "sweep":
         return run_sweep(args)
     if args.impl == "reference":

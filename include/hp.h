@@ -223,10 +223,13 @@ int hp_threshold_local3d(const hp_volume* in, hp_volume* out, double sigma, doub
  *   HP_LOCAL_MEAN:    T = m - c
  *   HP_LOCAL_NIBLACK: T = m + k s
  *   HP_LOCAL_SAUVOLA: T = m (1 + k (s / c - 1))   (c = the dynamic range R)
- * Window sums run separably (x, then y, then z, each in increasing source
- * coordinate): exactly in integers for u8 / u16 input, in FP64 for f16 / f32;
- * m = S1/N, s = sqrt(max(S2/N - m^2, 0)), T and the comparison are FP64, one
- * rounded operation at a time, so the decision is reproducible bit for bit.
+ * Window sums run separably (x, then y, then z): exactly in integers for
+ * u8 / u16 input (running sums along each line), in FP64 for f16 / f32 (each
+ * window in increasing source coordinate); the decision is that of
+ * m = S1/N, s = sqrt(max(S2/N - m^2, 0)), T and f > T in FP64, one rounded
+ * operation at a time, so it is reproducible bit for bit. For integer input
+ * an FP32 evaluation with a proven error margin settles every voxel whose
+ * value is clear of T, and the FP64 sequence decides the rest.
  * radius in [0, 15]; c > 0 for Sauvola. Host volumes run out of core (halo
  * = radius); device volumes use library scratch of 24 (integer input) or 32
  * (floating-point input) bytes per voxel. */

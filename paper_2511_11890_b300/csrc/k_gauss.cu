@@ -526,6 +526,142 @@ __global__ void k_axis_pass(const TIN* __restrict__ src, const AxisBox S, float*
   }
 }
 
+// The same passes for radii above the z-march kernels (13 .. kMaxRGeneric),
+// with every output still one FMA chain from +0 over its taps in increasing
+// input coordinate (so the results equal k_axis_pass's bit for bit):
+//   z / y (k_gcol): one thread per line of the destination region, lines of
+//     consecutive x (every warp access is one coalesced row); the thread
+//     marches the line's reflected samples and keeps the 2R + 1 partial
+//     outputs in registers as a shift ring: sample i adds tap s to the output
+//     in slot s, slot 0 is then complete, and every slot moves down one.
+//   x (k_grow): a CTA stages kGR rows x (kGX + 2R) reflected samples as FP32
+//     in shared memory with coalesced loads, one thread marches each row the
+//     same way (odd row stride: conflict free) and writes its outputs over the
+//     samples it has consumed, and the CTA stores them coalesced.
+// Taps sit in the kernel parameters at compile-time indices, so each FMA
+// takes its weight from the constant bank.
+template <int R>
+struct GW {
+  float w[2 * R + 1];
+};
+
+template <int R, int AXIS, bool TO_OUT>
+__global__ void __launch_bounds__(128) k_gcol(const float* __restrict__ src, const AxisBox S,
+                                              float* __restrict__ dst, const AxisBox D, DevOut O,
+                                              const GW<R> W, int64_t Gn) {
+  constexpr int L = 2 * R + 1;
+  constexpr int a1 = AXIS == 0 ? 1 : 0;  // the other axes: a1 slow, x fast
+  const int64_t nlines = D.dims[a1] * D.dims[2];
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nlines) return;
+  int64_t c3[3];
+  c3[2] = D.lo[2] + l % D.dims[2];
+  c3[a1] = D.lo[a1] + l / D.dims[2];
+  c3[AXIS] = S.lo[AXIS];
+  const int64_t sstr = AXIS == 1 ? S.dims[2] : S.dims[1] * S.dims[2];
+  const float* sp = src + ((c3[0] - S.lo[0]) * S.dims[1] + (c3[1] - S.lo[1])) * S.dims[2] +
+                    (c3[2] - S.lo[2]) - S.lo[AXIS] * sstr;
+  c3[AXIS] = D.lo[AXIS];
+  int64_t ob, ostr;
+  if constexpr (TO_OUT) {
+    ob = ((c3[0] - O.lo[0]) * O.dims[1] + (c3[1] - O.lo[1])) * O.dims[2] + (c3[2] - O.lo[2]);
+    ostr = AXIS == 1 ? O.dims[2] : O.dims[1] * O.dims[2];
+  } else {
+    ob = ((c3[0] - D.lo[0]) * D.dims[1] + (c3[1] - D.lo[1])) * D.dims[2] + (c3[2] - D.lo[2]);
+    ostr = AXIS == 1 ? D.dims[2] : D.dims[1] * D.dims[2];
+  }
+  const int n = (int)D.dims[AXIS];
+  const int64_t p0 = D.lo[AXIS] - R;  // global coordinate of sample 0
+  const bool inner = p0 >= 0 && p0 + n + 2 * R <= Gn;
+  float acc[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) acc[k] = 0.0f;
+  // after sample i, output i - 2R is complete
+#pragma unroll 4
+  for (int i = 0; i < n + 2 * R; ++i) {
+    const float v = sp[(inner ? p0 + i : reflect(p0 + i, Gn)) * sstr];
+    const float done = fmaf(W.w[0], v, acc[0]);
+#pragma unroll
+    for (int k = 1; k < L; ++k) acc[k - 1] = fmaf(W.w[k], v, acc[k]);
+    acc[L - 1] = 0.0f;
+    if (i >= 2 * R) {
+      const int64_t q = ob + (int64_t)(i - 2 * R) * ostr;
+      if constexpr (TO_OUT) store_out(O, q, done);
+      else dst[q] = done;
+    }
+  }
+}
+
+constexpr int kGR = 128;  // rows per CTA (one thread each)
+constexpr int kGX = 64;   // outputs per row per CTA
+
+template <int R>
+constexpr int grow_ws() { return (kGX + 2 * R) | 1; }
+
+template <typename TIN, int R>
+__global__ void __launch_bounds__(kGR) k_grow(const TIN* __restrict__ src, const AxisBox S,
+                                              float* __restrict__ dst, const AxisBox D,
+                                              const GW<R> W, int64_t Gx) {
+  constexpr int L = 2 * R + 1, WS = grow_ws<R>();
+  extern __shared__ float Eg[];
+  __shared__ int64_t s_sb[kGR], s_db[kGR];
+  const int tid = threadIdx.x;
+  const int64_t nlines = D.dims[0] * D.dims[1];
+  const int64_t s0 = (int64_t)blockIdx.x * kGX;  // first output of the segment (region index)
+  const int n = (int)min((int64_t)kGX, D.dims[2] - s0);
+  const int ns = n + 2 * R;
+  const int64_t p0 = D.lo[2] + s0 - R;           // global x of sample 0
+  const bool inner = p0 >= 0 && p0 + ns <= Gx;
+  for (int64_t line0 = (int64_t)blockIdx.y * kGR; line0 < nlines; line0 += (int64_t)gridDim.y * kGR) {
+    const int nlin = (int)min((int64_t)kGR, nlines - line0);
+    {
+      const int64_t l = min(line0 + tid, nlines - 1);
+      const int64_t z = D.lo[0] + l / D.dims[1], y = D.lo[1] + l % D.dims[1];
+      s_sb[tid] = ((z - S.lo[0]) * S.dims[1] + (y - S.lo[1])) * S.dims[2] - S.lo[2];
+      s_db[tid] = ((z - D.lo[0]) * D.dims[1] + (y - D.lo[1])) * D.dims[2];
+    }
+    __syncthreads();
+    constexpr int kU = 8;  // loads in flight per thread
+    for (int i0 = tid; i0 < kGR * ns; i0 += kGR * kU) {
+      float v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * kGR, r = i / ns, pos = i - r * ns;
+        v[u] = 0.0f;
+        if (i < kGR * ns && r < nlin)
+          v[u] = to_f32<TIN>(src[s_sb[r] + (inner ? p0 + pos : reflect(p0 + pos, Gx))]);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * kGR;
+        if (i < kGR * ns) Eg[(i / ns) * WS + i % ns] = v[u];
+      }
+    }
+    __syncthreads();
+    {
+      float* e = Eg + tid * WS;
+      float acc[L];
+#pragma unroll
+      for (int k = 0; k < L; ++k) acc[k] = 0.0f;
+#pragma unroll 4
+      for (int i = 0; i < ns; ++i) {
+        const float v = e[i];
+        const float done = fmaf(W.w[0], v, acc[0]);
+#pragma unroll
+        for (int k = 1; k < L; ++k) acc[k - 1] = fmaf(W.w[k], v, acc[k]);
+        acc[L - 1] = 0.0f;
+        if (i >= 2 * R) e[i - 2 * R] = done;  // sample i - 2R is consumed
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < kGR * kGX; i += kGR) {
+      const int r = i / kGX, o = i - r * kGX;
+      if (r < nlin && o < n) dst[s_db[r] + s0 + o] = Eg[r * WS + o];
+    }
+    __syncthreads();  // the next round restages Eg and the row offsets
+  }
+}
+
 template <int R, typename TIN>
 cudaError_t launch_zm_t(const GaussParams& P, const CUtensorMap& map, dim3 grid, cudaStream_t s) {
   static bool attr_set = false;  // per instantiation; set once per process
@@ -568,6 +704,56 @@ bool needs_generic(const Job& job, int r) {
   return !(r >= 1 && r <= kMaxR && job.gdims[2] >= r && job.gdims[1] >= r);
 }
 
+// Generic path for radius R above the z-march kernels: k_grow, then k_gcol
+// along y, then along z into the job's output.
+template <int R>
+cudaError_t launch_generic_r(const Job& job, const Taps& taps, float* t1, float* t2,
+                             const SepRegions& g, cudaStream_t s) {
+  GW<R> wz, wy, wx;
+  for (int k = 0; k < 2 * R + 1; ++k) {
+    wz.w[k] = taps.w[0][k];
+    wy.w[k] = taps.w[1][k];
+    wx.w[k] = taps.w[2][k];
+  }
+  const AxisBox sin{{job.in.lo[0], job.in.lo[1], job.in.lo[2]},
+                    {job.in.dims[0], job.in.dims[1], job.in.dims[2]}};
+  const AxisBox s1{{g.rlo[0], g.rlo[1], job.core_lo[2]}, {g.n_x[0], g.n_x[1], g.n_x[2]}};
+  const AxisBox s2{{g.rlo[0], job.core_lo[1], job.core_lo[2]}, {g.n_y[0], g.n_y[1], g.n_y[2]}};
+  const AxisBox core{{job.core_lo[0], job.core_lo[1], job.core_lo[2]},
+                     {job.core_hi[0] - job.core_lo[0], job.core_hi[1] - job.core_lo[1],
+                      job.core_hi[2] - job.core_lo[2]}};
+  const int smem = kGR * grow_ws<R>() * 4;
+  const int64_t rows = s1.dims[0] * s1.dims[1];
+  const dim3 gx((unsigned)((s1.dims[2] + kGX - 1) / kGX),
+                (unsigned)std::min<int64_t>((rows + kGR - 1) / kGR, 65535));
+  cudaError_t e = cudaSuccess;
+  switch (job.in.dtype) {
+#define HP_GROW(T)                                                                             \
+  {                                                                                            \
+    static bool attr = false;                                                                  \
+    if (!attr) {                                                                               \
+      e = cudaFuncSetAttribute(k_grow<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+      if (e != cudaSuccess) return e;                                                          \
+      attr = true;                                                                             \
+    }                                                                                          \
+    k_grow<T, R><<<gx, kGR, smem, s>>>(static_cast<const T*>(job.in.ptr), sin, t1, s1, wx,      \
+                                       job.gdims[2]);                                          \
+  } break;
+    case HP_U8: HP_GROW(uint8_t)
+    case HP_U16: HP_GROW(uint16_t)
+    case HP_F16: HP_GROW(__half)
+    case HP_F32: HP_GROW(float)
+#undef HP_GROW
+    default: return cudaErrorInvalidValue;
+  }
+  const int64_t ly = s2.dims[0] * s2.dims[2], lz = core.dims[1] * core.dims[2];
+  k_gcol<R, 1, false><<<(unsigned)((ly + 127) / 128), 128, 0, s>>>(t1, s1, t2, s2, job.out, wy,
+                                                                    job.gdims[1]);
+  k_gcol<R, 0, true><<<(unsigned)((lz + 127) / 128), 128, 0, s>>>(t2, s2, nullptr, core, job.out,
+                                                                   wz, job.gdims[0]);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
   // Three passes x -> y -> z; the x and y passes go through two FP32
   // scratch volumes that the caller provides in job.scratch (the z pass
@@ -582,6 +768,15 @@ cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
   if (!job.scratch || job.scratch_bytes < b1 + b2) return cudaErrorInvalidValue;
   float* t1 = static_cast<float*>(job.scratch);
   float* t2 = t1 + b1 / sizeof(float);
+  switch (r) {
+#define HP_GR(RR) \
+  case RR: return launch_generic_r<RR>(job, taps, t1, t2, g, s);
+    HP_GR(13) HP_GR(14) HP_GR(15) HP_GR(16) HP_GR(17) HP_GR(18) HP_GR(19) HP_GR(20)
+    HP_GR(21) HP_GR(22) HP_GR(23) HP_GR(24) HP_GR(25) HP_GR(26) HP_GR(27) HP_GR(28)
+    HP_GR(29) HP_GR(30) HP_GR(31) HP_GR(32)
+#undef HP_GR
+    default: break;  // radii of the z-march kernels on volumes thinner than r: per-output passes
+  }
   AxisTaps1 wz, wy, wx;
   for (int k = 0; k < kMaxTaps; ++k) {
     wz.w[k] = taps.w[0][k];

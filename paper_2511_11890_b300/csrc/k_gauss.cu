@@ -576,8 +576,8 @@ __global__ void __launch_bounds__(128) k_gcol(const float* __restrict__ src, con
   float acc[L];
 #pragma unroll
   for (int k = 0; k < L; ++k) acc[k] = 0.0f;
-  // after sample i, output i - 2R is complete
-#pragma unroll 4
+  // after sample i, output i - 2R is complete (8 samples' loads in flight)
+#pragma unroll 8
   for (int i = 0; i < n + 2 * R; ++i) {
     const float v = sp[(inner ? p0 + i : reflect(p0 + i, Gn)) * sstr];
     const float done = fmaf(W.w[0], v, acc[0]);
@@ -601,7 +601,7 @@ constexpr int grow_ws() { return (kGX + 2 * R) | 1; }
 template <typename TIN, int R>
 __global__ void __launch_bounds__(kGR) k_grow(const TIN* __restrict__ src, const AxisBox S,
                                               float* __restrict__ dst, const AxisBox D,
-                                              const GW<R> W, int64_t Gx) {
+                                              const GW<R> W, int64_t Gx, int vec_rows) {
   constexpr int L = 2 * R + 1, WS = grow_ws<R>();
   extern __shared__ float Eg[];
   __shared__ int64_t s_sb[kGR], s_db[kGR];
@@ -622,6 +622,39 @@ __global__ void __launch_bounds__(kGR) k_grow(const TIN* __restrict__ src, const
     }
     __syncthreads();
     constexpr int kU = 8;  // loads in flight per thread
+    if (inner && vec_rows) {
+      // rows start on 16-byte boundaries: stage whole aligned 16-byte words
+      // covering samples [0, ns) of each row (a word never crosses the end of
+      // its row: row lengths are whole words)
+      constexpr int EPV = 16 / (int)sizeof(TIN);
+      const int64_t off0 = p0 - S.lo[2];
+      const int64_t w0 = off0 & ~(int64_t)(EPV - 1);
+      const int nw = (int)((off0 + ns - w0 + EPV - 1) / EPV);
+      constexpr int kV = 4;
+      for (int i0 = tid; i0 < nlin * nw; i0 += kGR * kV) {
+        uint4 q[kV];
+#pragma unroll
+        for (int u = 0; u < kV; ++u) {
+          const int i = i0 + u * kGR;
+          if (i < nlin * nw) {
+            const int r = i / nw, k = i - r * nw;
+            q[u] = *reinterpret_cast<const uint4*>(src + s_sb[r] + S.lo[2] + w0 + (int64_t)k * EPV);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kV; ++u) {
+          const int i = i0 + u * kGR;
+          if (i < nlin * nw) {
+            const int r = i / nw, k = i - r * nw;
+            const TIN* el = reinterpret_cast<const TIN*>(&q[u]);
+            const int pos0 = (int)(w0 - off0) + k * EPV;
+#pragma unroll
+            for (int c = 0; c < EPV; ++c)
+              if (pos0 + c >= 0 && pos0 + c < ns) Eg[r * WS + pos0 + c] = to_f32<TIN>(el[c]);
+          }
+        }
+      }
+    } else
     for (int i0 = tid; i0 < kGR * ns; i0 += kGR * kU) {
       float v[kU];
 #pragma unroll
@@ -736,8 +769,10 @@ cudaError_t launch_generic_r(const Job& job, const Taps& taps, float* t1, float*
       if (e != cudaSuccess) return e;                                                          \
       attr = true;                                                                             \
     }                                                                                          \
+    const int vec = reinterpret_cast<uintptr_t>(job.in.ptr) % 16 == 0 &&                       \
+                    (job.in.dims[2] * (int64_t)sizeof(T)) % 16 == 0;                            \
     k_grow<T, R><<<gx, kGR, smem, s>>>(static_cast<const T*>(job.in.ptr), sin, t1, s1, wx,      \
-                                       job.gdims[2]);                                          \
+                                       job.gdims[2], vec);                                     \
   } break;
     case HP_U8: HP_GROW(uint8_t)
     case HP_U16: HP_GROW(uint16_t)

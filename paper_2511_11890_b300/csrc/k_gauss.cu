@@ -576,18 +576,30 @@ __global__ void __launch_bounds__(128) k_gcol(const float* __restrict__ src, con
   float acc[L];
 #pragma unroll
   for (int k = 0; k < L; ++k) acc[k] = 0.0f;
-  // after sample i, output i - 2R is complete (8 samples' loads in flight)
-#pragma unroll 8
-  for (int i = 0; i < n + 2 * R; ++i) {
-    const float v = sp[(inner ? p0 + i : reflect(p0 + i, Gn)) * sstr];
-    const float done = fmaf(W.w[0], v, acc[0]);
+  // after sample i, output i - 2R is complete. The samples of a chunk of
+  // kGQ are loaded into registers before any of its outputs is stored (the
+  // stores could alias the source as far as the compiler can tell, which
+  // would otherwise keep each load behind the previous sample's store).
+  constexpr int kGQ = 8;
+  const int ns = n + 2 * R;
+  for (int i0 = 0; i0 < ns; i0 += kGQ) {
+    float v[kGQ];
 #pragma unroll
-    for (int k = 1; k < L; ++k) acc[k - 1] = fmaf(W.w[k], v, acc[k]);
-    acc[L - 1] = 0.0f;
-    if (i >= 2 * R) {
-      const int64_t q = ob + (int64_t)(i - 2 * R) * ostr;
-      if constexpr (TO_OUT) store_out(O, q, done);
-      else dst[q] = done;
+    for (int u = 0; u < kGQ; ++u)
+      v[u] = i0 + u < ns ? sp[(inner ? p0 + i0 + u : reflect(p0 + i0 + u, Gn)) * sstr] : 0.0f;
+#pragma unroll
+    for (int u = 0; u < kGQ; ++u) {
+      const int i = i0 + u;
+      if (i >= ns) break;
+      const float done = fmaf(W.w[0], v[u], acc[0]);
+#pragma unroll
+      for (int k = 1; k < L; ++k) acc[k - 1] = fmaf(W.w[k], v[u], acc[k]);
+      acc[L - 1] = 0.0f;
+      if (i >= 2 * R) {
+        const int64_t q = ob + (int64_t)(i - 2 * R) * ostr;
+        if constexpr (TO_OUT) store_out(O, q, done);
+        else dst[q] = done;
+      }
     }
   }
 }

@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(128) k_gcol(const float* __restrict__ src, con
   // kGQ are loaded into registers before any of its outputs is stored (the
   // stores could alias the source as far as the compiler can tell, which
   // would otherwise keep each load behind the previous sample's store).
-  constexpr int kGQ = 8;
+  constexpr int kGQ = 16;
   const int ns = n + 2 * R;
   for (int i0 = 0; i0 < ns; i0 += kGQ) {
     float v[kGQ];
@@ -688,14 +688,22 @@ __global__ void __launch_bounds__(kGR) k_grow(const TIN* __restrict__ src, const
       float acc[L];
 #pragma unroll
       for (int k = 0; k < L; ++k) acc[k] = 0.0f;
-#pragma unroll 4
-      for (int i = 0; i < ns; ++i) {
-        const float v = e[i];
-        const float done = fmaf(W.w[0], v, acc[0]);
+      // chunks of 8 samples loaded before their outputs are written back
+      // (output i - 2R overwrites a sample consumed 2R > 8 steps before)
+      for (int i0 = 0; i0 < ns; i0 += 8) {
+        float v[8];
 #pragma unroll
-        for (int k = 1; k < L; ++k) acc[k - 1] = fmaf(W.w[k], v, acc[k]);
-        acc[L - 1] = 0.0f;
-        if (i >= 2 * R) e[i - 2 * R] = done;  // sample i - 2R is consumed
+        for (int u = 0; u < 8; ++u) v[u] = i0 + u < ns ? e[i0 + u] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u;
+          if (i >= ns) break;
+          const float done = fmaf(W.w[0], v[u], acc[0]);
+#pragma unroll
+          for (int k = 1; k < L; ++k) acc[k - 1] = fmaf(W.w[k], v[u], acc[k]);
+          acc[L - 1] = 0.0f;
+          if (i >= 2 * R) e[i - 2 * R] = done;
+        }
       }
     }
     __syncthreads();

@@ -594,8 +594,8 @@ cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3]
     float* out = ax == 0 ? t1 : (ax == 1 ? t2 : dst);
     const int acc = ax == 2 ? accumulate : 0;
     // compile-time radius where the grid fits (lines and planes below 65536)
-    const bool fits = taps.r >= 1 && taps.r <= kMaxR && dims[0] < 65536 && dims[1] < 65536 &&
-                      dims[2] < (1LL << 31) / 4;
+    const bool fits = taps.r >= 1 && taps.r <= kMaxRGeneric && dims[0] < 65536 &&
+                      dims[1] < 65536 && dims[2] < (1LL << 31) / 4;
     if (fits) {
       cudaError_t e = cudaErrorInvalidValue;
       switch (taps.r) {
@@ -603,6 +603,10 @@ cudaError_t launch_sep_adjoint(const float* w, float* dst, const int64_t dims[3]
   case RR: e = launch_axis_r<RR>(src, out, dims, ax, a, acc, s); break;
         HP_AR(1) HP_AR(2) HP_AR(3) HP_AR(4) HP_AR(5) HP_AR(6)
         HP_AR(7) HP_AR(8) HP_AR(9) HP_AR(10) HP_AR(11) HP_AR(12)
+        HP_AR(13) HP_AR(14) HP_AR(15) HP_AR(16) HP_AR(17) HP_AR(18)
+        HP_AR(19) HP_AR(20) HP_AR(21) HP_AR(22) HP_AR(23) HP_AR(24)
+        HP_AR(25) HP_AR(26) HP_AR(27) HP_AR(28) HP_AR(29) HP_AR(30)
+        HP_AR(31) HP_AR(32)
 #undef HP_AR
       }
       if (e != cudaSuccess) return e;

@@ -146,3 +146,19 @@ def test_cube_subgradient_many_ties(rad, dilate):
     g = to_np(hp.morph3d_backward(to_dev(f), to_dev(w), dilate, "cube", rad))
     ref = oracle.morph3d_vjp(f, oracle.SE_CUBE, rad, dilate, w.astype(np.float64))
     assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape", [(40, 36, 64), (20, 90, 33)])
+def test_adjoint_large_radii_vs_oracle(shape):
+    """Adjoints of G, GM and LoG at sigma 5 and 9 (radii 15 and 27, above the
+    forward z-march kernels): the radius-templated transposes against the
+    oracle's adjoint, on a volume with interior x windows (64 = 4 x 16
+    columns) and one whose extents fall below 2r + 1 in z and x (every sample
+    reflected several times)."""
+    f = synth.spheres(shape, 12, synth.SEED_BASE + 5)
+    filt = [(hp.G, 5.0), (hp.GM, 5.0), (hp.LOG, 9.0)]
+    ws = [synth.normal_field(shape, synth.SEED_BASE + 60 + i) for i in range(len(filt))]
+    gin = to_np(hp.filterbank3d_adjoint(to_dev(f), [to_dev(w) for w in ws], filt))
+    ref = oracle.filterbank3d_vjp(f, [(OK[k], s) for k, s in filt], [w.astype(np.float64) for w in ws])
+    err = np.abs(gin - ref).max()
+    assert err <= 1e-4 * np.abs(ref).max(), err

@@ -526,8 +526,9 @@ __global__ void k_axis_pass(const TIN* __restrict__ src, const AxisBox S, float*
   }
 }
 
-// The same passes for radii above the z-march kernels (13 .. kMaxRGeneric),
-// with every output still one FMA chain from +0 over its taps in increasing
+// The same passes for every radius 1 .. kMaxRGeneric (above the z-march
+// kernels' 12, and any radius on volumes thinner than it in x or y), with
+// every output still one FMA chain from +0 over its taps in increasing
 // input coordinate (so the results equal k_axis_pass's bit for bit):
 //   z / y (k_gcol): one thread per line of the destination region, lines of
 //     consecutive x (every warp access is one coalesced row); the thread
@@ -688,8 +689,9 @@ __global__ void __launch_bounds__(kGR) k_grow(const TIN* __restrict__ src, const
       float acc[L];
 #pragma unroll
       for (int k = 0; k < L; ++k) acc[k] = 0.0f;
-      // chunks of 8 samples loaded before their outputs are written back
-      // (output i - 2R overwrites a sample consumed 2R > 8 steps before)
+      // chunks of 8 samples loaded into registers before their outputs are
+      // written back (output i - 2R overwrites a sample of this or an earlier
+      // chunk, already in registers or consumed)
       for (int i0 = 0; i0 < ns; i0 += 8) {
         float v[8];
 #pragma unroll
@@ -826,11 +828,12 @@ cudaError_t launch_generic(const Job& job, const Taps& taps, cudaStream_t s) {
   switch (r) {
 #define HP_GR(RR) \
   case RR: return launch_generic_r<RR>(job, taps, t1, t2, g, s);
-    HP_GR(13) HP_GR(14) HP_GR(15) HP_GR(16) HP_GR(17) HP_GR(18) HP_GR(19) HP_GR(20)
+    HP_GR(1) HP_GR(2) HP_GR(3) HP_GR(4) HP_GR(5) HP_GR(6) HP_GR(7) HP_GR(8) HP_GR(9) HP_GR(10)
+    HP_GR(11) HP_GR(12) HP_GR(13) HP_GR(14) HP_GR(15) HP_GR(16) HP_GR(17) HP_GR(18) HP_GR(19) HP_GR(20)
     HP_GR(21) HP_GR(22) HP_GR(23) HP_GR(24) HP_GR(25) HP_GR(26) HP_GR(27) HP_GR(28)
     HP_GR(29) HP_GR(30) HP_GR(31) HP_GR(32)
 #undef HP_GR
-    default: break;  // radii of the z-march kernels on volumes thinner than r: per-output passes
+    default: break;  // radius 0: per-output passes
   }
   AxisTaps1 wz, wy, wx;
   for (int k = 0; k < kMaxTaps; ++k) {

@@ -405,6 +405,9 @@ struct Op {
   std::function<size_t(const Job&)> scratch_bytes;
   // host-mode bricks also get a page-locked host buffer of the same size
   bool host_scratch = false;
+  // the kernels stage the input with TMA where its rows allow: device inputs
+  // whose rows do not are copied with padded rows first (pad_device_input)
+  bool pad_rows = true;
   // enqueue the op for one job: job.out is output 0, outs[k] output k (each
   // a dense box like job.out); job.scratch is set when scratch_bytes > 0.
   // Returns an hp_status.
@@ -805,22 +808,62 @@ static void begin_call() {
   g_stats.wall_ms = 0;
 }
 
-static int run_multi(const Op& op, const hp_volume* in, hp_volume* const* outs, void* stream) {
-  begin_call();
-  if (in->loc == HP_HOST) return run_host(op, in, outs);
+// Device inputs whose rows the TMA kernels cannot address (a base that is
+// not 16-byte aligned, or rows that are not a whole number of 16-byte words,
+// e.g. 2052 uint16 samples) would take the kernels' element-load paths,
+// 6-15x slower at 1024^3. Such an input is first copied, with rows padded to
+// 16 bytes, into library scratch (k_pad_rows on the stream); the job's
+// input box then describes the padded copy. The kernels never read the pad:
+// every source x reflects into [0, nx). pad_bytes returns the bytes of the
+// padded copy (0: none needed).
+static int64_t padded_nx(int64_t nx) { return (nx + 15) / 16 * 16; }  // a 16-byte row for every dtype
+
+static bool rows_aligned(const void* p, int64_t nx, size_t es) {
+  return (uintptr_t)p % 16 == 0 && ((size_t)nx * es) % 16 == 0;
+}
+
+static size_t pad_bytes(const Op& op, const hp_volume* in) {
+  const size_t es = dtype_size(in->dtype);
+  if (!op.pad_rows || es == 0 || rows_aligned(in->data, in->nx, es)) return 0;
+  return (size_t)padded_nx(in->nx) * es * (size_t)in->ny * (size_t)in->nz;
+}
+
+static int pad_device_input(Job& j, const hp_volume* in, Scratch& sc, size_t bytes,
+                            cudaStream_t s) {
+  void* p = nullptr;
+  cudaError_t e = sc.alloc(&p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "padded input copy");
+  const int64_t px = padded_nx(in->nx);
+  e = launch_pad_rows(in->data, p, in->dtype, in->nx, px, in->ny * in->nz, s);
+  if (e != cudaSuccess) return cuda_fail(e, "padded input copy");
+  j.in.ptr = p;
+  j.in.dims[2] = px;
+  return HP_OK;
+}
+
+// Runs op on a device job: the input padding where needed, kernel scratch
+// and the launch.
+static int run_device(const Op& op, const hp_volume* in, hp_volume* const* outs, int nout,
+                      cudaStream_t s) {
   Job j = whole_job(in, outs[0], op.out_dtype);
-  const cudaStream_t s = (cudaStream_t)stream;
   Scratch sc(s);
   const size_t need = op.scratch_bytes ? op.scratch_bytes(j) : 0;
-  if (need > 0) {
-    const int st = check_scratch_budget(need);
+  const size_t padb = pad_bytes(op, in);
+  if (need + padb > 0) {
+    const int st = check_scratch_budget(need + padb);
     if (st != HP_OK) return st;
+  }
+  if (padb > 0) {
+    const int st = pad_device_input(j, in, sc, padb, s);
+    if (st != HP_OK) return st;
+  }
+  if (need > 0) {
     cudaError_t e = sc.alloc(&j.scratch, need);
     if (e != cudaSuccess) return cuda_fail(e, "kernel scratch");
     j.scratch_bytes = need;
   }
-  std::vector<void*> ptrs(op.nout);
-  for (int k = 0; k < op.nout; ++k) ptrs[k] = outs[k]->data;
+  std::vector<void*> ptrs(nout);
+  for (int k = 0; k < nout; ++k) ptrs[k] = outs[k]->data;
   const int st = op.launch(j, ptrs.data(), s);
   if (st != HP_OK) return st;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -828,25 +871,16 @@ static int run_multi(const Op& op, const hp_volume* in, hp_volume* const* outs, 
   return HP_OK;
 }
 
+static int run_multi(const Op& op, const hp_volume* in, hp_volume* const* outs, void* stream) {
+  begin_call();
+  if (in->loc == HP_HOST) return run_host(op, in, outs);
+  return run_device(op, in, outs, op.nout, (cudaStream_t)stream);
+}
+
 static int run(const Op& op, const hp_volume* in, hp_volume* out, void* stream) {
   begin_call();
   if (in->loc == HP_HOST) return run_host(op, in, &out);
-  Job j = whole_job(in, out, op.out_dtype);
-  const cudaStream_t s = (cudaStream_t)stream;
-  Scratch sc(s);
-  const size_t need = op.scratch_bytes ? op.scratch_bytes(j) : 0;
-  if (need > 0) {
-    const int st = check_scratch_budget(need);
-    if (st != HP_OK) return st;
-    cudaError_t e = sc.alloc(&j.scratch, need);
-    if (e != cudaSuccess) return cuda_fail(e, "kernel scratch");
-    j.scratch_bytes = need;
-  }
-  const int st = op.launch(j, &out->data, s);
-  if (st != HP_OK) return st;
-  std::lock_guard<std::mutex> lk(g_mu);
-  g_stats.bricks = 1;
-  return HP_OK;
+  return run_device(op, in, &out, 1, (cudaStream_t)stream);
 }
 
 // Out-of-core filter bank (Sec. III-D applied to the bank): Z slabs whose
@@ -997,6 +1031,7 @@ int hp_threshold3d(const hp_volume* in, hp_volume* out, double t, void* stream) 
   Op op;
   op.halo = 0;
   op.out_dtype = HP_U8;
+  op.pad_rows = false;  // an elementwise comparison: no staging to gain from
   op.launch = [t](const Job& j, void* const*, cudaStream_t s) { return launched(launch_threshold(j, t, s)); };
   return run(op, in, out, stream);
 }

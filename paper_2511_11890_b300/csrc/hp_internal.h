@@ -143,6 +143,12 @@ bool make_tmap_3d(CUtensorMap* map, const void* base, int dtype, const int64_t d
 
 int num_sms();
 
+// Copy `rows` dense rows of n elements of dtype into rows of `pitch`
+// elements at dst (16-byte aligned; pitch * element size a multiple of 16),
+// the elements past n zero; on stream s.
+cudaError_t launch_pad_rows(const void* src, void* dst, int dtype, int64_t n, int64_t pitch,
+                            int64_t rows, cudaStream_t s);
+
 // out[i] = in[i] - out[i] over n elements of dtype (FP32 difference rounded
 // to the dtype), on stream s.
 cudaError_t launch_difference(const void* in, void* out, int dtype, int64_t n, cudaStream_t s);

@@ -275,8 +275,9 @@ __device__ __forceinline__ void zgroup_from(u64 (&acc)[ZP][L], const u64* zs, in
 }
 
 // Steady-state group: all kKP planes present, every output complete and
-// stored as one aligned FP32 vector at ob + K * pstride.
-template <int C, int L, int ZP, int KP>
+// stored at ob + K * pstride: one FP32 vector where the row allows (vec),
+// else one FP32 store per output (rows of an odd number of floats).
+template <int C, int L, int ZP, int KP, bool VEC>
 __device__ __forceinline__ void zgroup_fast(u64 (&acc)[ZP][L], const u64* zs, int zpl,
                                            const ZrParams& P, unsigned char* ob,
                                            int64_t pstride) {
@@ -298,10 +299,19 @@ __device__ __forceinline__ void zgroup_fast(u64 (&acc)[ZP][L], const u64* zs, in
     if (K == 2) zstep<(C + 2) % L, L, ZP>(acc, v, P, done);
     if (K == 3) zstep<(C + 3) % L, L, ZP>(acc, v, P, done);
     unsigned char* d = ob + K * pstride;
-    if constexpr (ZP == 2)
-      *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(done[0], done[1]);
-    else
-      *reinterpret_cast<u64*>(d) = done[0];
+    if constexpr (VEC) {
+      if constexpr (ZP == 2)
+        *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(done[0], done[1]);
+      else
+        *reinterpret_cast<u64*>(d) = done[0];
+    } else {
+#pragma unroll
+      for (int zp = 0; zp < ZP; ++zp) {
+        const float2 f = unpack2(done[zp]);
+        reinterpret_cast<float*>(d)[2 * zp] = f.x;
+        reinterpret_cast<float*>(d)[2 * zp + 1] = f.y;
+      }
+    }
   }
 }
 
@@ -514,7 +524,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
     p2_x[m] = ok ? k * G::XP + (NY * b / 2) * G::RPS + 2 * xp : 0;
     p2_z[m] = ok ? k * G::ZPL + (NY * b) * ZW + xp : 0;
   }
-  const bool zfast = S.zrow && S.ovec && S.of32;  // full aligned FP32 stores
+  const bool zfast = S.zrow && S.of32 && S.xrem == 2 * ZP;  // full FP32 outputs
   const u64* zsrc = Zb + zy * ZW + ZP * zxg;
 
   u64 acc[ZP][L];
@@ -577,16 +587,30 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
       const int oz0 = q0 - 2 * R;  // output plane completed by plane q0
       if (zfast && nv == KP && oz0 >= 0) {
         unsigned char* ob = S.ob + (int64_t)oz0 * S.pstride_b;
-        switch (ph) {
+        if (S.ovec) {
+          switch (ph) {
 #define HP_ZC(kk)                                                                              \
   case kk:                                                                                     \
-    if constexpr (kk < L) zgroup_fast<(kk < L ? kk : 0), L, ZP, KP>(acc, zsrc, G::ZPL, P, ob, S.pstride_b); \
+    if constexpr (kk < L) zgroup_fast<(kk < L ? kk : 0), L, ZP, KP, true>(acc, zsrc, G::ZPL, P, ob, S.pstride_b); \
     break;
-          HP_ZC(0) HP_ZC(1) HP_ZC(2) HP_ZC(3) HP_ZC(4) HP_ZC(5) HP_ZC(6) HP_ZC(7) HP_ZC(8)
-          HP_ZC(9) HP_ZC(10) HP_ZC(11) HP_ZC(12) HP_ZC(13) HP_ZC(14) HP_ZC(15) HP_ZC(16)
-          HP_ZC(17) HP_ZC(18) HP_ZC(19) HP_ZC(20) HP_ZC(21) HP_ZC(22) HP_ZC(23) HP_ZC(24)
+            HP_ZC(0) HP_ZC(1) HP_ZC(2) HP_ZC(3) HP_ZC(4) HP_ZC(5) HP_ZC(6) HP_ZC(7) HP_ZC(8)
+            HP_ZC(9) HP_ZC(10) HP_ZC(11) HP_ZC(12) HP_ZC(13) HP_ZC(14) HP_ZC(15) HP_ZC(16)
+            HP_ZC(17) HP_ZC(18) HP_ZC(19) HP_ZC(20) HP_ZC(21) HP_ZC(22) HP_ZC(23) HP_ZC(24)
 #undef HP_ZC
-          default: break;
+            default: break;
+          }
+        } else {
+          switch (ph) {
+#define HP_ZC(kk)                                                                              \
+  case kk:                                                                                     \
+    if constexpr (kk < L) zgroup_fast<(kk < L ? kk : 0), L, ZP, KP, false>(acc, zsrc, G::ZPL, P, ob, S.pstride_b); \
+    break;
+            HP_ZC(0) HP_ZC(1) HP_ZC(2) HP_ZC(3) HP_ZC(4) HP_ZC(5) HP_ZC(6) HP_ZC(7) HP_ZC(8)
+            HP_ZC(9) HP_ZC(10) HP_ZC(11) HP_ZC(12) HP_ZC(13) HP_ZC(14) HP_ZC(15) HP_ZC(16)
+            HP_ZC(17) HP_ZC(18) HP_ZC(19) HP_ZC(20) HP_ZC(21) HP_ZC(22) HP_ZC(23) HP_ZC(24)
+#undef HP_ZC
+            default: break;
+          }
         }
       } else {
         switch (ph) {

@@ -657,6 +657,43 @@ __global__ void k_difference_v(const uint4* __restrict__ in, uint4* __restrict__
   }
 }
 
+// Rows of `rows` x `n` elements of type T (dense, source) into rows of
+// `pitch` elements (destination, 16-byte aligned, pitch a whole number of
+// 16-byte words): one thread per destination word, elements past n zero.
+template <typename T>
+__global__ void k_pad_rows(const T* __restrict__ src, uint4* __restrict__ dst, int64_t n,
+                           int64_t pitch, int64_t rows) {
+  constexpr int V = 16 / sizeof(T);
+  const int64_t wpr = pitch / V;  // words per destination row
+  const int64_t total = rows * wpr;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / wpr, c0 = (q - r * wpr) * V;
+    const T* sr = src + r * n;
+    uint4 w;
+    T* e = reinterpret_cast<T*>(&w);
+#pragma unroll
+    for (int k = 0; k < V; ++k) e[k] = c0 + k < n ? sr[c0 + k] : T(0);
+    dst[q] = w;
+  }
+}
+
+cudaError_t launch_pad_rows(const void* src, void* dst, int dtype, int64_t n, int64_t pitch,
+                            int64_t rows, cudaStream_t s) {
+  const size_t es = dtype_size(dtype);
+  if (es == 0 || (pitch * (int64_t)es) % 16 != 0 || (uintptr_t)dst % 16 != 0 || pitch < n)
+    return cudaErrorInvalidValue;
+  const int64_t words = rows * pitch * (int64_t)es / 16;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((words + 255) / 256, (int64_t)num_sms() * 32));
+  uint4* d = static_cast<uint4*>(dst);
+  switch (es) {
+    case 1: k_pad_rows<uint8_t><<<grid, 256, 0, s>>>(static_cast<const uint8_t*>(src), d, n, pitch, rows); break;
+    case 2: k_pad_rows<uint16_t><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(src), d, n, pitch, rows); break;
+    default: k_pad_rows<uint32_t><<<grid, 256, 0, s>>>(static_cast<const uint32_t*>(src), d, n, pitch, rows); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_difference(const void* in, void* out, int dtype, int64_t n, cudaStream_t s) {
   const int64_t es = (int64_t)dtype_size(dtype);
   if (es > 0 && (uintptr_t)in % 16 == 0 && (uintptr_t)out % 16 == 0 && (n * es) % 16 == 0) {

@@ -298,18 +298,20 @@ __device__ __forceinline__ void zgroup_fast(u64 (&acc)[ZP][L], const u64* zs, in
     if (K == 1) zstep<(C + 1) % L, L, ZP>(acc, v, P, done);
     if (K == 2) zstep<(C + 2) % L, L, ZP>(acc, v, P, done);
     if (K == 3) zstep<(C + 3) % L, L, ZP>(acc, v, P, done);
+    // evict-first stores: the outputs are not read again here, and L2
+    // keeps the input rows that neighbouring tiles still have to read
     unsigned char* d = ob + K * pstride;
     if constexpr (VEC) {
       if constexpr (ZP == 2)
-        *reinterpret_cast<ulonglong2*>(d) = make_ulonglong2(done[0], done[1]);
+        __stcs(reinterpret_cast<ulonglong2*>(d), make_ulonglong2(done[0], done[1]));
       else
-        *reinterpret_cast<u64*>(d) = done[0];
+        __stcs(reinterpret_cast<float2*>(d), unpack2(done[0]));
     } else {
 #pragma unroll
       for (int zp = 0; zp < ZP; ++zp) {
         const float2 f = unpack2(done[zp]);
-        reinterpret_cast<float*>(d)[2 * zp] = f.x;
-        reinterpret_cast<float*>(d)[2 * zp + 1] = f.y;
+        __stcs(reinterpret_cast<float*>(d) + 2 * zp, f.x);
+        __stcs(reinterpret_cast<float*>(d) + 2 * zp + 1, f.y);
       }
     }
   }

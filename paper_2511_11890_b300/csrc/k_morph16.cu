@@ -741,9 +741,10 @@ __global__ void __launch_bounds__(kSThreads, 4)
       if (n >= 2 * R) {
         uint16_t* o = optr + (int64_t)(n - 2 * R) * pstride;
         if (full) {
+          // evict-first: L2 keeps the input rows neighbouring tiles still read
 #pragma unroll
           for (int i = 0; i < kSS; ++i)
-            *reinterpret_cast<uint32_t*>(o + i * rstride) = from_keys<KIND>(out[i]);
+            __stcs(reinterpret_cast<unsigned int*>(o + i * rstride), (unsigned int)from_keys<KIND>(out[i]));
         } else {
 #pragma unroll
           for (int i = 0; i < kSS; ++i) {

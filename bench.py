@@ -125,9 +125,10 @@ class ClockSampler:
 
 def _traffic(kernel: str, nvox: int):
     """DRAM bytes per launch of the dominant kernel from its committed ncu
-    capture (a smaller volume of the same generator, scaled by the voxel
-    count); None when that kernel is not the captured one or its sources
-    changed since the capture."""
+    capture (one-pass DRAM counters at the captured volume, scaled by the
+    voxel count where the bench runs another size: an estimate there, since
+    halo re-reads grow with the volume); None when that kernel is not the
+    captured one or its sources changed since the capture."""
     if kernel != "gauss_s4":
         return None
     try:

@@ -461,6 +461,7 @@ constexpr int kSKP = 4;                      // input planes per phase (TMA box 
 constexpr int kSNSG = 2;                     // plane groups in flight
 constexpr int kSThreads = kPC * (kPY / kSS);  // 128
 constexpr int kSFix = 8;                     // face cells per thread in registers
+constexpr int kSDrift = 96;                  // z-chunk length that keeps halo reuse in L2
 
 __host__ __device__ constexpr int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
 
@@ -795,7 +796,19 @@ cudaError_t launch_s(const Morph16Params& P0, const Job& job, int64_t tiles, int
       !make_tmap_3d(&one, job.in.ptr, job.in.dtype, dims, G::BW, G::BHP, 1))
     return cudaErrorNotSupported;
   Morph16Params P = P0;
-  P.zchunk = (int)pick_zchunk(cz, tiles, (int64_t)slots_per_sm * num_sms(), 2 * R + kSKP, kSKP);
+  const int64_t slots = (int64_t)slots_per_sm * num_sms();
+  P.zchunk = (int)pick_zchunk(cz, tiles, slots, 2 * R + kSKP, kSKP);
+  // Over a long chunk, CTAs that started together drift apart in z, until
+  // L2 no longer holds the halo rows one of them read for its neighbour
+  // (1024^3 ball-3 erosion: 128-plane chunks read 1.56x the input from
+  // DRAM, 96-plane chunks 1.40x, 64-plane chunks 1.19x but pay more
+  // pipeline fill). Where the grid runs many waves anyway, chunks are cut
+  // to about kSDrift planes.
+  if (P.zchunk > kSDrift) {
+    const int64_t n = (cz + kSDrift - 1) / kSDrift;
+    const int64_t zc = ((cz + n - 1) / n + kSKP - 1) / kSKP * kSKP;
+    if (tiles * ((cz + zc - 1) / zc) >= 4 * slots) P.zchunk = (int)zc;
+  }
   dim3 grid((unsigned)tiles, (unsigned)((cz + P.zchunk - 1) / P.zchunk));
   if (log_level() > 0)
     fprintf(stderr, "[hp] morph16 strip r=%d ball=%d kind=%d dilate=%d grid=%ux%u zchunk=%d slots/SM=%d\n",

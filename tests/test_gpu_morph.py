@@ -159,13 +159,15 @@ def test_cube_van_herk_out_of_core_within_budget():
 
 def test_full_size_face_planes_ball3_1024():
     """Erosion and dilation (ball r = 3) of the 1024^3 step on whole face
-    planes and an interior 64^3 block, bit for bit against the oracle."""
+    planes, an interior 64^3 block and an interior block across z = 256 and
+    z = 288 (where z chunks of 128 or 96 planes meet), bit for bit against
+    the oracle."""
     n = 1024
     f, _ = synth.porous(n, synth.SEED_BASE + 1)
     x = to_dev(f)
     rad = 3
     boxes = [((0, 0, 0), (1, n, n)), ((n - 1, 0, 0), (1, n, n)), ((0, 0, n - 1), (n, n, 1)),
-             ((0, 0, 0), (n, 1, n)), ((200, 600, 900), (64, 64, 64))]
+             ((0, 0, 0), (n, 1, n)), ((200, 600, 900), (64, 64, 64)), ((250, 300, 400), (48, 48, 48))]
     oracle.use_threads(True)
     try:
         for fn, dil in ((hp.erode3d, False), (hp.dilate3d, True)):

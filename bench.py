@@ -69,25 +69,71 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clock, its maximum and the clock-event (throttle) reasons, sampled
+    during the timed region: NVML polled from a thread every 5 ms, or
+    nvidia-smi every 20 ms where NVML cannot be opened (its first sample
+    taken before the timed region starts). Reads only."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines: list[str] = []
+        self.nv = None
+        self.samples: list[tuple[float, int]] = []
+        self.mx = None
+        self.stop = threading.Event()
+        self.nvml_error = None
+        self.first = threading.Event()
+
+    def _nvml(self):
+        import pynvml as nv
+        import torch
+        nv.nvmlInit()
+        h = None
+        try:  # the CUDA device's own GPU, whatever NVML's enumeration order
+            u = str(torch.cuda.get_device_properties(self.index).uuid)
+            h = nv.nvmlDeviceGetHandleByUUID(u if u.startswith("GPU-") else "GPU-" + u)
+        except Exception:
+            h = nv.nvmlDeviceGetHandleByIndex(self.index)
+        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.bits = (nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
+                     nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap)
+        self.mx = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+
+        def poll():
+            while not self.stop.is_set():
+                try:
+                    self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)),
+                                         int(reasons(h))))
+                except Exception:
+                    pass
+                self.stop.wait(0.005)
+        self.nv = nv
+        self.t = threading.Thread(target=poll, daemon=True)
+        self.t.start()
 
     def __enter__(self):
         try:
+            self._nvml()
+            return self
+        except Exception as e:
+            self.nv = None
+            self.nvml_error = f"{type(e).__name__}: {e}"[:160]
+        try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(timeout=3.0)
+            self.lines.clear()  # keep only samples taken from here on
         except Exception:
             self.proc = None
         return self
@@ -95,8 +141,12 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
 
     def __exit__(self, *exc):
+        if self.nv is not None:
+            self.stop.set()
+            self.t.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -105,8 +155,15 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], self.mx, set()
+        if self.nv is not None:
+            for mhz, r in self.samples:
+                sm.append(mhz)
+                for nm, b in zip(self.NAMES, self.bits):
+                    if r & b:
+                        reasons.add(nm)
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                    "reasons": sorted(reasons), "samples": len(sm), "source": "nvml, 5 ms"}
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
@@ -116,11 +173,14 @@ class ClockSampler:
                 mx = float(parts[1])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
+            for nm, v in zip(self.NAMES, parts[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+               "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 20 ms"}
+        if self.nvml_error:
+            out["nvml_error"] = self.nvml_error
+        return out
 
 
 def _traffic(kernel: str, nvox: int):

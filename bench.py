@@ -90,31 +90,78 @@ class ClockSampler:
         self.nvml_error = None
         self.first = threading.Event()
 
+    @staticmethod
+    def _nvml_lib():
+        """(max SM clock, SM clock, reasons) readers for one device handle:
+        the pynvml binding where installed, else NVML's C API through ctypes
+        (nvmlInit_v2, nvmlDeviceGetHandleByUUID / ByIndex_v2,
+        nvmlDeviceGetClockInfo, nvmlDeviceGetMaxClockInfo,
+        nvmlDeviceGetCurrentClocksEventReasons; NVML_CLOCK_SM = 1; reason
+        bits sw_power_cap 0x4, hw_slowdown 0x8, sw_thermal 0x20, hw_thermal
+        0x40)."""
+        try:
+            import pynvml as nv
+            nv.nvmlInit()
+            reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            return (nv.nvmlDeviceGetHandleByUUID, nv.nvmlDeviceGetHandleByIndex,
+                    lambda h: nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM),
+                    lambda h: nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), reasons, "pynvml")
+        except ImportError:
+            pass
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+        def ok(rc):
+            if rc != 0:
+                raise RuntimeError(f"NVML error {rc}")
+        ok(lib.nvmlInit_v2())
+
+        def by_uuid(u):
+            h = ctypes.c_void_p()
+            ok(lib.nvmlDeviceGetHandleByUUID(u.encode(), ctypes.byref(h)))
+            return h
+
+        def by_index(i):
+            h = ctypes.c_void_p()
+            ok(lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(i), ctypes.byref(h)))
+            return h
+
+        def clock(fn):
+            def get(h):
+                v = ctypes.c_uint()
+                ok(fn(h, ctypes.c_int(1), ctypes.byref(v)))
+                return v.value
+            return get
+        rfn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+        def reasons(h):
+            v = ctypes.c_ulonglong()
+            ok(rfn(h, ctypes.byref(v)))
+            return v.value
+        return (by_uuid, by_index, clock(lib.nvmlDeviceGetMaxClockInfo),
+                clock(lib.nvmlDeviceGetClockInfo), reasons, "ctypes")
+
     def _nvml(self):
-        import pynvml as nv
         import torch
-        nv.nvmlInit()
-        h = None
+        by_uuid, by_index, max_clock, clock, reasons, how = self._nvml_lib()
         try:  # the CUDA device's own GPU, whatever NVML's enumeration order
             u = str(torch.cuda.get_device_properties(self.index).uuid)
-            h = nv.nvmlDeviceGetHandleByUUID(u if u.startswith("GPU-") else "GPU-" + u)
+            h = by_uuid(u if u.startswith("GPU-") else "GPU-" + u)
         except Exception:
-            h = nv.nvmlDeviceGetHandleByIndex(self.index)
-        reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            nv.nvmlDeviceGetCurrentClocksThrottleReasons
-        self.bits = (nv.nvmlClocksEventReasonHwSlowdown, nv.nvmlClocksEventReasonHwThermalSlowdown,
-                     nv.nvmlClocksEventReasonSwThermalSlowdown, nv.nvmlClocksEventReasonSwPowerCap)
-        self.mx = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            h = by_index(self.index)
+        self.bits = (0x8, 0x40, 0x20, 0x4)  # NAMES order
+        self.mx = float(max_clock(h))
 
         def poll():
             while not self.stop.is_set():
                 try:
-                    self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)),
-                                         int(reasons(h))))
+                    self.samples.append((float(clock(h)), int(reasons(h))))
                 except Exception:
                     pass
                 self.stop.wait(0.005)
-        self.nv = nv
+        self.nv = how
         self.t = threading.Thread(target=poll, daemon=True)
         self.t.start()
 
@@ -163,7 +210,7 @@ class ClockSampler:
                     if r & b:
                         reasons.add(nm)
             return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                    "reasons": sorted(reasons), "samples": len(sm), "source": "nvml, 5 ms"}
+                    "reasons": sorted(reasons), "samples": len(sm), "source": f"nvml ({self.nv}), 5 ms"}
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:

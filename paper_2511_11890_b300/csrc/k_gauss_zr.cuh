@@ -51,6 +51,13 @@ constexpr int kKP = 4;   // input planes per pipeline phase (= TMA box depth)
 constexpr int kNSG = 3;  // plane groups in flight (stage ring depth)
 constexpr int kFixC = 4; // face cells a thread patches from its register list
 
+// CTAs started per SM. At radii 5 and 6 (two CTAs per SM) the x-pass items
+// of a phase give two of an SM's four schedulers one warp-round more than
+// the other two; every other CTA an SM starts shifts its item map by two
+// warps, so that two co-resident CTAs load the schedulers in complementary
+// ways (warp w issues on scheduler w mod 4).
+static __device__ unsigned g_sm_ctas[1024];
+
 struct ZrParams {
   Job job;
   u64 w2[3][2 * kMaxR + 1];  // taps per axis (z, y, x), each as an FP32 pair (w, w)
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
   constexpr int BW = G::BW, BH = G::BH, RA = G::RA, ES = G::ES, XS = G::XS, ZW = G::ZW;
   constexpr int KP = kKP, NSG = G::NSG;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ int s_abort, s_fixovf;
+  __shared__ int s_abort, s_fixovf, s_rot;
   __shared__ int s_frow[BH], s_fcol[BW], s_brow[BH], s_bcol[BW];
   __shared__ int s_nbr, s_nbc;
 
@@ -403,6 +410,13 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
   }
   if (tid == 0) {
     s_abort = 0;
+    int rot = 0;
+    if constexpr (R == 5 || R == 6) {
+      unsigned sm;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+      rot = (atomicAdd(&g_sm_ctas[sm & 1023u], 1u) & 1u) ? 64 : 0;
+    }
+    s_rot = rot;
     prefetch_tmap(&tmap_deep);
     prefetch_tmap(&tmap_one);
     for (int s = 0; s < NSG; ++s) mbar_init(&bars[s], 1);
@@ -505,7 +519,7 @@ __global__ void __launch_bounds__(ZrShape<R>::NT, ZrShape<R>::MINB)
   bool p1_any = false;  // the thread reads stages (and so waits for them)
 #pragma unroll
   for (int m = 0; m < G::MI1; ++m) {
-    const int i1 = tid + m * NT;
+    const int i1 = (tid + s_rot) % NT + m * NT;  // a permutation of the threads
     const int k = i1 / G::NI1, sl = i1 - k * G::NI1;
     const int g = ((sl >> 3) % G::GH) * 4 + (sl & 3);
     const int rp = ((sl >> 3) / G::GH) * 2 + ((sl >> 2) & 1);

@@ -571,7 +571,8 @@ def run_hp(args):
             "data": f"synthetic porous tomogram (seeded, porosity {porosity:.3f})",
             "config": {"workload": f"porous {N}^3 u16: gaussian s=1,2,4 -> f32; erode+dilate ball r=3",
                        "volume": [N, N, N], "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs (2 GiB) and outputs (16 GiB) larger than L2",
+                       "l2": f"input ({2 * N ** 3 / 2 ** 30:.3g} GiB) and outputs "
+                             f"({16 * N ** 3 / 2 ** 30:.3g} GiB) larger than L2",
                        "hbm_frac_of_step": hbm_step_frac},
             "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "cpu_baseline_mt": cpu_mt,
             "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk.summary(),
